@@ -1,0 +1,181 @@
+"""Seeded synthetic spike-train workloads (inputs only; no counting arithmetic).
+
+Every generator draws from ``numpy.random.Generator(PCG64(seed))`` and returns
+plain arrays, so the CUDA path and the CPU oracle are fed identical inputs.
+The streams stand in for the paper's Sym26 simulation and its cortical-culture
+recordings (Section 6.1), which are not available: each neuron (event type)
+fires as a homogeneous Poisson process, and a few causal chains are embedded
+as cascades (a trigger fires the chain's first neuron, each next neuron fires
+after a delay drawn inside one of the interval set's intervals).
+
+Times are integer microseconds (uint32).  Events are ordered by time, ties by
+type, then by emission order, which is the order every consumer must keep.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+LMAX = 8
+
+# Interval set of the 64-type workloads: (0,2], (2,5], (5,10], (10,20] ms, in microseconds.
+I_MS4 = np.array([[0, 2000], [2000, 5000], [5000, 10000], [10000, 20000]], np.uint32)
+
+
+@dataclass
+class Stream:
+    types: np.ndarray          # uint8[n]
+    t: np.ndarray              # uint32[n], non-decreasing
+    n_types: int
+    chains: list = field(default_factory=list)   # [(types tuple, interval-index tuple, rate Hz)]
+
+    @property
+    def n(self) -> int:
+        return int(self.t.shape[0])
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def poisson_stream(seed, n_types, rates_hz, duration_s, chains=(), delay_fn=None):
+    """Background Poisson firing plus embedded cascades.
+
+    rates_hz: scalar or float[n_types].  chains: iterable of
+    (types tuple, trigger rate Hz, per-edge (lo, hi) microsecond ranges);
+    each trigger at t0 emits types[0] at t0 and types[k+1] at
+    t_k + d_k, d_k drawn by ``delay_fn(rng, lo, hi)`` (default: the interval
+    midpoint plus integer jitter in [-500, 500] µs, clipped inside (lo, hi]).
+    Events past the duration are dropped.
+    """
+    rng = _rng(seed)
+    T_us = int(round(duration_s * 1e6))
+    rates = np.broadcast_to(np.asarray(rates_hz, dtype=np.float64), (n_types,))
+    ts, ty = [], []
+    for a in range(n_types):
+        k = rng.poisson(rates[a] * duration_s)
+        ts.append(np.floor(rng.random(k) * T_us).astype(np.int64))
+        ty.append(np.full(k, a, np.int64))
+    if delay_fn is None:
+        def delay_fn(r, lo, hi, size):
+            mid = (int(lo) + int(hi)) // 2
+            d = mid + r.integers(-500, 501, size=size)
+            return np.clip(d, int(lo) + 1, int(hi))
+    for ctypes_, rate, edges in chains:
+        k = rng.poisson(rate * duration_s)
+        t0 = np.floor(rng.random(k) * T_us).astype(np.int64)
+        cur = t0
+        ts.append(cur)
+        ty.append(np.full(k, ctypes_[0], np.int64))
+        for j, (lo, hi) in enumerate(edges):
+            cur = cur + delay_fn(rng, lo, hi, k)
+            ts.append(cur.copy())
+            ty.append(np.full(k, ctypes_[j + 1], np.int64))
+    t_all = np.concatenate(ts) if ts else np.zeros(0, np.int64)
+    ty_all = np.concatenate(ty) if ty else np.zeros(0, np.int64)
+    emit = np.arange(t_all.shape[0])
+    keep = t_all < T_us
+    t_all, ty_all, emit = t_all[keep], ty_all[keep], emit[keep]
+    order = np.lexsort((emit, ty_all, t_all))
+    return t_all[order].astype(np.uint32), ty_all[order].astype(np.uint8)
+
+
+def chance_theta(rate_hz, duration_s, window_s, factor=5.0, power=1):
+    """ceil(factor * rate*T * (1 - exp(-rate*window))**power): a support threshold
+    set at `factor` times a Poisson chance count (the workload's stated rule)."""
+    return int(math.ceil(factor * rate_hz * duration_s * (1 - math.exp(-rate_hz * window_s)) ** power))
+
+
+# --------------------------------------------------------------------------- named workloads
+def tiny_mining(seed=0xFE01):
+    """16 types at 20 Hz for 10 s, cascade 0->1->2->3 at 2 Hz with delays uniform in
+    [4500, 5500] µs; interval set {(4,6] ms}; threshold 15; mined to length 4."""
+    def uni(r, lo, hi, size):
+        return r.integers(4500, 5501, size=size)
+    t, ty = poisson_stream(seed, 16, 20.0, 10.0,
+                           chains=[((0, 1, 2, 3), 2.0, [(4000, 6000)] * 3)], delay_fn=uni)
+    I = np.array([[4000, 6000]], np.uint32)
+    return dict(name="tiny_mining_16types_10s", stream=Stream(ty, t, 16, [((0, 1, 2, 3), (0, 0, 0), 2.0)]),
+                intervals=I, theta=15, max_len=4)
+
+
+def _chains(rng, n_chains, n_types, lens, n_int, rate_lo, rate_hi):
+    out = []
+    for _ in range(n_chains):
+        L = int(rng.choice(lens))
+        tys = tuple(int(x) for x in rng.choice(n_types, size=L, replace=False))
+        ivs = tuple(int(x) for x in rng.integers(0, n_int, size=L - 1))
+        rate = float(rng.uniform(rate_lo, rate_hi))
+        out.append((tys, ivs, rate))
+    return out
+
+
+def single_recording(seed=0xFE02, deep=False):
+    """64 types at 20 Hz for 300 s with 8 chains (lengths 4-6, 1-3 Hz, delays inside
+    intervals of I_MS4 with +-0.5 ms jitter); level-2 candidates 64*63*4 = 16,128;
+    mined to length 6.  Threshold: 5x the chance count of the narrowest interval
+    (1177), or 300 for the deep variant."""
+    rng = _rng(seed + 0x100)
+    ch = _chains(rng, 8, 64, [4, 5, 6], len(I_MS4), 1.0, 3.0)
+    spec = [(tys, rate, [tuple(I_MS4[i]) for i in ivs]) for tys, ivs, rate in ch]
+    t, ty = poisson_stream(seed, 64, 20.0, 300.0, chains=spec)
+    theta = 300 if deep else chance_theta(20.0, 300.0, 0.002)
+    return dict(name="single_recording_64types_300s" + ("_deep" if deep else ""),
+                stream=Stream(ty, t, 64, ch), intervals=I_MS4.copy(), theta=theta, max_len=6)
+
+
+def large_stream(seed=0xFE04, n_candidates=100_000, duration_s=3600.0):
+    """64 types at 50 Hz for 1 h plus 8 chains; 100k random candidates of lengths 3-5
+    with distinct types and random intervals from I_MS4; threshold 5x the chance
+    count of the narrowest length-3 episode."""
+    rng = _rng(seed + 0x100)
+    ch = _chains(rng, 8, 64, [4, 5, 6], len(I_MS4), 1.0, 3.0)
+    spec = [(tys, rate, [tuple(I_MS4[i]) for i in ivs]) for tys, ivs, rate in ch]
+    t, ty = poisson_stream(seed, 64, 50.0, duration_s, chains=spec)
+    cands = random_candidates(seed + 0x200, n_candidates, 64, [3, 4, 5], len(I_MS4))
+    theta = chance_theta(50.0, duration_s, 0.002, power=2)
+    return dict(name=f"large_stream_64types_{int(duration_s)}s", stream=Stream(ty, t, 64, ch),
+                intervals=I_MS4.copy(), theta=theta, candidates=cands)
+
+
+def random_candidates(seed, m, n_types, lens, n_int, distinct=True):
+    """m random episodes: (len uint8[m], types uint8[m,8], ivl uint8[m,7])."""
+    rng = _rng(seed)
+    L = rng.choice(np.asarray(lens), size=m).astype(np.uint8)
+    E = np.zeros((m, LMAX), np.uint8)
+    iv = np.zeros((m, LMAX - 1), np.uint8)
+    for c in range(m):
+        k = int(L[c])
+        if distinct:
+            E[c, :k] = rng.choice(n_types, size=k, replace=False)
+        else:
+            E[c, :k] = rng.integers(0, n_types, size=k)
+        iv[c, : k - 1] = rng.integers(0, n_int, size=k - 1)
+    return L, E, iv
+
+
+def level2_candidates(frequent_types, n_intervals):
+    """All ordered pairs of distinct types, once per interval, in canonical order
+    (first type, interval, second type)."""
+    f = list(frequent_types)
+    rows = [(a, iv, b) for a in f for iv in range(n_intervals) for b in f if a != b]
+    m = len(rows)
+    L = np.full(m, 2, np.uint8)
+    E = np.zeros((m, LMAX), np.uint8)
+    iv = np.zeros((m, LMAX - 1), np.uint8)
+    for c, (a, i, b) in enumerate(rows):
+        E[c, 0], E[c, 1], iv[c, 0] = a, b, i
+    return L, E, iv
+
+
+def tiny_stream(seed, n, n_types, max_gap_us, tie_prob=0.2):
+    """A short random stream for brute-force checks: gaps uniform in [1, max_gap]
+    with some zero gaps (timestamp ties)."""
+    rng = _rng(seed)
+    gaps = rng.integers(1, max_gap_us + 1, size=n)
+    gaps[rng.random(n) < tie_prob] = 0
+    t = np.cumsum(gaps).astype(np.uint32)
+    ty = rng.integers(0, n_types, size=n).astype(np.uint8)
+    return ty, t
