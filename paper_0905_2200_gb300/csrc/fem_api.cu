@@ -1,0 +1,722 @@
+// fem_api.cu -- the C ABI of libfem.so (include/fem.h): contexts, resident
+// streams, the counting driver (segment choice, capacity retries), Algorithm 4
+// and the level-wise miner of Problem 1.  Every step of the method runs in the
+// kernels of fem_stream.cu, fem_count.cu and fem_mine.cu; this file only
+// allocates device memory, launches, and copies results.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fem_internal.cuh"
+
+using namespace fem;
+
+struct fem_result {
+    std::vector<std::vector<fem_episode>> eps;    // [level-1]
+    std::vector<std::vector<uint32_t>> counts;  // [level-1]
+};
+
+namespace {
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+}  // namespace
+
+struct fem_ctx {
+    int device = 0;
+    cudaStream_t own = nullptr;
+    fem_config cfg{};
+    int sm_count = 152;
+    std::map<int32_t, StreamDev> streams;
+    int32_t next_id = 1;
+    uint32_t *d_err = nullptr;    // device error word
+    uint32_t *d_small = nullptr;  // 64 device words for counters
+    uint32_t *h_small = nullptr;  // 64 pinned host words
+    std::map<std::string, DevBuf> bufs;
+    std::vector<fem_level_stats> stats;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+#define CK(x)                                   \
+    do {                                        \
+        cudaError_t e_ = (x);                   \
+        if (e_ != cudaSuccess) return FEM_ECUDA; \
+    } while (0)
+#define RET(x)                  \
+    do {                        \
+        int r_ = (x);           \
+        if (r_ != FEM_OK) return r_; \
+    } while (0)
+
+// d_small word assignment
+enum { W_COUNT0 = 0, W_COUNT1 = 1, W_COUNT2 = 2, W_INFO = 8 /* 2 words */ };
+
+template <typename T>
+int dbuf(fem_ctx *c, const char *name, size_t count, T **out) {
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 256);
+    DevBuf &b = c->bufs[name];
+    if (b.cap < bytes) {
+        size_t nb = std::max(bytes, (size_t)(b.cap * 3 / 2));
+        if (b.p) cudaFree(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+        nb = (nb + 4095) & ~(size_t)4095;
+        if (cudaMalloc(&b.p, nb) != cudaSuccess) {
+            cudaGetLastError();
+            return FEM_ENOMEM;
+        }
+        b.cap = nb;
+    }
+    *out = static_cast<T *>(b.p);
+    return FEM_OK;
+}
+
+cudaStream_t pick(fem_ctx *c, void *s) { return s ? static_cast<cudaStream_t>(s) : c->own; }
+
+int read_words(fem_ctx *c, const uint32_t *d, uint32_t n, uint32_t *h, cudaStream_t st) {
+    CK(cudaMemcpyAsync(c->h_small, d, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::memcpy(h, c->h_small, n * sizeof(uint32_t));
+    return FEM_OK;
+}
+
+int read_err(fem_ctx *c, cudaStream_t st, uint32_t *err) {
+    return read_words(c, c->d_err, 1, err, st);
+}
+
+int err_status(uint32_t e) {
+    if (e & ERR_TIMEOUT) return FEM_ETIMEOUT;
+    if (e & ERR_BADEP) return FEM_EINVAL;
+    if (e & ERR_TYPE) return FEM_ETYPE;
+    if (e & ERR_UNSORTED) return FEM_EUNSORTED;
+    return FEM_OK;
+}
+
+const StreamDev *find_stream(fem_ctx *c, int32_t id) {
+    auto it = c->streams.find(id);
+    return it == c->streams.end() ? nullptr : &it->second;
+}
+
+int check_intervals(const StreamDev &s, const fem_interval *I, uint32_t nI) {
+    if (nI > FEM_MAX_INTERVALS) return FEM_EINVAL;
+    if (nI && !I) return FEM_EINVAL;
+    uint64_t max_hi = 0;
+    for (uint32_t i = 0; i < nI; ++i) {
+        if (I[i].lo_us >= I[i].hi_us) return FEM_EINVAL;
+        max_hi = std::max<uint64_t>(max_hi, I[i].hi_us);
+    }
+    // deadlines t + hi + 1 must fit in 32 bits
+    if ((uint64_t)s.t_max + max_hi + 1 > 0xFFFFFFFFull) return FEM_ERANGE;
+    return FEM_OK;
+}
+
+int upload_intervals(fem_ctx *c, const fem_interval *I, uint32_t nI, cudaStream_t st,
+                     uint2 **d_ivl) {
+    RET(dbuf(c, "ivl", std::max<uint32_t>(nI, 1), d_ivl));
+    if (nI) CK(cudaMemcpyAsync(*d_ivl, I, nI * sizeof(uint2), cudaMemcpyHostToDevice, st));
+    return FEM_OK;
+}
+
+// Segments per episode for one pass.  One thread per (episode, segment); the
+// aim is about 2048 resident threads per SM, with segments of at least four
+// chunks so the look-back window stays a small fraction of the work.
+uint32_t choose_segments(fem_ctx *c, const StreamDev &s, uint32_t m, bool distinct) {
+    if (s.n_chunks == 0) return 1;
+    uint32_t maxP = std::max<uint32_t>(1, s.n_chunks / 4);
+    maxP = std::min<uint32_t>(maxP, 65535);
+    if (c->cfg.segments) return std::min<uint32_t>(c->cfg.segments, s.n_chunks);
+    if (!distinct) return 1;
+    const uint64_t target = (uint64_t)c->sm_count * 2048;
+    uint64_t P = (target + m - 1) / m;
+    if (P < 2) return 1;
+    return (uint32_t)std::min<uint64_t>(P, maxP);
+}
+
+uint32_t choose_threads(fem_ctx *c, int N, int pass, bool mc, uint32_t R, uint32_t offs) {
+    if (c->cfg.threads_per_block) return c->cfg.threads_per_block;
+    for (uint32_t T : {128u, 64u, 32u}) {
+        if (count_smem_bytes(N, pass, mc, R, T, offs) <= 80 * 1024) return T;
+    }
+    return 32;
+}
+
+struct PassInfo {
+    uint32_t segments = 1;
+};
+
+// One counting pass over m candidates (all of length N) -> out[0..m).
+int count_pass(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const uint32_t *gather,
+               uint32_t m, int N, const uint2 *d_ivl, uint32_t nI, int pass, uint32_t *out,
+               bool distinct, cudaStream_t st, PassInfo *info) {
+    if (m == 0) return FEM_OK;
+    CountParams p{};
+    p.bev = s.bev;
+    p.boff = s.boff;
+    p.cfirst = s.cfirst;
+    p.offs = s.offs;
+    p.n_chunks = s.n_chunks;
+    p.n = s.n;
+    p.K = s.K;
+    p.cands = cands;
+    p.gather = gather;
+    p.m = m;
+    p.ivl = d_ivl;
+    p.n_ivl = nI;
+    p.out = out;
+    p.err = c->d_err;
+    uint8_t *redo;
+    RET(dbuf(c, "redo", m, &redo));
+    CK(cudaMemsetAsync(redo, 0, m, st));
+    p.redo = redo;
+
+    uint32_t P = choose_segments(c, s, m, distinct);
+    uint32_t R = 1;
+    if (pass == FEM_PASS_EXACT) R = c->cfg.ring_capacity ? c->cfg.ring_capacity : 16;
+    if (P > 1 && pass == FEM_PASS_EXACT && R > 32) R = 32;
+    if (!count_config_supported(N, pass, P > 1, R)) return FEM_EINVAL;
+    const uint32_t cps = P > 1 ? (s.n_chunks + P - 1) / P : std::max<uint32_t>(s.n_chunks, 1);
+    if (P > 1) P = (s.n_chunks + cps - 1) / cps;
+    p.cps = cps;
+    p.P = P;
+    if (P > 1) {
+        RET(dbuf(c, "tables", (size_t)P * m * S_MAX, &p.tables));
+    }
+    const uint32_t T = choose_threads(c, N, pass, P > 1, R, s.offs);
+    CK(launch_count(N, pass, P > 1, R, T, p, st));
+    if (P > 1) CK(launch_stitch(p.tables, m, P, out, redo, c->d_err, st));
+    if (info) info->segments = P;
+
+    uint32_t e;
+    RET(read_err(c, st, &e));
+    RET(err_status(e));
+    if (!(e & (ERR_RING | ERR_TABLE))) return FEM_OK;
+
+    // Recount the flagged episodes with one segment and larger rings.
+    uint32_t *ridx, *rg, *rout, *scratch;
+    RET(dbuf(c, "redo_idx", m, &ridx));
+    RET(dbuf(c, "redo_scratch", compact_scratch_words(m), &scratch));
+    CK(launch_compact(nullptr, redo, 0, m, ridx, c->d_small + W_COUNT2, scratch, st));
+    uint32_t r;
+    RET(read_words(c, c->d_small + W_COUNT2, 1, &r, st));
+    if (r == 0) return FEM_OK;
+    RET(dbuf(c, "redo_gather", r, &rg));
+    RET(dbuf(c, "redo_out", r, &rout));
+    CK(launch_compose_idx(gather, ridx, r, rg, st));
+    const uint32_t caps[] = {16, 32, 128};
+    for (uint32_t R2 : caps) {
+        if (pass == FEM_PASS_EXACT && R2 < R) continue;
+        if (pass == FEM_PASS_RELAXED && R2 != 16) continue;
+        CK(cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), st));
+        CountParams q = p;
+        q.gather = rg;
+        q.m = r;
+        q.out = rout;
+        q.P = 1;
+        q.cps = std::max<uint32_t>(s.n_chunks, 1);
+        q.tables = nullptr;
+        RET(dbuf(c, "redo2", r, &q.redo));
+        CK(cudaMemsetAsync(q.redo, 0, r, st));
+        const uint32_t Rq = pass == FEM_PASS_EXACT ? R2 : 1;
+        const uint32_t T2 = choose_threads(c, N, pass, false, Rq, s.offs);
+        CK(launch_count(N, pass, false, Rq, T2, q, st));
+        RET(read_err(c, st, &e));
+        RET(err_status(e));
+        if (!(e & ERR_RING)) {
+            CK(launch_scatter_u32(rout, ridx, r, out, st));
+            return FEM_OK;
+        }
+    }
+    return FEM_EOVERFLOW;
+}
+
+// Validate a candidate set (optionally gathered) and count it with `pass`,
+// grouping candidates by length.  out[i] is the count of candidate i of the
+// (gathered) set.
+int count_any(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const uint32_t *gather,
+              uint32_t m, const uint2 *d_ivl, uint32_t nI, int pass, uint32_t *out,
+              cudaStream_t st) {
+    if (m == 0) return FEM_OK;
+    CK(cudaMemsetAsync(c->d_small + W_INFO, 0, 2 * sizeof(uint32_t), st));
+    CK(launch_validate_cands(cands, gather, m, s.K, nI, c->d_small + W_INFO, c->d_err, st));
+    uint32_t info[2], e;
+    RET(read_words(c, c->d_small + W_INFO, 2, info, st));
+    RET(read_err(c, st, &e));
+    RET(err_status(e));
+    const bool distinct = info[1] == 0;
+    const uint32_t lens = info[0];
+    if (__builtin_popcount(lens) == 1) {
+        const int N = __builtin_ctz(lens);
+        return count_pass(c, s, cands, gather, m, N, d_ivl, nI, pass, out, distinct, st, nullptr);
+    }
+    uint8_t *flags;
+    uint32_t *idx, *g2, *tmp, *scratch;
+    RET(dbuf(c, "len_flags", m, &flags));
+    RET(dbuf(c, "len_idx", m, &idx));
+    RET(dbuf(c, "len_gather", m, &g2));
+    RET(dbuf(c, "len_out", m, &tmp));
+    RET(dbuf(c, "len_scratch", compact_scratch_words(m), &scratch));
+    for (int N = 1; N <= FEM_MAX_LEN; ++N) {
+        if (!(lens & (1u << N))) continue;
+        CK(launch_len_flags(cands, gather, m, (uint32_t)N, flags, st));
+        CK(launch_compact(nullptr, flags, 0, m, idx, c->d_small + W_COUNT1, scratch, st));
+        uint32_t k;
+        RET(read_words(c, c->d_small + W_COUNT1, 1, &k, st));
+        if (!k) continue;
+        CK(launch_compose_idx(gather, idx, k, g2, st));
+        RET(count_pass(c, s, cands, g2, k, N, d_ivl, nI, pass, tmp, distinct, st, nullptr));
+        CK(launch_scatter_u32(tmp, idx, k, out, st));
+    }
+    return FEM_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+const char *fem_strerror(int s) {
+    switch (s) {
+        case FEM_OK: return "ok";
+        case FEM_EINVAL: return "invalid argument";
+        case FEM_EUNSORTED: return "stream times are not non-decreasing";
+        case FEM_ETYPE: return "event type out of range";
+        case FEM_ERANGE: return "time span plus interval bound exceeds 32 bits";
+        case FEM_ENOMEM: return "out of memory";
+        case FEM_EADMIT: return "request not admitted";
+        case FEM_ETIMEOUT: return "bounded device wait timed out";
+        case FEM_ECUDA: return "CUDA runtime error";
+        case FEM_EOVERFLOW: return "internal capacity exceeded";
+        case FEM_ENOSTREAM: return "unknown stream id";
+        default: return "unknown status";
+    }
+}
+
+int fem_create(fem_ctx **out, int device) {
+    if (!out) return FEM_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return FEM_ECUDA;
+    }
+    fem_ctx *c = new (std::nothrow) fem_ctx;
+    if (!c) return FEM_ENOMEM;
+    c->device = device;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) !=
+            cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&c->d_err, sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&c->d_small, 64 * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost(&c->h_small, 64 * sizeof(uint32_t)) != cudaSuccess ||
+        cudaEventCreate(&c->ev[0]) != cudaSuccess || cudaEventCreate(&c->ev[1]) != cudaSuccess) {
+        cudaGetLastError();
+        fem_destroy(c);
+        return FEM_ECUDA;
+    }
+    cudaMemset(c->d_err, 0, sizeof(uint32_t));
+    *out = c;
+    return FEM_OK;
+}
+
+int fem_destroy(fem_ctx *c) {
+    if (!c) return FEM_EINVAL;
+    cudaSetDevice(c->device);
+    if (c->own) cudaStreamSynchronize(c->own);
+    for (auto &kv : c->streams) {
+        StreamDev &s = kv.second;
+        cudaFree(s.t);
+        cudaFree(s.type);
+        cudaFree(s.bev);
+        cudaFree(s.boff);
+        cudaFree(s.cfirst);
+        cudaFree(s.hist);
+    }
+    for (auto &kv : c->bufs) cudaFree(kv.second.p);
+    if (c->d_err) cudaFree(c->d_err);
+    if (c->d_small) cudaFree(c->d_small);
+    if (c->h_small) cudaFreeHost(c->h_small);
+    for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->own) cudaStreamDestroy(c->own);
+    delete c;
+    return FEM_OK;
+}
+
+int fem_set_config(fem_ctx *c, const fem_config *cfg) {
+    if (!c) return FEM_EINVAL;
+    if (!cfg) {
+        c->cfg = fem_config{};
+        return FEM_OK;
+    }
+    if (cfg->threads_per_block &&
+        (cfg->threads_per_block % 32 || cfg->threads_per_block > 256))
+        return FEM_EINVAL;
+    if (cfg->ring_capacity && !count_config_supported(2, FEM_PASS_EXACT, false, cfg->ring_capacity))
+        return FEM_EINVAL;
+    c->cfg = *cfg;
+    return FEM_OK;
+}
+
+int fem_load_stream(fem_ctx *c, const uint8_t *types, const uint32_t *t_us, uint64_t n,
+                    uint32_t n_types, int on_device, void *cuda_stream, int32_t *id_out) {
+    if (!c || !id_out || n_types == 0 || n_types > FEM_MAX_TYPES) return FEM_EINVAL;
+    if (n && (!types || !t_us)) return FEM_EINVAL;
+    if (n >= 0xFFFFFFF0ull) return FEM_EINVAL;
+    cudaSetDevice(c->device);
+    cudaStream_t st = pick(c, cuda_stream);
+    StreamDev s;
+    s.n = n;
+    s.K = n_types;
+    s.n_chunks = (uint32_t)((n + CHUNK - 1) / CHUNK);
+    s.offs = offs_stride(n_types);
+    const size_t nn = std::max<uint64_t>(n, 1);
+    const size_t nc = std::max<uint32_t>(s.n_chunks, 1);
+    bool okm = cudaMalloc(&s.t, nn * 4) == cudaSuccess && cudaMalloc(&s.type, nn) == cudaSuccess &&
+               cudaMalloc(&s.bev, nc * CHUNK * 8) == cudaSuccess &&
+               cudaMalloc(&s.boff, nc * s.offs * 2) == cudaSuccess &&
+               cudaMalloc(&s.cfirst, (nc + 1) * 4) == cudaSuccess &&
+               cudaMalloc(&s.hist, 256 * 4) == cudaSuccess;
+    auto release = [&] {
+        cudaFree(s.t);
+        cudaFree(s.type);
+        cudaFree(s.bev);
+        cudaFree(s.boff);
+        cudaFree(s.cfirst);
+        cudaFree(s.hist);
+    };
+    if (!okm) {
+        cudaGetLastError();
+        release();
+        return FEM_ENOMEM;
+    }
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    int rc = FEM_OK;
+    do {
+        if (cudaMemsetAsync(c->d_err, 0, 4, st) != cudaSuccess ||
+            cudaMemsetAsync(s.hist, 0, 256 * 4, st) != cudaSuccess ||
+            cudaMemsetAsync(s.cfirst, 0xFF, (nc + 1) * 4, st) != cudaSuccess) {
+            rc = FEM_ECUDA;
+            break;
+        }
+        if (n) {
+            if (cudaMemcpyAsync(s.t, t_us, n * 4, kind, st) != cudaSuccess ||
+                cudaMemcpyAsync(s.type, types, n, kind, st) != cudaSuccess ||
+                launch_load_stream(s, st, c->d_err) != cudaSuccess) {
+                rc = FEM_ECUDA;
+                break;
+            }
+        }
+        uint32_t e = 0;
+        if ((rc = read_err(c, st, &e)) != FEM_OK) break;
+        if ((rc = err_status(e)) != FEM_OK) break;
+        if (n) {
+            uint32_t tm;
+            if ((rc = read_words(c, s.t + (n - 1), 1, &tm, st)) != FEM_OK) break;
+            s.t_max = tm;
+        }
+    } while (0);
+    if (rc != FEM_OK) {
+        cudaGetLastError();
+        cudaStreamSynchronize(st);
+        release();
+        return rc;
+    }
+    const int32_t id = c->next_id++;
+    c->streams[id] = s;
+    *id_out = id;
+    return FEM_OK;
+}
+
+int fem_free_stream(fem_ctx *c, int32_t id) {
+    if (!c) return FEM_EINVAL;
+    auto it = c->streams.find(id);
+    if (it == c->streams.end()) return FEM_ENOSTREAM;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    StreamDev &s = it->second;
+    cudaFree(s.t);
+    cudaFree(s.type);
+    cudaFree(s.bev);
+    cudaFree(s.boff);
+    cudaFree(s.cfirst);
+    cudaFree(s.hist);
+    c->streams.erase(it);
+    return FEM_OK;
+}
+
+int fem_type_counts(fem_ctx *c, int32_t id, uint32_t *counts_out) {
+    if (!c || !counts_out) return FEM_EINVAL;
+    const StreamDev *s = find_stream(c, id);
+    if (!s) return FEM_ENOSTREAM;
+    cudaSetDevice(c->device);
+    CK(cudaMemcpyAsync(counts_out, s->hist, s->K * 4, cudaMemcpyDeviceToHost, c->own));
+    CK(cudaStreamSynchronize(c->own));
+    return FEM_OK;
+}
+
+int fem_count_candidates(fem_ctx *c, int32_t id, const fem_episode *cands, uint32_t m,
+                         int cands_on_device, const fem_interval *I, uint32_t nI, int pass,
+                         uint32_t *counts_out, int counts_on_device, void *cuda_stream) {
+    if (!c || (m && (!cands || !counts_out))) return FEM_EINVAL;
+    if (pass != FEM_PASS_RELAXED && pass != FEM_PASS_EXACT) return FEM_EINVAL;
+    const StreamDev *s = find_stream(c, id);
+    if (!s) return FEM_ENOSTREAM;
+    RET(check_intervals(*s, I, nI));
+    if (m == 0) return FEM_OK;
+    cudaSetDevice(c->device);
+    cudaStream_t st = pick(c, cuda_stream);
+    CK(cudaMemsetAsync(c->d_err, 0, 4, st));
+    uint2 *d_ivl;
+    RET(upload_intervals(c, I, nI, st, &d_ivl));
+    const fem_episode *dc = cands;
+    if (!cands_on_device) {
+        fem_episode *tmp;
+        RET(dbuf(c, "cands_in", m, &tmp));
+        CK(cudaMemcpyAsync(tmp, cands, (size_t)m * sizeof(fem_episode), cudaMemcpyHostToDevice, st));
+        dc = tmp;
+    }
+    uint32_t *dout = counts_out;
+    if (!counts_on_device) RET(dbuf(c, "counts_out", m, &dout));
+    RET(count_any(c, *s, dc, nullptr, m, d_ivl, nI, pass, dout, st));
+    if (!counts_on_device) {
+        CK(cudaMemcpyAsync(counts_out, dout, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return FEM_OK;
+}
+
+int fem_count_two_pass(fem_ctx *c, int32_t id, const fem_episode *cands, uint32_t m,
+                       int cands_on_device, const fem_interval *I, uint32_t nI, uint32_t theta,
+                       uint32_t *exact_out, uint8_t *survived_out, int outs_on_device,
+                       void *cuda_stream) {
+    if (!c || (m && !cands)) return FEM_EINVAL;
+    const StreamDev *s = find_stream(c, id);
+    if (!s) return FEM_ENOSTREAM;
+    RET(check_intervals(*s, I, nI));
+    if (m == 0) return FEM_OK;
+    cudaSetDevice(c->device);
+    cudaStream_t st = pick(c, cuda_stream);
+    CK(cudaMemsetAsync(c->d_err, 0, 4, st));
+    uint2 *d_ivl;
+    RET(upload_intervals(c, I, nI, st, &d_ivl));
+    const fem_episode *dc = cands;
+    if (!cands_on_device) {
+        fem_episode *tmp;
+        RET(dbuf(c, "cands_in", m, &tmp));
+        CK(cudaMemcpyAsync(tmp, cands, (size_t)m * sizeof(fem_episode), cudaMemcpyHostToDevice, st));
+        dc = tmp;
+    }
+    uint32_t *rel, *idx, *ex, *exo, *scratch;
+    uint8_t *sv;
+    RET(dbuf(c, "tp_rel", m, &rel));
+    RET(dbuf(c, "tp_idx", m, &idx));
+    RET(dbuf(c, "tp_ex", m, &ex));
+    RET(dbuf(c, "scratch", compact_scratch_words(m), &scratch));
+    exo = (outs_on_device && exact_out) ? exact_out : nullptr;
+    if (!exo) RET(dbuf(c, "tp_exo", m, &exo));
+    sv = (outs_on_device && survived_out) ? survived_out : nullptr;
+    if (!sv) RET(dbuf(c, "tp_sv", m, &sv));
+    // first pass: relaxed counts, eliminate count < theta
+    RET(count_any(c, *s, dc, nullptr, m, d_ivl, nI, FEM_PASS_RELAXED, rel, st));
+    CK(launch_compact(rel, nullptr, theta, m, idx, c->d_small + W_COUNT0, scratch, st));
+    uint32_t ms;
+    RET(read_words(c, c->d_small + W_COUNT0, 1, &ms, st));
+    // second pass: exact counts of the survivors
+    RET(count_any(c, *s, dc, idx, ms, d_ivl, nI, FEM_PASS_EXACT, ex, st));
+    CK(cudaMemsetAsync(exo, 0, (size_t)m * 4, st));
+    CK(cudaMemsetAsync(sv, 0, m, st));
+    CK(launch_scatter_u32(ex, idx, ms, exo, st));
+    CK(launch_fill_flags(idx, ms, sv, st));
+    if (!outs_on_device) {
+        if (exact_out) CK(cudaMemcpyAsync(exact_out, exo, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+        if (survived_out) CK(cudaMemcpyAsync(survived_out, sv, m, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    return FEM_OK;
+}
+
+int fem_mine_levelwise(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t nI,
+                       uint32_t theta, uint32_t max_len, void *cuda_stream, fem_result **out) {
+    if (!c || !out || max_len < 1 || max_len > FEM_MAX_LEN) return FEM_EINVAL;
+    *out = nullptr;
+    const StreamDev *sp = find_stream(c, id);
+    if (!sp) return FEM_ENOSTREAM;
+    const StreamDev &s = *sp;
+    RET(check_intervals(s, I, nI));
+    cudaSetDevice(c->device);
+    cudaStream_t st = pick(c, cuda_stream);
+    CK(cudaMemsetAsync(c->d_err, 0, 4, st));
+    c->stats.clear();
+    fem_result *res = new (std::nothrow) fem_result;
+    if (!res) return FEM_ENOMEM;
+    res->eps.resize(max_len);
+    res->counts.resize(max_len);
+    auto fail = [&](int rc) {
+        delete res;
+        return rc;
+    };
+#define RETF(x)                         \
+    do {                                \
+        int r_ = (x);                   \
+        if (r_ != FEM_OK) return fail(r_); \
+    } while (0)
+#define CKF(x)                                         \
+    do {                                               \
+        if ((x) != cudaSuccess) return fail(FEM_ECUDA); \
+    } while (0)
+
+    uint2 *d_ivl;
+    RETF(upload_intervals(c, I, nI, st, &d_ivl));
+    // level 1: the count of a one-node episode is the number of events of its type
+    uint32_t *ftypes;
+    RETF(dbuf(c, "ftypes", 256, &ftypes));
+    CKF(launch_type_filter(s.hist, s.K, theta, ftypes, c->d_small + W_COUNT0, st));
+    std::vector<uint32_t> hist(s.K), ft(256);
+    CKF(cudaMemcpyAsync(hist.data(), s.hist, s.K * 4, cudaMemcpyDeviceToHost, st));
+    CKF(cudaMemcpyAsync(ft.data(), ftypes, 256 * 4, cudaMemcpyDeviceToHost, st));
+    uint32_t f1;
+    RETF(read_words(c, c->d_small + W_COUNT0, 1, &f1, st));
+    for (uint32_t i = 0; i < f1; ++i) {
+        fem_episode e;
+        std::memset(&e, 0, sizeof(e));
+        e.types[0] = (uint8_t)ft[i];
+        e.len = 1;
+        res->eps[0].push_back(e);
+        res->counts[0].push_back(hist[ft[i]]);
+    }
+    if (max_len < 2 || f1 < 2 || nI == 0) {
+        *out = res;
+        return FEM_OK;
+    }
+    // level 2: ordered pairs of distinct frequent types x intervals
+    uint64_t m64 = (uint64_t)f1 * nI * (f1 - 1);
+    if (m64 > 0xFFFFFFF0ull) return fail(FEM_ENOMEM);
+    uint32_t m = (uint32_t)m64;
+    const char *cname[2] = {"candsA", "candsB"};
+    int cur = 0;
+    fem_episode *cands;
+    RETF(dbuf(c, cname[cur], m, &cands));
+    cudaEventRecord(c->ev[0], st);
+    CKF(launch_level2(ftypes, f1, nI, cands, st));
+    cudaEventRecord(c->ev[1], st);
+    float ms_gen = 0;
+    for (uint32_t N = 2; N <= max_len && m > 0; ++N) {
+        fem_level_stats ls{};
+        ls.level = N;
+        ls.candidates = m;
+        ls.ms_generate = 0;
+        cudaEventSynchronize(c->ev[1]);
+        cudaEventElapsedTime(&ms_gen, c->ev[0], c->ev[1]);
+        ls.ms_generate = ms_gen;
+        uint32_t *rel, *idx_s, *ex, *idx_f, *fidx, *fcnt, *scratch;
+        fem_episode *F;
+        RETF(dbuf(c, "rel", m, &rel));
+        RETF(dbuf(c, "idx_s", m, &idx_s));
+        RETF(dbuf(c, "scratch", compact_scratch_words(m), &scratch));
+        // first pass (Algorithm 3) on every candidate
+        PassInfo pi;
+        cudaEventRecord(c->ev[0], st);
+        RETF(count_pass(c, s, cands, nullptr, m, (int)N, d_ivl, nI, FEM_PASS_RELAXED, rel, true,
+                        st, &pi));
+        cudaEventRecord(c->ev[1], st);
+        cudaEventSynchronize(c->ev[1]);
+        cudaEventElapsedTime(&ls.ms_relaxed, c->ev[0], c->ev[1]);
+        ls.segments = pi.segments;
+        // eliminate relaxed < theta
+        cudaEventRecord(c->ev[0], st);
+        CKF(launch_compact(rel, nullptr, theta, m, idx_s, c->d_small + W_COUNT0, scratch, st));
+        cudaEventRecord(c->ev[1], st);
+        uint32_t ms;
+        RETF(read_words(c, c->d_small + W_COUNT0, 1, &ms, st));
+        cudaEventElapsedTime(&ls.ms_compact, c->ev[0], c->ev[1]);
+        ls.survivors = ms;
+        // second pass (Algorithm 1) on the survivors
+        RETF(dbuf(c, "ex", ms, &ex));
+        RETF(dbuf(c, "idx_f", ms, &idx_f));
+        cudaEventRecord(c->ev[0], st);
+        RETF(count_pass(c, s, cands, idx_s, ms, (int)N, d_ivl, nI, FEM_PASS_EXACT, ex, true, st,
+                        nullptr));
+        cudaEventRecord(c->ev[1], st);
+        cudaEventSynchronize(c->ev[1]);
+        cudaEventElapsedTime(&ls.ms_exact, c->ev[0], c->ev[1]);
+        CKF(launch_compact(ex, nullptr, theta, ms, idx_f, c->d_small + W_COUNT1, scratch, st));
+        uint32_t f;
+        RETF(read_words(c, c->d_small + W_COUNT1, 1, &f, st));
+        ls.frequent = f;
+        c->stats.push_back(ls);
+        if (f == 0) break;
+        RETF(dbuf(c, "fidx", f, &fidx));
+        RETF(dbuf(c, "fcnt", f, &fcnt));
+        RETF(dbuf(c, "F", f, &F));
+        CKF(launch_compose_idx(idx_s, idx_f, f, fidx, st));
+        CKF(launch_gather_episodes(cands, fidx, f, F, nullptr, nullptr, st));
+        CKF(launch_gather_episodes(nullptr, idx_f, f, nullptr, ex, fcnt, st));
+        res->eps[N - 1].resize(f);
+        res->counts[N - 1].resize(f);
+        CKF(cudaMemcpyAsync(res->eps[N - 1].data(), F, (size_t)f * sizeof(fem_episode),
+                            cudaMemcpyDeviceToHost, st));
+        CKF(cudaMemcpyAsync(res->counts[N - 1].data(), fcnt, (size_t)f * 4,
+                            cudaMemcpyDeviceToHost, st));
+        if (N == max_len) {
+            CKF(cudaStreamSynchronize(st));
+            break;
+        }
+        // join level N -> N + 1
+        uint32_t *jc, *joff;
+        RETF(dbuf(c, "jc", f, &jc));
+        RETF(dbuf(c, "joff", f, &joff));
+        cudaEventRecord(c->ev[0], st);
+        CKF(launch_join_count(F, f, N, jc, st));
+        CKF(launch_exclusive_scan(jc, f, joff, c->d_small + W_COUNT2, scratch, st));
+        uint32_t mn;
+        RETF(read_words(c, c->d_small + W_COUNT2, 1, &mn, st));
+        cur ^= 1;
+        RETF(dbuf(c, cname[cur], std::max<uint32_t>(mn, 1), &cands));
+        CKF(launch_join_emit(F, f, N, joff, cands, st));
+        cudaEventRecord(c->ev[1], st);
+        m = mn;
+    }
+    CKF(cudaStreamSynchronize(st));
+    uint32_t e;
+    RETF(read_err(c, st, &e));
+    RETF(err_status(e));
+    *out = res;
+    return FEM_OK;
+#undef RETF
+#undef CKF
+}
+
+int fem_result_level(const fem_result *r, uint32_t level, uint32_t *m_out,
+                     const fem_episode **eps, const uint32_t **counts) {
+    if (!r || !m_out || level < 1 || level > r->eps.size()) return FEM_EINVAL;
+    *m_out = (uint32_t)r->eps[level - 1].size();
+    if (eps) *eps = r->eps[level - 1].data();
+    if (counts) *counts = r->counts[level - 1].data();
+    return FEM_OK;
+}
+
+uint32_t fem_result_max_level(const fem_result *r) {
+    if (!r) return 0;
+    uint32_t L = 0;
+    for (uint32_t i = 0; i < r->eps.size(); ++i)
+        if (!r->eps[i].empty()) L = i + 1;
+    return L;
+}
+
+void fem_result_free(fem_result *r) { delete r; }
+
+int fem_last_mine_stats(fem_ctx *c, fem_level_stats *out, uint32_t cap) {
+    if (!c || (cap && !out)) return FEM_EINVAL;
+    const uint32_t k = std::min<uint32_t>(cap, (uint32_t)c->stats.size());
+    for (uint32_t i = 0; i < k; ++i) out[i] = c->stats[i];
+    return (int)k;
+}
+
+}  // extern "C"

@@ -1,0 +1,396 @@
+// fem_count.cuh -- the counting kernels (Algorithm 1 exact, Algorithm 3 relaxed),
+// one thread per (episode, segment).
+//
+// Data flow per block: the block's threads count T episodes over one stream
+// segment.  Thread 0 streams the segment's chunks into two shared-memory stages
+// with 1-D bulk (TMA) copies completed on mbarriers; every thread then merges,
+// by local index, the groups of its episode's N types in the staged chunk, so
+// it visits exactly the events that can change its state machine, in stream
+// order.  Nothing per event is read from global memory.
+//
+// Machines (node k = 0..N-1, edge k joins node k and k+1 with interval (lo, hi]):
+//  * relaxed (Algorithm 3, Section 5.3.1): one slot per node holding the
+//    deadline s + hi + 1 of the latest admitted time s (0 = unset);
+//  * exact (Algorithm 1, Section 5.1): per node a FIFO ring of admitted times in
+//    shared memory; entries older than hi are dropped (they can never satisfy
+//    the edge again because times do not decrease) and the oldest remaining
+//    entry decides the lower bound check.  A ring that would overflow sets
+//    ERR_RING and the host recounts the episode with a larger ring.
+//
+// MapConcatenate (Section 5.2.2), exact form (template flag MC): the thread
+// counting segment p starts at the window start w_p (first event with
+// t >= t[L_p] - W, W = sum of hi) and tabulates, for each entry class
+// (class "none" = no completion since before w_p, or any last-node event r in
+// [w_p, L_p)), the completions inside [L_p, R_p) and the class handed to the
+// next segment.  All classes are tracked by one annotated machine: every
+// admitted entry carries the largest start index of a chain that reaches it,
+// and a class whose machine (re)started at `start` sees exactly the entries
+// whose annotation is >= start.  A completion whose annotation is ms restarts
+// every class with start <= ms at the next event.  The tables are composed by
+// the stitch kernel.
+#pragma once
+
+#include <type_traits>
+
+#include "fem_internal.cuh"
+
+namespace fem {
+
+// Calls f(integral_constant<int, K>), f(...K-1), ..., f(...0): the node loop of
+// Algorithms 1 and 3 runs from the last node down to the first.
+template <int K, typename F>
+__device__ __forceinline__ void for_nodes_desc(F &&f) {
+    if constexpr (K >= 0) {
+        f(std::integral_constant<int, K>{});
+        for_nodes_desc<K - 1>(f);
+    }
+}
+
+template <int N>
+struct EpRegs {
+    static constexpr int NE = N > 1 ? N - 1 : 1;
+    uint32_t E[N];
+    uint32_t lo[NE], hi[NE];
+};
+
+template <int N, int PASS, bool MC, int R>
+__global__ void __launch_bounds__(256) k_count(const CountParams p) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    constexpr int NE = EpRegs<N>::NE;
+    const uint32_t T = blockDim.x, tid = threadIdx.x;
+    const uint32_t SB = stage_bytes(p.offs);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * SB);
+    uint32_t *s_minc = reinterpret_cast<uint32_t *>(smem + 2 * SB + 16);
+    uint8_t *ring_raw = smem + 2 * SB + 128;
+
+    const uint32_t ci = blockIdx.x * T + tid;
+    const uint32_t seg = blockIdx.y;
+
+    // ---------------------------------------------------------------- episode
+    EpRegs<N> ep;
+    bool ok = ci < p.m;
+    if (ok) {
+        const fem_episode rec = p.cands[p.gather ? p.gather[ci] : ci];
+        ok = rec.len == N;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            ep.E[k] = rec.types[k];
+            ok = ok && ep.E[k] < p.K;
+        }
+#pragma unroll
+        for (int k = 0; k < NE; ++k) {
+            ep.lo[k] = 0;
+            ep.hi[k] = 0;
+            if (k < N - 1) {
+                const uint32_t iv = rec.ivl[k];
+                ok = ok && iv < p.n_ivl;
+                const uint2 b = p.ivl[iv < p.n_ivl ? iv : 0];
+                ep.lo[k] = b.x;
+                ep.hi[k] = b.y;
+            }
+        }
+        if (MC) {
+#pragma unroll
+            for (int a = 0; a < N; ++a)
+#pragma unroll
+                for (int b = a + 1; b < N; ++b) ok = ok && ep.E[a] != ep.E[b];
+        }
+        if (!ok) atomicOr(p.err, ERR_BADEP);
+    }
+
+    // ---------------------------------------------------------------- segment and window
+    const uint32_t c_seg0 = seg * p.cps;
+    const uint32_t c_end = min(c_seg0 + p.cps, p.n_chunks);
+    const uint64_t L = (uint64_t)c_seg0 * CHUNK;
+    uint32_t X = 0, Xn = 0, c_w = c_seg0;
+    bool last_seg = c_end >= p.n_chunks;
+    if (MC) {
+        uint64_t W = 0;
+#pragma unroll
+        for (int k = 0; k < N - 1; ++k) W += ep.hi[k];
+        if (ok && seg > 0) {
+            const uint32_t tL = p.cfirst[c_seg0];
+            X = (uint64_t)tL >= W ? (uint32_t)(tL - W) : 0u;
+            uint32_t c = c_seg0;
+            if (X == 0) c = 0;
+            else
+                while (c > 0 && p.cfirst[c] >= X) --c;
+            c_w = c;
+        }
+        if (!last_seg) {
+            const uint32_t tR = p.cfirst[c_end];
+            Xn = (uint64_t)tR >= W ? (uint32_t)(tR - W) : 0u;
+        }
+        if (tid == 0) *s_minc = c_seg0;
+        __syncthreads();
+        if (ok) atomicMin(s_minc, c_w);
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const uint32_t c_first = MC ? *s_minc : c_seg0;
+
+    // ---------------------------------------------------------------- machine state
+    uint32_t cnt = 0;
+    bool overflow = false;
+    uint32_t dl[NE], ms[NE];       // relaxed: deadline, chain start annotation (MC)
+    uint32_t head[NE], tail[NE];   // exact: ring cursors
+#pragma unroll
+    for (int k = 0; k < NE; ++k) dl[k] = ms[k] = head[k] = tail[k] = 0;
+    // MapConcatenate classes
+    uint32_t ns = 1;
+    uint32_t c_key[MC ? S_MAX : 1], c_start[MC ? S_MAX : 1], c_cnt[MC ? S_MAX : 1],
+        c_last[MC ? S_MAX : 1], c_lastt[MC ? S_MAX : 1];
+#pragma unroll
+    for (int j = 0; j < (MC ? S_MAX : 1); ++j) {
+        c_key[j] = CLS_NONE;
+        c_start[j] = 0;
+        c_cnt[j] = 0;
+        c_last[j] = CLS_NONE;
+        c_lastt[j] = 0;
+    }
+
+    uint32_t *ring32 = reinterpret_cast<uint32_t *>(ring_raw) + tid;
+    uint2 *ring64 = reinterpret_cast<uint2 *>(ring_raw) + tid;
+
+    auto complete = [&](uint32_t msv, uint32_t gidx, uint32_t tt) {
+        if constexpr (!MC) {
+            ++cnt;
+        } else {
+#pragma unroll
+            for (int j = 0; j < S_MAX; ++j) {
+                if ((uint32_t)j < ns && c_start[j] <= msv) {
+                    c_start[j] = gidx + 1;
+                    c_last[j] = gidx;
+                    c_lastt[j] = tt;
+                    if ((uint64_t)gidx >= L) ++c_cnt[j];
+                }
+            }
+        }
+    };
+
+    // one node of the machine for an event at node k (k static after unrolling);
+    // returns true when the event completed an occurrence (stop handling it).
+    auto step = [&](auto kc, uint32_t tt, uint32_t gidx) -> bool {
+        constexpr int k = decltype(kc)::value;
+        if constexpr (PASS == FEM_PASS_RELAXED) {
+            if constexpr (k == 0) {
+                if constexpr (N == 1) {
+                    complete(gidx, gidx, tt);
+                    return true;
+                } else {
+                    dl[0] = tt + ep.hi[0] + 1u;
+                    if (MC) ms[0] = gidx;
+                    return false;
+                }
+            } else {
+                if (!(tt < dl[k - 1])) return false;
+                if constexpr (k == N - 1) {
+                    complete(MC ? ms[k - 1] : 0u, gidx, tt);
+                    if (!MC) {
+#pragma unroll
+                        for (int q = 0; q < NE; ++q) dl[q] = 0;
+                    }
+                    return true;
+                } else {
+                    dl[k] = tt + ep.hi[k] + 1u;
+                    if (MC) ms[k] = ms[k - 1];
+                    return false;
+                }
+            }
+        } else {  // exact
+            auto slot32 = [&](int q, uint32_t i) -> uint32_t & {
+                return ring32[((uint32_t)q * R + (i & (R - 1))) * T];
+            };
+            auto slot64 = [&](int q, uint32_t i) -> uint2 & {
+                return ring64[((uint32_t)q * R + (i & (R - 1))) * T];
+            };
+            auto pop_dead = [&](int q) {
+                if (MC) {
+                    while (head[q] != tail[q] && tt - slot64(q, head[q]).x > ep.hi[q]) ++head[q];
+                } else {
+                    while (head[q] != tail[q] && tt - slot32(q, head[q]) > ep.hi[q]) ++head[q];
+                }
+            };
+            auto push = [&](int q, uint32_t msv) {
+                pop_dead(q);
+                if (tail[q] - head[q] == (uint32_t)R) {
+                    overflow = true;
+                    ++head[q];
+                }
+                if (MC) slot64(q, tail[q]) = make_uint2(tt, msv);
+                else slot32(q, tail[q]) = tt;
+                ++tail[q];
+            };
+            if constexpr (k == 0) {
+                if constexpr (N == 1) {
+                    complete(gidx, gidx, tt);
+                    return true;
+                } else {
+                    push(0, gidx);
+                    return false;
+                }
+            } else {
+                pop_dead(k - 1);
+                bool hit = false;
+                uint32_t msv = 0;
+                if (MC) {
+                    for (uint32_t i = head[k - 1]; i != tail[k - 1]; ++i) {
+                        const uint2 e = slot64(k - 1, i);
+                        if (!(tt - e.x > ep.lo[k - 1])) break;
+                        hit = true;
+                        msv = max(msv, e.y);
+                    }
+                } else {
+                    hit = head[k - 1] != tail[k - 1] && tt - slot32(k - 1, head[k - 1]) > ep.lo[k - 1];
+                }
+                if (!hit) return false;
+                if constexpr (k == N - 1) {
+                    complete(msv, gidx, tt);
+                    if (!MC) {
+#pragma unroll
+                        for (int q = 0; q < NE; ++q) head[q] = tail[q];
+                    }
+                    return true;
+                } else {
+                    push(k, msv);
+                    return false;
+                }
+            }
+        }
+    };
+
+    // ---------------------------------------------------------------- chunk pipeline
+    const uint32_t chunk_ev_bytes = CHUNK * 8u;
+    const uint32_t chunk_off_bytes = p.offs * 2u;
+    auto issue = [&](uint32_t c, uint32_t s) {
+        uint8_t *dst = smem + s * SB;
+        mbar_expect_tx(&bar[s], chunk_ev_bytes + chunk_off_bytes);
+        bulk_g2s(dst, p.bev + (uint64_t)c * CHUNK, chunk_ev_bytes, &bar[s]);
+        bulk_g2s(dst + chunk_ev_bytes, p.boff + (uint64_t)c * p.offs, chunk_off_bytes, &bar[s]);
+    };
+    if (tid == 0) {
+        if (c_first < c_end) issue(c_first, 0);
+        if (c_first + 1 < c_end) issue(c_first + 1, 1);
+    }
+
+    bool bail = false;
+    uint32_t c = c_first;
+    for (; c < c_end; ++c) {
+        const uint32_t j = c - c_first, s = j & 1u, par = (j >> 1) & 1u;
+        const bool waited = mbar_wait_bounded(&bar[s], par, p.err);
+        if (!__syncthreads_and(waited)) {
+            bail = true;
+            break;
+        }
+        if (ok && c >= c_w) {
+            const uint2 *ev = reinterpret_cast<const uint2 *>(smem + s * SB);
+            const uint16_t *off = reinterpret_cast<const uint16_t *>(smem + s * SB + chunk_ev_bytes);
+            const uint64_t cbase = (uint64_t)c * CHUNK;
+            uint32_t ptr[N], end[N], key[N], tv[N];
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                ptr[k] = off[ep.E[k]];
+                end[k] = off[ep.E[k] + 1];
+                if (MC && c == c_w && X > 0)
+                    while (ptr[k] < end[k] && ev[ptr[k]].x < X) ++ptr[k];
+                if (ptr[k] < end[k]) {
+                    const uint2 e = ev[ptr[k]];
+                    tv[k] = e.x;
+                    key[k] = e.y;
+                } else {
+                    key[k] = KEY_END;
+                    tv[k] = 0;
+                }
+            }
+            for (;;) {
+                uint32_t mk = key[0];
+#pragma unroll
+                for (int k = 1; k < N; ++k) mk = min(mk, key[k]);
+                if (mk == KEY_END) break;
+                const uint32_t gidx = (uint32_t)(cbase + mk);
+                bool done = false;
+                bool last_node = false;
+                uint32_t tt_last = 0;
+for_nodes_desc<N - 1>([&](auto kc) {
+                    constexpr int k = decltype(kc)::value;
+                    if (key[k] == mk) {
+                        if (!done) done = step(kc, tv[k], gidx);
+                        if constexpr (k == N - 1) {
+                            last_node = true;
+                            tt_last = tv[k];
+                        }
+                        ++ptr[k];
+                        if (ptr[k] < end[k]) {
+                            const uint2 e = ev[ptr[k]];
+                            tv[k] = e.x;
+                            key[k] = e.y;
+                        } else {
+                            key[k] = KEY_END;
+                        }
+                    }
+                });
+                if (MC && last_node && (uint64_t)gidx < L) {
+                    // register entry class r = gidx: a machine that restarts after r
+                    if (ns < (uint32_t)S_MAX) {
+#pragma unroll
+                        for (int q = 0; q < (MC ? S_MAX : 1); ++q) {
+                            if ((uint32_t)q == ns) {
+                                c_key[q] = gidx;
+                                c_start[q] = gidx + 1;
+                                c_cnt[q] = 0;
+                                c_last[q] = gidx;
+                                c_lastt[q] = tt_last;
+                            }
+                        }
+                        ++ns;
+                    } else {
+                        overflow = true;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && c + 2 < c_end) {
+            fence_proxy_async_smem();
+            issue(c + 2, s);
+        }
+    }
+    if (bail) {
+        // drain the copies still in flight before the block's shared memory goes away
+        if (tid == 0) {
+            for (uint32_t cc = c; cc < min(c + 2, c_end); ++cc) {
+                const uint32_t j = cc - c_first;
+                mbar_wait_bounded(&bar[j & 1u], (j >> 1) & 1u, p.err);
+            }
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- results
+    if (ci >= p.m) return;
+    if (overflow) {
+        atomicOr(p.err, ERR_RING);
+        p.redo[ci] = 1;
+    }
+    if (!MC) {
+        p.out[ci] = ok ? cnt : 0u;
+    } else {
+        uint4 *tab = p.tables + ((uint64_t)seg * p.m + ci) * S_MAX;
+#pragma unroll
+        for (int q = 0; q < (MC ? S_MAX : 1); ++q) {
+            uint4 e = make_uint4(CLS_EMPTY, 0, CLS_NONE, 0);
+            if (ok && (uint32_t)q < ns) {
+                uint32_t ex = c_last[q];
+                if (ex != CLS_NONE && !last_seg && c_lastt[q] < Xn) ex = CLS_NONE;
+                e = make_uint4(c_key[q], c_cnt[q], ex, 0);
+            }
+            tab[q] = e;
+        }
+    }
+}
+
+}  // namespace fem

@@ -1,0 +1,181 @@
+// fem_internal.cuh -- internal declarations shared by the libfem.so translation units.
+//
+// Device layout of a resident event stream (built by fem_load_stream):
+//   t[n], type[n]             the stream as given (Def. 2.1), SoA
+//   bev[n_chunks * CHUNK]     per chunk of CHUNK consecutive events, the events
+//                             stably grouped by type: (t, local index in chunk)
+//   boff[n_chunks * offs]     per chunk, the start of each type's group (uint16),
+//                             boff[c*offs + K] = events in the chunk; padded to a
+//                             16-byte multiple so one bulk copy moves a chunk's table
+//   cfirst[n_chunks + 1]      time of the first event of each chunk (+ UINT32_MAX)
+//   hist[K]                   events per type (the level-1 counts)
+// A counting block stages one chunk at a time into shared memory with a bulk
+// (TMA) copy; each thread then walks only the groups of its episode's types.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fem.h"
+
+namespace fem {
+
+constexpr uint32_t CHUNK = 2048;            // events per staged chunk
+constexpr uint32_t KEY_END = 0xFFFFFFFFu;   // "list exhausted"
+constexpr uint32_t CLS_NONE = 0xFFFFFFFFu;  // MapConcatenate class "no recent completion"
+constexpr uint32_t CLS_EMPTY = 0xFFFFFFFEu; // unused transfer-table slot
+constexpr int S_MAX = 8;                    // MapConcatenate entry classes per table
+
+// device error word bits
+constexpr uint32_t ERR_TIMEOUT = 1u;       // a bounded mbarrier wait gave up
+constexpr uint32_t ERR_RING = 2u;          // an exact-pass list outgrew its ring (host retries)
+constexpr uint32_t ERR_BADEP = 4u;         // malformed candidate (type/len/interval index)
+constexpr uint32_t ERR_UNSORTED = 8u;
+constexpr uint32_t ERR_TYPE = 16u;
+constexpr uint32_t ERR_TABLE = 32u;        // transfer table missing a class (internal)
+
+constexpr uint64_t WAIT_NS = 2000000000ull; // bound on any single device wait (2 s)
+
+__host__ __device__ inline uint32_t offs_stride(uint32_t K) { return (K + 1 + 7) & ~7u; }
+__host__ __device__ inline uint32_t stage_bytes(uint32_t offs) {
+    return (CHUNK * 8u + offs * 2u + 127u) & ~127u;
+}
+
+struct StreamDev {
+    uint64_t n = 0;
+    uint32_t K = 0, n_chunks = 0, offs = 0;
+    uint32_t t_max = 0;
+    uint32_t *t = nullptr;
+    uint8_t *type = nullptr;
+    uint2 *bev = nullptr;
+    uint16_t *boff = nullptr;
+    uint32_t *cfirst = nullptr;
+    uint32_t *hist = nullptr;
+};
+
+// Arguments of the counting kernels (one pass over one candidate set).
+struct CountParams {
+    const uint2 *bev;
+    const uint16_t *boff;
+    const uint32_t *cfirst;
+    uint32_t offs, n_chunks;
+    uint64_t n;
+    uint32_t K;
+    const fem_episode *cands;   // candidate records
+    const uint32_t *gather;     // optional: count cands[gather[i]] as candidate i
+    uint32_t m;
+    const uint2 *ivl;           // (lo, hi) table
+    uint32_t n_ivl;
+    uint32_t *out;              // counts [m] (single segment)
+    uint32_t cps;               // chunks per segment
+    uint32_t P;                 // segments
+    uint4 *tables;              // [P][m][S_MAX] (key, count, exit, 0) when P > 1
+    uint8_t *redo;              // [m] set to 1 when a candidate must be recounted
+    uint32_t *err;
+};
+
+// ---------------------------------------------------------------- PTX helpers
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// 1-D bulk copy global -> shared (TMA engine), completion counted on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for phase `parity` of `bar`, giving up after WAIT_NS (sets ERR_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t *err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 0 && global_ns() - t0 > WAIT_NS) {
+            atomicOr(err, ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+#endif
+
+// ---------------------------------------------------------------- launchers (host side)
+// fem_stream.cu
+cudaError_t launch_load_stream(StreamDev &s, cudaStream_t st, uint32_t *d_err);
+// fem_count.cu
+cudaError_t launch_count(int N, int pass, bool mc, uint32_t ring_cap, uint32_t threads,
+                         const CountParams &p, cudaStream_t st);
+size_t count_smem_bytes(int N, int pass, bool mc, uint32_t ring_cap, uint32_t threads,
+                        uint32_t offs);
+bool count_config_supported(int N, int pass, bool mc, uint32_t ring_cap);
+cudaError_t count_set_smem_limits();
+// fem_mine.cu
+cudaError_t launch_stitch(const uint4 *tables, uint32_t m, uint32_t P, uint32_t *out,
+                          uint8_t *redo, uint32_t *err, cudaStream_t st);
+// info[0] |= 1 << len of every candidate; info[1] += candidates with a repeated type
+cudaError_t launch_validate_cands(const fem_episode *c, const uint32_t *gather, uint32_t m,
+                                  uint32_t K, uint32_t n_ivl, uint32_t *info, uint32_t *err,
+                                  cudaStream_t st);
+cudaError_t launch_len_flags(const fem_episode *c, const uint32_t *gather, uint32_t m, uint32_t N,
+                             uint8_t *flags, cudaStream_t st);
+// dst[i] = outer ? outer[inner[i]] : inner[i]
+cudaError_t launch_compose_idx(const uint32_t *outer, const uint32_t *inner, uint32_t m,
+                               uint32_t *dst, cudaStream_t st);
+// stable compaction: keep[i] = (vals[i] >= theta) (or flags[i] != 0 if vals == NULL)
+cudaError_t launch_compact(const uint32_t *vals, const uint8_t *flags, uint32_t theta, uint32_t m,
+                           uint32_t *idx_out, uint32_t *count_out, uint32_t *block_scratch,
+                           cudaStream_t st);
+size_t compact_scratch_words(uint32_t m);
+cudaError_t launch_gather_episodes(const fem_episode *src, const uint32_t *idx, uint32_t m,
+                                   fem_episode *dst, const uint32_t *vals, uint32_t *vals_dst,
+                                   cudaStream_t st);
+cudaError_t launch_scatter_u32(const uint32_t *src, const uint32_t *idx, uint32_t m,
+                               uint32_t *dst, cudaStream_t st);
+cudaError_t launch_fill_flags(const uint32_t *idx, uint32_t m, uint8_t *flags, cudaStream_t st);
+cudaError_t launch_level2(const uint32_t *ftypes, uint32_t f, uint32_t n_ivl, fem_episode *out,
+                          cudaStream_t st);
+cudaError_t launch_join_count(const fem_episode *F, uint32_t f, uint32_t N, uint32_t *cnt,
+                              cudaStream_t st);
+cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t m, uint32_t *out,
+                                  uint32_t *total, uint32_t *scratch, cudaStream_t st);
+cudaError_t launch_join_emit(const fem_episode *F, uint32_t f, uint32_t N, const uint32_t *off,
+                             fem_episode *out, cudaStream_t st);
+cudaError_t launch_type_filter(const uint32_t *hist, uint32_t K, uint32_t theta,
+                               uint32_t *ftypes, uint32_t *fcount, cudaStream_t st);
+
+}  // namespace fem

@@ -1,0 +1,520 @@
+// fem_mine.cu -- the kernels around the counters: MapConcatenate stitch,
+// candidate validation, stable compaction (Algorithm 4's elimination), scans,
+// and level-wise candidate generation.
+#include <string.h>
+
+#include "fem_internal.cuh"
+
+namespace fem {
+
+namespace {
+
+__device__ __forceinline__ fem_episode ld_ep(const fem_episode *p, uint64_t i) {
+    const uint4 v = reinterpret_cast<const uint4 *>(p)[i];
+    fem_episode e;
+    memcpy(&e, &v, sizeof(e));
+    return e;
+}
+__device__ __forceinline__ void st_ep(fem_episode *p, uint64_t i, const fem_episode &e) {
+    uint4 v;
+    memcpy(&v, &e, sizeof(v));
+    reinterpret_cast<uint4 *>(p)[i] = v;
+}
+
+// Block-wide exclusive scan of one value per thread (blockDim.x <= 1024).
+__device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t wtotal;
+    const uint32_t lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= (uint32_t)d) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t nw = (blockDim.x + 31) >> 5;
+        uint32_t s = lane < nw ? wsum[lane] : 0u;
+        uint32_t si = s;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, si, d);
+            if (lane >= (uint32_t)d) si += y;
+        }
+        if (lane < nw) wsum[lane] = si - s;
+        if (lane == nw - 1) wtotal = si;
+    }
+    __syncthreads();
+    const uint32_t res = wsum[w] + inc - v;
+    if (total) *total = wtotal;
+    __syncthreads();
+    return res;
+}
+
+constexpr uint32_t CT = 256;          // threads per compaction block
+constexpr uint32_t CI = 4;            // items per thread
+constexpr uint32_t CB = CT * CI;      // items per block
+
+__device__ __forceinline__ bool keep_at(const uint32_t *vals, const uint8_t *flags, uint32_t theta,
+                                        uint32_t i) {
+    return vals ? vals[i] >= theta : flags[i] != 0;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ MapConcatenate stitch
+// One warp per episode.  Lane l composes the transfer tables of its contiguous
+// run of segments (for every entry class of the run's first segment); the 32
+// partial functions are then composed pairwise in log2(32) shuffle rounds, the
+// tree of Concatenate steps; lane 0 evaluates the result at class "none".
+__global__ void __launch_bounds__(256) k_stitch(const uint4 *__restrict__ tables, uint32_t m,
+                                                uint32_t P, uint32_t *__restrict__ out,
+                                                uint8_t *__restrict__ redo, uint32_t *err) {
+    const uint32_t ci = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t lane = threadIdx.x & 31;
+    if (ci >= m) return;
+    if (redo[ci]) return;  // the host recounts this episode
+    const uint32_t a = (uint32_t)(((uint64_t)P * lane) >> 5);
+    const uint32_t b = (uint32_t)(((uint64_t)P * (lane + 1)) >> 5);
+    uint32_t fk[S_MAX], fc[S_MAX], fe[S_MAX];
+    bool ident = a == b, bad = false;
+#pragma unroll
+    for (int j = 0; j < S_MAX; ++j) fk[j] = CLS_EMPTY, fc[j] = 0, fe[j] = CLS_NONE;
+    if (!ident) {
+        const uint4 *ta = tables + ((uint64_t)a * m + ci) * S_MAX;
+#pragma unroll
+        for (int j = 0; j < S_MAX; ++j) {
+            const uint4 e = ta[j];
+            fk[j] = e.x, fc[j] = e.y, fe[j] = e.z;
+        }
+        for (uint32_t q = a + 1; q < b; ++q) {
+            const uint4 *tq = tables + ((uint64_t)q * m + ci) * S_MAX;
+            uint32_t gk[S_MAX], gc[S_MAX], ge[S_MAX];
+#pragma unroll
+            for (int i = 0; i < S_MAX; ++i) {
+                const uint4 e = tq[i];
+                gk[i] = e.x, gc[i] = e.y, ge[i] = e.z;
+            }
+#pragma unroll
+            for (int j = 0; j < S_MAX; ++j) {
+                if (fk[j] == CLS_EMPTY) continue;
+                bool hit = false;
+                uint32_t nc = 0, ne = CLS_NONE;
+#pragma unroll
+                for (int i = 0; i < S_MAX; ++i)
+                    if (!hit && gk[i] == fe[j]) hit = true, nc = gc[i], ne = ge[i];
+                if (!hit) bad = true;
+                fc[j] += nc;
+                fe[j] = ne;
+            }
+        }
+    }
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t pk[S_MAX], pc[S_MAX], pe[S_MAX];
+#pragma unroll
+        for (int i = 0; i < S_MAX; ++i) {
+            pk[i] = __shfl_down_sync(0xffffffffu, fk[i], d);
+            pc[i] = __shfl_down_sync(0xffffffffu, fc[i], d);
+            pe[i] = __shfl_down_sync(0xffffffffu, fe[i], d);
+        }
+        const bool pident = __shfl_down_sync(0xffffffffu, (int)ident, d) != 0;
+        if ((lane & (2 * d - 1)) == 0 && lane + d < 32 && !pident) {
+            if (ident) {
+#pragma unroll
+                for (int i = 0; i < S_MAX; ++i) fk[i] = pk[i], fc[i] = pc[i], fe[i] = pe[i];
+                ident = false;
+            } else {
+#pragma unroll
+                for (int j = 0; j < S_MAX; ++j) {
+                    if (fk[j] == CLS_EMPTY) continue;
+                    bool hit = false;
+                    uint32_t nc = 0, ne = CLS_NONE;
+#pragma unroll
+                    for (int i = 0; i < S_MAX; ++i)
+                        if (!hit && pk[i] == fe[j]) hit = true, nc = pc[i], ne = pe[i];
+                    if (!hit) bad = true;
+                    fc[j] += nc;
+                    fe[j] = ne;
+                }
+            }
+        }
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+        bool found = false;
+        uint32_t total = 0;
+#pragma unroll
+        for (int j = 0; j < S_MAX; ++j)
+            if (!found && fk[j] == CLS_NONE) found = true, total = fc[j];
+        if (bad || !found) {
+            redo[ci] = 1;
+            atomicOr(err, ERR_TABLE);
+        } else {
+            out[ci] = total;
+        }
+    }
+}
+
+cudaError_t launch_stitch(const uint4 *tables, uint32_t m, uint32_t P, uint32_t *out,
+                          uint8_t *redo, uint32_t *err, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    const uint32_t blocks = (uint32_t)(((uint64_t)m * 32 + 255) / 256);
+    k_stitch<<<blocks, 256, 0, st>>>(tables, m, P, out, redo, err);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ candidate validation
+// info[0] |= 1 << len for every candidate; info[1] += candidates with a repeated type.
+__global__ void k_validate_cands(const fem_episode *__restrict__ c, const uint32_t *gather,
+                                 uint32_t m, uint32_t K, uint32_t n_ivl, uint32_t *info,
+                                 uint32_t *err) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t lenbit = 0, rep = 0, bad = 0;
+    if (i < m) {
+        const fem_episode e = ld_ep(c, gather ? gather[i] : i);
+        const uint32_t N = e.len;
+        if (N < 1 || N > FEM_MAX_LEN) {
+            bad = ERR_BADEP;
+        } else {
+            lenbit = 1u << N;
+            for (uint32_t k = 0; k < N; ++k)
+                if (e.types[k] >= K) bad = ERR_BADEP;
+            for (uint32_t k = 0; k + 1 < N; ++k)
+                if (e.ivl[k] >= n_ivl) bad = ERR_BADEP;
+            for (uint32_t a = 0; a < N; ++a)
+                for (uint32_t b2 = a + 1; b2 < N; ++b2)
+                    if (e.types[a] == e.types[b2]) rep = 1;
+        }
+    }
+    lenbit = __reduce_or_sync(0xffffffffu, lenbit);
+    rep = __reduce_add_sync(0xffffffffu, rep);
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+        if (lenbit) atomicOr(&info[0], lenbit);
+        if (rep) atomicAdd(&info[1], rep);
+        if (bad) atomicOr(err, bad);
+    }
+}
+
+cudaError_t launch_validate_cands(const fem_episode *c, const uint32_t *gather, uint32_t m,
+                                  uint32_t K, uint32_t n_ivl, uint32_t *info, uint32_t *err,
+                                  cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    k_validate_cands<<<(m + 255) / 256, 256, 0, st>>>(c, gather, m, K, n_ivl, info, err);
+    return cudaGetLastError();
+}
+
+__global__ void k_len_flags(const fem_episode *__restrict__ c, const uint32_t *gather,
+                            uint32_t m, uint32_t N, uint8_t *__restrict__ flags) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) flags[i] = ld_ep(c, gather ? gather[i] : i).len == N;
+}
+
+cudaError_t launch_len_flags(const fem_episode *c, const uint32_t *gather, uint32_t m, uint32_t N,
+                             uint8_t *flags, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    k_len_flags<<<(m + 255) / 256, 256, 0, st>>>(c, gather, m, N, flags);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ stable compaction
+size_t compact_scratch_words(uint32_t m) { return (m + CB - 1) / CB + 32; }
+
+__global__ void __launch_bounds__(CT) k_keep_count(const uint32_t *vals, const uint8_t *flags,
+                                                    uint32_t theta, uint32_t m,
+                                                    uint32_t *blocksum) {
+    const uint32_t base = blockIdx.x * CB + threadIdx.x * CI;
+    uint32_t c = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < CI; ++k)
+        if (base + k < m) c += keep_at(vals, flags, theta, base + k);
+    uint32_t tot;
+    block_exclusive_scan(c, &tot);
+    if (threadIdx.x == 0) blocksum[blockIdx.x] = tot;
+}
+
+// In-place exclusive scan of a[0..nb) by one block of 1024 threads; *total = sum.
+__global__ void __launch_bounds__(1024) k_scan_small(uint32_t *a, uint32_t nb, uint32_t *total) {
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < nb; base += 1024) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t v = i < nb ? a[i] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan(v, &tot);
+        if (i < nb) a[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void __launch_bounds__(CT) k_keep_scatter(const uint32_t *vals, const uint8_t *flags,
+                                                      uint32_t theta, uint32_t m,
+                                                      const uint32_t *blockoff, uint32_t *idx) {
+    const uint32_t base = blockIdx.x * CB + threadIdx.x * CI;
+    bool kp[CI];
+    uint32_t c = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < CI; ++k) {
+        kp[k] = base + k < m && keep_at(vals, flags, theta, base + k);
+        c += kp[k];
+    }
+    uint32_t pos = blockoff[blockIdx.x] + block_exclusive_scan(c, nullptr);
+#pragma unroll
+    for (uint32_t k = 0; k < CI; ++k)
+        if (kp[k]) idx[pos++] = base + k;
+}
+
+cudaError_t launch_compact(const uint32_t *vals, const uint8_t *flags, uint32_t theta, uint32_t m,
+                           uint32_t *idx_out, uint32_t *count_out, uint32_t *scratch,
+                           cudaStream_t st) {
+    if (m == 0) return cudaMemsetAsync(count_out, 0, sizeof(uint32_t), st);
+    const uint32_t nb = (m + CB - 1) / CB;
+    k_keep_count<<<nb, CT, 0, st>>>(vals, flags, theta, m, scratch);
+    k_scan_small<<<1, 1024, 0, st>>>(scratch, nb, count_out);
+    k_keep_scatter<<<nb, CT, 0, st>>>(vals, flags, theta, m, scratch, idx_out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ exclusive scan of counts
+__global__ void __launch_bounds__(CT) k_sum_blocks(const uint32_t *in, uint32_t m,
+                                                    uint32_t *blocksum) {
+    const uint32_t base = blockIdx.x * CB + threadIdx.x * CI;
+    uint32_t c = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < CI; ++k)
+        if (base + k < m) c += in[base + k];
+    uint32_t tot;
+    block_exclusive_scan(c, &tot);
+    if (threadIdx.x == 0) blocksum[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(CT) k_scan_apply(const uint32_t *in, uint32_t m,
+                                                    const uint32_t *blockoff, uint32_t *out) {
+    const uint32_t base = blockIdx.x * CB + threadIdx.x * CI;
+    uint32_t v[CI], c = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < CI; ++k) {
+        v[k] = base + k < m ? in[base + k] : 0u;
+        c += v[k];
+    }
+    uint32_t pos = blockoff[blockIdx.x] + block_exclusive_scan(c, nullptr);
+#pragma unroll
+    for (uint32_t k = 0; k < CI; ++k) {
+        if (base + k < m) out[base + k] = pos;
+        pos += v[k];
+    }
+}
+
+cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t m, uint32_t *out, uint32_t *total,
+                                  uint32_t *scratch, cudaStream_t st) {
+    if (m == 0) return cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
+    const uint32_t nb = (m + CB - 1) / CB;
+    k_sum_blocks<<<nb, CT, 0, st>>>(in, m, scratch);
+    k_scan_small<<<1, 1024, 0, st>>>(scratch, nb, total);
+    k_scan_apply<<<nb, CT, 0, st>>>(in, m, scratch, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ gathers and scatters
+__global__ void k_gather_ep(const fem_episode *__restrict__ src, const uint32_t *__restrict__ idx,
+                            uint32_t m, fem_episode *__restrict__ dst,
+                            const uint32_t *__restrict__ vals, uint32_t *__restrict__ vdst) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const uint32_t j = idx[i];
+    if (dst) st_ep(dst, i, ld_ep(src, j));
+    if (vdst) vdst[i] = vals[j];
+}
+
+cudaError_t launch_gather_episodes(const fem_episode *src, const uint32_t *idx, uint32_t m,
+                                   fem_episode *dst, const uint32_t *vals, uint32_t *vals_dst,
+                                   cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    k_gather_ep<<<(m + 255) / 256, 256, 0, st>>>(src, idx, m, dst, vals, vals_dst);
+    return cudaGetLastError();
+}
+
+__global__ void k_scatter_u32(const uint32_t *__restrict__ src, const uint32_t *__restrict__ idx,
+                              uint32_t m, uint32_t *__restrict__ dst) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) dst[idx[i]] = src[i];
+}
+
+cudaError_t launch_scatter_u32(const uint32_t *src, const uint32_t *idx, uint32_t m,
+                               uint32_t *dst, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    k_scatter_u32<<<(m + 255) / 256, 256, 0, st>>>(src, idx, m, dst);
+    return cudaGetLastError();
+}
+
+__global__ void k_fill_flags(const uint32_t *__restrict__ idx, uint32_t m,
+                             uint8_t *__restrict__ flags) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) flags[idx[i]] = 1;
+}
+
+cudaError_t launch_fill_flags(const uint32_t *idx, uint32_t m, uint8_t *flags, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    k_fill_flags<<<(m + 255) / 256, 256, 0, st>>>(idx, m, flags);
+    return cudaGetLastError();
+}
+
+__global__ void k_compose_idx(const uint32_t *__restrict__ outer, const uint32_t *__restrict__ inner,
+                              uint32_t m, uint32_t *__restrict__ dst) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) dst[i] = outer ? outer[inner[i]] : inner[i];
+}
+
+cudaError_t launch_compose_idx(const uint32_t *outer, const uint32_t *inner, uint32_t m,
+                               uint32_t *dst, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    k_compose_idx<<<(m + 255) / 256, 256, 0, st>>>(outer, inner, m, dst);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ level-wise generation
+// Frequent types: hist[a] >= theta, in increasing type order (one block, K <= 256).
+__global__ void k_type_filter(const uint32_t *hist, uint32_t K, uint32_t theta, uint32_t *ftypes,
+                              uint32_t *fcount) {
+    const uint32_t a = threadIdx.x;
+    const uint32_t keep = a < K && hist[a] >= theta;
+    uint32_t tot;
+    const uint32_t pos = block_exclusive_scan(keep, &tot);
+    if (keep) ftypes[pos] = a;
+    if (threadIdx.x == 0) *fcount = tot;
+}
+
+cudaError_t launch_type_filter(const uint32_t *hist, uint32_t K, uint32_t theta, uint32_t *ftypes,
+                               uint32_t *fcount, cudaStream_t st) {
+    k_type_filter<<<1, 256, 0, st>>>(hist, K, theta, ftypes, fcount);
+    return cudaGetLastError();
+}
+
+// Level 2: every ordered pair (a, b) of distinct frequent types, once per interval,
+// in canonical order (a, interval, b).
+__global__ void k_level2(const uint32_t *__restrict__ ftypes, uint32_t f, uint32_t n_ivl,
+                         fem_episode *__restrict__ out) {
+    const uint64_t m = (uint64_t)f * n_ivl * (f - 1);
+    const uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    const uint64_t per_a = (uint64_t)n_ivl * (f - 1);
+    const uint32_t ai = (uint32_t)(c / per_a);
+    const uint32_t r = (uint32_t)(c % per_a);
+    const uint32_t iv = r / (f - 1);
+    const uint32_t bj = r % (f - 1);
+    const uint32_t bi = bj < ai ? bj : bj + 1;
+    fem_episode e;
+    memset(&e, 0, sizeof(e));
+    e.types[0] = (uint8_t)ftypes[ai];
+    e.types[1] = (uint8_t)ftypes[bi];
+    e.ivl[0] = (uint8_t)iv;
+    e.len = 2;
+    st_ep(out, c, e);
+}
+
+cudaError_t launch_level2(const uint32_t *ftypes, uint32_t f, uint32_t n_ivl, fem_episode *out,
+                          cudaStream_t st) {
+    if (f < 2 || n_ivl == 0) return cudaSuccess;
+    const uint64_t m = (uint64_t)f * n_ivl * (f - 1);
+    k_level2<<<(uint32_t)((m + 255) / 256), 256, 0, st>>>(ftypes, f, n_ivl, out);
+    return cudaGetLastError();
+}
+
+namespace {
+// Compare beta's first N-1 nodes (with its first N-2 intervals) against alpha's
+// last N-1 nodes (with its last N-2 intervals), in interleaved order.
+__device__ __forceinline__ int cmp_prefix_suffix(const fem_episode &b, const fem_episode &a,
+                                                 uint32_t N) {
+    for (uint32_t k = 0; k + 1 < N; ++k) {
+        int d = (int)b.types[k] - (int)a.types[k + 1];
+        if (d) return d;
+        if (k + 2 < N) {
+            d = (int)b.ivl[k] - (int)a.ivl[k + 1];
+            if (d) return d;
+        }
+    }
+    return 0;
+}
+// [lo, hi) of the frequent episodes whose prefix equals alpha's suffix.
+__device__ void join_range(const fem_episode *F, uint32_t f, uint32_t N, const fem_episode &a,
+                           uint32_t *lo_out, uint32_t *hi_out) {
+    uint32_t lo = 0, hi = f;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (cmp_prefix_suffix(ld_ep(F, mid), a, N) < 0) lo = mid + 1;
+        else hi = mid;
+    }
+    uint32_t lo2 = lo, hi2 = f;
+    while (lo2 < hi2) {
+        const uint32_t mid = (lo2 + hi2) >> 1;
+        if (cmp_prefix_suffix(ld_ep(F, mid), a, N) <= 0) lo2 = mid + 1;
+        else hi2 = mid;
+    }
+    *lo_out = lo;
+    *hi_out = lo2;
+}
+__device__ __forceinline__ bool has_type(const fem_episode &a, uint32_t N, uint32_t x) {
+    bool h = false;
+    for (uint32_t k = 0; k < N; ++k) h |= a.types[k] == x;
+    return h;
+}
+}  // namespace
+
+// Join (level N -> N+1): alpha joins beta when alpha minus its first node equals
+// beta minus its last node; the child appends beta's last edge and node, whose
+// type must be new to alpha.  F is in canonical order, so the betas of one
+// alpha are contiguous and the children come out in canonical order.
+__global__ void k_join_count(const fem_episode *__restrict__ F, uint32_t f, uint32_t N,
+                             uint32_t *__restrict__ cnt) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= f) return;
+    const fem_episode a = ld_ep(F, i);
+    uint32_t lo, hi;
+    join_range(F, f, N, a, &lo, &hi);
+    uint32_t c = 0;
+    for (uint32_t j = lo; j < hi; ++j) c += !has_type(a, N, ld_ep(F, j).types[N - 1]);
+    cnt[i] = c;
+}
+
+__global__ void k_join_emit(const fem_episode *__restrict__ F, uint32_t f, uint32_t N,
+                            const uint32_t *__restrict__ off, fem_episode *__restrict__ out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= f) return;
+    const fem_episode a = ld_ep(F, i);
+    uint32_t lo, hi;
+    join_range(F, f, N, a, &lo, &hi);
+    uint32_t pos = off[i];
+    for (uint32_t j = lo; j < hi; ++j) {
+        const fem_episode b = ld_ep(F, j);
+        const uint32_t x = b.types[N - 1];
+        if (has_type(a, N, x)) continue;
+        fem_episode c = a;
+        c.types[N] = (uint8_t)x;
+        c.ivl[N - 1] = b.ivl[N - 2];
+        c.len = (uint8_t)(N + 1);
+        st_ep(out, pos++, c);
+    }
+}
+
+cudaError_t launch_join_count(const fem_episode *F, uint32_t f, uint32_t N, uint32_t *cnt,
+                              cudaStream_t st) {
+    if (f == 0) return cudaSuccess;
+    k_join_count<<<(f + 127) / 128, 128, 0, st>>>(F, f, N, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_join_emit(const fem_episode *F, uint32_t f, uint32_t N, const uint32_t *off,
+                             fem_episode *out, cudaStream_t st) {
+    if (f == 0) return cudaSuccess;
+    k_join_emit<<<(f + 127) / 128, 128, 0, st>>>(F, f, N, off, out);
+    return cudaGetLastError();
+}
+
+}  // namespace fem

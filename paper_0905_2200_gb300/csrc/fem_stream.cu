@@ -1,0 +1,121 @@
+// fem_stream.cu -- staging of a resident event stream (load_stream).
+//
+// Validates the stream of Def. 2.1 (times non-decreasing, types < K) and builds
+// the chunked per-type layout every counting kernel reads: for each chunk of
+// CHUNK consecutive events, the events stably grouped by type with their time
+// and local index, plus the group offsets.  Within a group the events keep
+// stream order, so a thread that merges its episode's groups by local index
+// sees exactly the subsequence of the stream made of its episode's types.
+#include "fem_internal.cuh"
+
+namespace fem {
+
+__global__ void k_validate(const uint32_t *__restrict__ t, const uint8_t *__restrict__ ty,
+                           uint64_t n, uint32_t K, uint32_t *err) {
+    uint32_t bad = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        if (ty[i] >= K) bad |= ERR_TYPE;
+        if (i + 1 < n && t[i] > t[i + 1]) bad |= ERR_UNSORTED;
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (bad && (threadIdx.x & 31) == 0) atomicOr(err, bad);
+}
+
+// One block of 256 threads per chunk.  Warp w ranks events [256w, 256w+256) of the
+// chunk within their type (match.any per 32-event round), the per-(warp, type)
+// counts are scanned type-major, and each event is written to its slot.
+__global__ void __launch_bounds__(256) k_bucket(const uint32_t *__restrict__ t,
+                                                const uint8_t *__restrict__ ty, uint64_t n,
+                                                uint32_t K, uint32_t offs, uint32_t n_chunks,
+                                                uint2 *__restrict__ bev,
+                                                uint16_t *__restrict__ boff,
+                                                uint32_t *__restrict__ cfirst,
+                                                uint32_t *__restrict__ hist) {
+    __shared__ uint16_t wcnt[8][256];
+    __shared__ uint32_t tbase[257];
+    __shared__ uint32_t wsum[8];
+    const uint32_t c = blockIdx.x;
+    const uint64_t base = (uint64_t)c * CHUNK;
+    const uint32_t cnt = (uint32_t)min((uint64_t)CHUNK, n - base);
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (uint32_t i = threadIdx.x; i < 8 * 256; i += 256) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+
+    uint32_t myty[8], myrank[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const uint32_t li = w * 256 + r * 32 + lane;
+        const bool valid = li < cnt;
+        const uint32_t v = valid ? ty[base + li] : 0u;
+        const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+        myty[r] = v;
+        myrank[r] = 0;
+        if (valid) {
+            const uint32_t peers = __match_any_sync(vmask, v);
+            const uint32_t below = __popc(peers & ((1u << lane) - 1u));
+            const uint32_t prev = wcnt[w][v];
+            __syncwarp(vmask);
+            if (below == 0) wcnt[w][v] = (uint16_t)(prev + __popc(peers));
+            myrank[r] = prev + below;
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // per type (thread = type value): per-warp exclusive prefix and total
+    const uint32_t tv = threadIdx.x;
+    uint32_t tot = 0;
+#pragma unroll
+    for (int ww = 0; ww < 8; ++ww) {
+        const uint32_t x = wcnt[ww][tv];
+        wcnt[ww][tv] = (uint16_t)tot;
+        tot += x;
+    }
+    // exclusive scan of tot over the 256 type values
+    uint32_t inc = tot;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= (uint32_t)d) inc += y;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    uint32_t woff = 0;
+    for (uint32_t ww = 0; ww < w; ++ww) woff += wsum[ww];
+    tbase[tv] = woff + inc - tot;
+    if (tv == 255) tbase[256] = woff + inc;
+    if (tv < K && tot) atomicAdd(&hist[tv], tot);
+    __syncthreads();
+
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const uint32_t li = w * 256 + r * 32 + lane;
+        if (li < cnt) {
+            const uint32_t pos = tbase[myty[r]] + wcnt[w][myty[r]] + myrank[r];
+            bev[base + pos] = make_uint2(t[base + li], li);
+        }
+    }
+    for (uint32_t k = threadIdx.x; k < offs; k += 256)
+        boff[(uint64_t)c * offs + k] = (uint16_t)(k <= K ? tbase[k] : cnt);
+    if (threadIdx.x == 0) {
+        cfirst[c] = t[base];
+        if (c + 1 == n_chunks) cfirst[n_chunks] = 0xFFFFFFFFu;
+    }
+}
+
+cudaError_t launch_load_stream(StreamDev &s, cudaStream_t st, uint32_t *d_err) {
+    if (s.n == 0) return cudaSuccess;
+    const uint64_t want = (s.n + 255) / 256;
+    const uint32_t vb = (uint32_t)(want < 2432ull ? want : 2432ull);
+    k_validate<<<vb, 256, 0, st>>>(s.t, s.type, s.n, s.K, d_err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * s.K, st);
+    if (e != cudaSuccess) return e;
+    k_bucket<<<s.n_chunks, 256, 0, st>>>(s.t, s.type, s.n, s.K, s.offs, s.n_chunks, s.bev, s.boff,
+                                         s.cfirst, s.hist);
+    return cudaGetLastError();
+}
+
+}  // namespace fem

@@ -1,0 +1,306 @@
+"""ctypes binding of libfem.so (C ABI in include/fem.h), same names as the C calls.
+
+Argument marshalling only: every step of counting and mining runs in the CUDA
+kernels of the library.  Host data is passed as numpy arrays; device data as
+PyTorch CUDA tensors (their ``data_ptr()``), with the current PyTorch stream
+used unless another is given.  If the library has not been built, loading it
+raises :class:`FemError` -- there is no CPU fallback.
+
+Episode records are uint8 arrays of shape [m, 16] laid out like ``fem_episode``:
+bytes 0..7 node types, 8..14 interval indices, 15 the length.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+MAX_LEN = 8
+PASS_RELAXED, PASS_EXACT = 0, 1
+STATUS = {0: "FEM_OK", -1: "FEM_EINVAL", -2: "FEM_EUNSORTED", -3: "FEM_ETYPE",
+          -4: "FEM_ERANGE", -5: "FEM_ENOMEM", -6: "FEM_EADMIT", -7: "FEM_ETIMEOUT",
+          -8: "FEM_ECUDA", -9: "FEM_EOVERFLOW", -10: "FEM_ENOSTREAM"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfem.so")
+
+
+class FemError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        name = STATUS.get(status, str(status))
+        super().__init__(f"{what}: {name}" if what else name)
+
+
+class fem_interval(ctypes.Structure):
+    _fields_ = [("lo_us", ctypes.c_uint32), ("hi_us", ctypes.c_uint32)]
+
+
+class fem_config(ctypes.Structure):
+    _fields_ = [("segments", ctypes.c_uint32), ("threads_per_block", ctypes.c_uint32),
+                ("ring_capacity", ctypes.c_uint32)]
+
+
+class fem_level_stats(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_uint32), ("candidates", ctypes.c_uint32),
+                ("survivors", ctypes.c_uint32), ("frequent", ctypes.c_uint32),
+                ("segments", ctypes.c_uint32), ("ms_generate", ctypes.c_float),
+                ("ms_relaxed", ctypes.c_float), ("ms_compact", ctypes.c_float),
+                ("ms_exact", ctypes.c_float)]
+
+
+EXPORTS = ["fem_create", "fem_destroy", "fem_set_config", "fem_load_stream", "fem_free_stream",
+           "fem_type_counts", "fem_count_candidates", "fem_count_two_pass",
+           "fem_mine_levelwise", "fem_result_level", "fem_result_max_level", "fem_result_free",
+           "fem_last_mine_stats", "fem_strerror"]
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libfem.so (built by ``paper_0905_2200_gb300.build``); raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise FemError(-8, f"libfem.so not built at {path}; run paper_0905_2200_gb300.build")
+    lib = ctypes.CDLL(path)
+    vp, u32, i32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64
+    I = ctypes.c_int
+    sig = {
+        "fem_create": (I, [ctypes.POINTER(vp), I]),
+        "fem_destroy": (I, [vp]),
+        "fem_set_config": (I, [vp, ctypes.POINTER(fem_config)]),
+        "fem_load_stream": (I, [vp, vp, vp, u64, u32, I, vp, ctypes.POINTER(i32)]),
+        "fem_free_stream": (I, [vp, i32]),
+        "fem_type_counts": (I, [vp, i32, vp]),
+        "fem_count_candidates": (I, [vp, i32, vp, u32, I, ctypes.POINTER(fem_interval), u32, I,
+                                     vp, I, vp]),
+        "fem_count_two_pass": (I, [vp, i32, vp, u32, I, ctypes.POINTER(fem_interval), u32, u32,
+                                   vp, vp, I, vp]),
+        "fem_mine_levelwise": (I, [vp, i32, ctypes.POINTER(fem_interval), u32, u32, u32, vp,
+                                   ctypes.POINTER(vp)]),
+        "fem_result_level": (I, [vp, u32, ctypes.POINTER(u32), ctypes.POINTER(vp),
+                                 ctypes.POINTER(vp)]),
+        "fem_result_max_level": (u32, [vp]),
+        "fem_result_free": (None, [vp]),
+        "fem_last_mine_stats": (I, [vp, ctypes.POINTER(fem_level_stats), u32]),
+        "fem_strerror": (ctypes.c_char_p, [I]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise FemError(rc, what)
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, on_device) of a numpy array or torch tensor."""
+    if x is None:
+        return None, 0
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), int(x.is_cuda)
+    if not (x.flags["C_CONTIGUOUS"]):
+        raise ValueError("array must be C-contiguous")
+    return x.ctypes.data_as(ctypes.c_void_p), 0
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _intervals(intervals):
+    iv = np.asarray(intervals, dtype=np.uint32).reshape(-1, 2)
+    arr = (fem_interval * max(len(iv), 1))()
+    for i, (lo, hi) in enumerate(iv):
+        arr[i].lo_us, arr[i].hi_us = int(lo), int(hi)
+    return arr, len(iv)
+
+
+def pack_episodes(lens, types, ivl) -> np.ndarray:
+    """[m, 16] uint8 episode records from len[m], types[m, 8], ivl[m, 7]."""
+    lens = np.asarray(lens, dtype=np.uint8)
+    m = lens.shape[0]
+    rec = np.zeros((m, 16), np.uint8)
+    rec[:, :8] = np.asarray(types, dtype=np.uint8).reshape(m, 8)
+    rec[:, 8:15] = np.asarray(ivl, dtype=np.uint8).reshape(m, 7)
+    rec[:, 15] = lens
+    return rec
+
+
+def unpack_episodes(rec):
+    rec = np.asarray(rec, dtype=np.uint8).reshape(-1, 16)
+    return rec[:, 15].copy(), rec[:, :8].copy(), rec[:, 8:15].copy()
+
+
+# --------------------------------------------------------------------------- calls
+def fem_create(device: int = 0):
+    lib = load()
+    h = ctypes.c_void_p()
+    _check(lib.fem_create(ctypes.byref(h), int(device)), "fem_create")
+    return h
+
+
+def fem_destroy(ctx):
+    _check(load().fem_destroy(ctx), "fem_destroy")
+
+
+def fem_set_config(ctx, segments=0, threads_per_block=0, ring_capacity=0, reset=False):
+    lib = load()
+    if reset:
+        _check(lib.fem_set_config(ctx, None), "fem_set_config")
+        return
+    cfg = fem_config(int(segments), int(threads_per_block), int(ring_capacity))
+    _check(lib.fem_set_config(ctx, ctypes.byref(cfg)), "fem_set_config")
+
+
+def fem_load_stream(ctx, types, t_us, n_types, stream=None) -> int:
+    """Load an event stream (numpy host arrays or CUDA tensors); returns its id."""
+    lib = load()
+    pt, dt = _ptr(types)
+    pu, du = _ptr(t_us)
+    if dt != du:
+        raise ValueError("types and t_us must both be host or both be device")
+    n = int(types.shape[0]) if types is not None else 0
+    if (int(t_us.shape[0]) if t_us is not None else 0) != n:
+        raise ValueError("types and t_us differ in length")
+    sid = ctypes.c_int32()
+    _check(lib.fem_load_stream(ctx, pt, pu, n, int(n_types), dt, _stream_handle(stream),
+                               ctypes.byref(sid)), "fem_load_stream")
+    return sid.value
+
+
+def fem_free_stream(ctx, sid):
+    _check(load().fem_free_stream(ctx, int(sid)), "fem_free_stream")
+
+
+def fem_type_counts(ctx, sid, n_types) -> np.ndarray:
+    out = np.zeros(n_types, np.uint32)
+    _check(load().fem_type_counts(ctx, int(sid), out.ctypes.data_as(ctypes.c_void_p)),
+           "fem_type_counts")
+    return out
+
+
+def fem_count_candidates(ctx, sid, cands, intervals, pass_=PASS_EXACT, out=None, stream=None):
+    """Count episode records `cands` ([m,16] numpy or CUDA uint8 tensor).
+
+    Returns `out` (a uint32 numpy array, or the given device tensor)."""
+    lib = load()
+    m = int(cands.shape[0])
+    pc, dc = _ptr(cands)
+    if out is None:
+        out = np.zeros(m, np.uint32)
+    po, do = _ptr(out)
+    iv, nI = _intervals(intervals)
+    _check(lib.fem_count_candidates(ctx, int(sid), pc, m, dc, iv, nI, int(pass_), po, do,
+                                    _stream_handle(stream)), "fem_count_candidates")
+    return out
+
+
+def fem_count_two_pass(ctx, sid, cands, intervals, theta, exact_out=None, survived_out=None,
+                       stream=None):
+    """Algorithm 4; returns (exact-or-zero uint32[m], survived uint8[m])."""
+    lib = load()
+    m = int(cands.shape[0])
+    pc, dc = _ptr(cands)
+    if exact_out is None:
+        exact_out = np.zeros(m, np.uint32)
+    if survived_out is None:
+        survived_out = np.zeros(m, np.uint8)
+    pe, de = _ptr(exact_out)
+    ps, ds = _ptr(survived_out)
+    if de != ds:
+        raise ValueError("outputs must both be host or both be device")
+    iv, nI = _intervals(intervals)
+    _check(lib.fem_count_two_pass(ctx, int(sid), pc, m, dc, iv, nI, int(theta), pe, ps, de,
+                                  _stream_handle(stream)), "fem_count_two_pass")
+    return exact_out, survived_out
+
+
+def fem_mine_levelwise(ctx, sid, intervals, theta, max_len, stream=None, raw=False):
+    """Problem 1: {level: [(types tuple, interval tuple, count), ...]} in canonical order.
+
+    raw=True returns {level: (records uint8[f,16], counts uint32[f])} instead."""
+    lib = load()
+    iv, nI = _intervals(intervals)
+    res = ctypes.c_void_p()
+    _check(lib.fem_mine_levelwise(ctx, int(sid), iv, nI, int(theta), int(max_len),
+                                  _stream_handle(stream), ctypes.byref(res)),
+           "fem_mine_levelwise")
+    try:
+        out = {}
+        for level in range(1, int(max_len) + 1):
+            m = ctypes.c_uint32()
+            pe, pcn = ctypes.c_void_p(), ctypes.c_void_p()
+            _check(lib.fem_result_level(res, level, ctypes.byref(m), ctypes.byref(pe),
+                                        ctypes.byref(pcn)), "fem_result_level")
+            f = m.value
+            if f == 0:
+                continue
+            rec = np.ctypeslib.as_array(ctypes.cast(pe, ctypes.POINTER(ctypes.c_uint8)),
+                                        shape=(f, 16)).copy()
+            cnt = np.ctypeslib.as_array(ctypes.cast(pcn, ctypes.POINTER(ctypes.c_uint32)),
+                                        shape=(f,)).copy()
+            if raw:
+                out[level] = (rec, cnt)
+            else:
+                out[level] = [(tuple(int(x) for x in rec[i, : rec[i, 15]]),
+                               tuple(int(x) for x in rec[i, 8: 8 + rec[i, 15] - 1]),
+                               int(cnt[i])) for i in range(f)]
+        return out
+    finally:
+        lib.fem_result_free(res)
+
+
+def fem_last_mine_stats(ctx):
+    arr = (fem_level_stats * 16)()
+    k = load().fem_last_mine_stats(ctx, arr, 16)
+    if k < 0:
+        raise FemError(k, "fem_last_mine_stats")
+    return [{f: getattr(arr[i], f) for f, _ in fem_level_stats._fields_} for i in range(k)]
+
+
+def fem_strerror(status: int) -> str:
+    return load().fem_strerror(int(status)).decode()
+
+
+class Context:
+    """Small convenience owner of a context (destroyed on close/exit)."""
+
+    def __init__(self, device=0):
+        self.h = fem_create(device)
+
+    def close(self):
+        if self.h:
+            fem_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,113 @@
+"""Parity of the on-device level-wise miner (candidate generation, two-pass counting,
+compaction, join) with the oracle's miner, and sampled full-size checks."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0905_2200_gb300 import fem, synth
+from tests.gpu_common import I_MS4, assert_counts_equal, ctx_fixture, mid_stream
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = ctx_fixture()
+    yield c
+    fem.fem_destroy(c)
+
+
+@pytest.fixture(autouse=True)
+def _reset_config(ctx):
+    fem.fem_set_config(ctx, reset=True)
+    yield
+    fem.fem_set_config(ctx, reset=True)
+
+
+def test_mine_tiny_equals_oracle(ctx):
+    cfg = synth.tiny_mining()
+    s = cfg["stream"]
+    sid = fem.fem_load_stream(ctx, s.types, s.t, s.n_types)
+    got = fem.fem_mine_levelwise(ctx, sid, cfg["intervals"], cfg["theta"], cfg["max_len"])
+    want = oracle.mine(s.types, s.t, s.n_types, cfg["intervals"], cfg["theta"], cfg["max_len"])
+    assert got == want
+    assert any(r[0] == (0, 1, 2, 3) for r in got[4])
+    stats = fem.fem_last_mine_stats(ctx)
+    assert stats[0]["level"] == 2 and stats[0]["candidates"] == 16 * 15
+
+
+@pytest.mark.parametrize("theta,segments", [(40, 0), (25, 0), (25, 1), (25, 5)])
+def test_mine_mid_equals_oracle(ctx, theta, segments):
+    ty, t, K, chains = mid_stream()
+    sid = fem.fem_load_stream(ctx, ty, t, K)
+    if segments:
+        fem.fem_set_config(ctx, segments=segments)
+    got = fem.fem_mine_levelwise(ctx, sid, I_MS4, theta, 6)
+    want = oracle.mine(ty, t, K, I_MS4, theta, 6)
+    assert got == want
+    assert max(got) >= 3
+    fem.fem_free_stream(ctx, sid)
+
+
+def test_mine_edge_cases(ctx):
+    I = np.array([[0, 1000]], np.uint32)
+    # empty stream, a stream where nothing is frequent, max_len 1
+    for n, theta, max_len in ((0, 1, 4), (50, 10**6, 4), (500, 5, 1), (500, 3, 2)):
+        ty, t = synth.tiny_stream(n, n, 3, 300)
+        sid = fem.fem_load_stream(ctx, ty, t, 3)
+        got = fem.fem_mine_levelwise(ctx, sid, I, theta, max_len)
+        want = oracle.mine(ty, t, 3, I, theta, max_len)
+        assert got == {k: v for k, v in want.items() if v}
+        fem.fem_free_stream(ctx, sid)
+
+
+@pytest.fixture(scope="module")
+def single_recording(ctx):
+    cfg = synth.single_recording()
+    s = cfg["stream"]
+    sid = fem.fem_load_stream(ctx, s.types, s.t, s.n_types)
+    return cfg, s, sid
+
+
+def test_single_recording_level2_sampled(ctx, single_recording):
+    """Full-size 64-type, 300 s recording: all 16,128 level-2 candidates counted in
+    the bench's launch configuration; 256 sampled candidates checked one by one
+    against the oracle, Theorem 5.1 checked on all."""
+    cfg, s, sid = single_recording
+    L, E, iv = synth.level2_candidates(range(64), 4)
+    rec = fem.pack_episodes(L, E, iv)
+    rel = fem.fem_count_candidates(ctx, sid, rec, cfg["intervals"], fem.PASS_RELAXED)
+    ex = fem.fem_count_candidates(ctx, sid, rec, cfg["intervals"], fem.PASS_EXACT)
+    assert np.all(rel >= ex)
+    rng = np.random.default_rng(0)
+    pick = np.sort(rng.choice(len(L), 256, replace=False))
+    for p, got in ((oracle.RELAXED, rel), (oracle.EXACT, ex)):
+        want = oracle.count_batch(s.types, s.t, L[pick], E[pick], iv[pick], cfg["intervals"], p)
+        assert_counts_equal(got[pick], want, f"sampled pass {p}")
+
+
+def test_single_recording_mining_sampled(ctx, single_recording):
+    """Full-size mining at the workload threshold: every reported episode's count is
+    re-derived by the oracle, every reported episode meets theta, and sampled level-2
+    candidates missing from the result are below theta per the oracle."""
+    cfg, s, sid = single_recording
+    theta = cfg["theta"]
+    got = fem.fem_mine_levelwise(ctx, sid, cfg["intervals"], theta, cfg["max_len"])
+    for level, rows in got.items():
+        if level == 1:
+            continue
+        keys = [oracle.canonical_key(r[0], r[1]) for r in rows]
+        assert keys == sorted(keys)
+        lens, E, iv = oracle._pack([(r[0], r[1]) for r in rows])
+        want = oracle.count_batch(s.types, s.t, lens, E, iv, cfg["intervals"], oracle.EXACT)
+        assert_counts_equal([r[2] for r in rows], want, f"level {level}")
+        assert all(r[2] >= theta for r in rows)
+    found2 = {(r[0], r[1]) for r in got.get(2, [])}
+    L, E, iv = synth.level2_candidates(range(64), 4)
+    rng = np.random.default_rng(1)
+    pick = [i for i in rng.choice(len(L), 400, replace=False)
+            if (tuple(E[i, :2]), (int(iv[i, 0]),)) not in found2][:200]
+    pick = np.array(sorted(pick))
+    want = oracle.count_batch(s.types, s.t, L[pick], E[pick], iv[pick], cfg["intervals"],
+                              oracle.EXACT)
+    assert np.all(want < theta)
