@@ -143,7 +143,10 @@ uint32_t choose_threads(fem_ctx *c, int N, int pass, bool mc, uint32_t R, uint32
     for (uint32_t T : {128u, 64u, 32u}) {
         if (count_smem_bytes(N, pass, mc, R, T, offs) <= 80 * 1024) return T;
     }
-    return 32;
+    for (uint32_t T : {32u, 16u, 8u}) {
+        if (count_smem_bytes(N, pass, mc, R, T, offs) <= 220 * 1024) return T;
+    }
+    return 8;
 }
 
 struct PassInfo {
@@ -177,7 +180,7 @@ int count_pass(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const u
 
     uint32_t P = choose_segments(c, s, m, distinct);
     uint32_t R = 1;
-    if (pass == FEM_PASS_EXACT) R = c->cfg.ring_capacity ? c->cfg.ring_capacity : 16;
+    if (pass == FEM_PASS_EXACT) R = c->cfg.ring_capacity ? c->cfg.ring_capacity : (P > 1 ? 16 : 8);
     if (P > 1 && pass == FEM_PASS_EXACT && R > 32) R = 32;
     if (!count_config_supported(N, pass, P > 1, R)) return FEM_EINVAL;
     const uint32_t cps = P > 1 ? (s.n_chunks + P - 1) / P : std::max<uint32_t>(s.n_chunks, 1);
@@ -210,7 +213,7 @@ int count_pass(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const u
     CK(launch_compose_idx(gather, ridx, r, rg, st));
     const uint32_t caps[] = {16, 32, 128};
     for (uint32_t R2 : caps) {
-        if (pass == FEM_PASS_EXACT && R2 < R) continue;
+        if (pass == FEM_PASS_EXACT && R2 <= R && R2 != 128) continue;
         if (pass == FEM_PASS_RELAXED && R2 != 16) continue;
         CK(cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), st));
         CountParams q = p;

@@ -10,7 +10,7 @@ size_t count_smem_bytes(int N, int pass, bool mc, uint32_t ring_cap, uint32_t th
                         uint32_t offs) {
     size_t b = 2 * (size_t)stage_bytes(offs) + 128;
     if (pass == FEM_PASS_EXACT && N > 1)
-        b += (size_t)(N - 1) * ring_cap * threads * (mc ? 8u : 4u);
+        b += (size_t)(N - 1) * ring_cap * threads * 8u;
     return b;
 }
 

@@ -11,11 +11,18 @@
 // Machines (node k = 0..N-1, edge k joins node k and k+1 with interval (lo, hi]):
 //  * relaxed (Algorithm 3, Section 5.3.1): one slot per node holding the
 //    deadline s + hi + 1 of the latest admitted time s (0 = unset);
-//  * exact (Algorithm 1, Section 5.1): per node a FIFO ring of admitted times in
-//    shared memory; entries older than hi are dropped (they can never satisfy
-//    the edge again because times do not decrease) and the oldest remaining
-//    entry decides the lower bound check.  A ring that would overflow sets
-//    ERR_RING and the host recounts the episode with a larger ring.
+//  * exact (Algorithm 1, Section 5.1): per node a FIFO ring in shared memory
+//    holding the list s[k] of admitted times as clusters [first, last]: a new
+//    time joins the newest cluster when it is within hi - lo of that cluster's
+//    last time.  A cluster matches exactly the event times in
+//    (first + lo, last + hi] (consecutive members are at most hi - lo apart, so
+//    the union of their (s + lo, s + hi] ranges has no hole), which is the
+//    list's own check "some t' in s[k] with lo < t - t' <= hi".  Clusters whose
+//    last time is older than hi can never match again (times do not decrease)
+//    and are dropped, so at most ceil(hi / (hi - lo)) clusters are live.  A ring
+//    that would overflow sets ERR_RING and the host recounts the episode with a
+//    larger ring.  The segmented variant keeps single times (with equal times
+//    merged), because it needs the annotation of the newest matching entry.
 //
 // MapConcatenate (Section 5.2.2), exact form (template flag MC): the thread
 // counting segment p starts at the window start w_p (first event with
@@ -153,7 +160,6 @@ __global__ void __launch_bounds__(256) k_count(const CountParams p) {
         c_lastt[j] = 0;
     }
 
-    uint32_t *ring32 = reinterpret_cast<uint32_t *>(ring_raw) + tid;
     uint2 *ring64 = reinterpret_cast<uint2 *>(ring_raw) + tid;
 
     auto complete = [&](uint32_t msv, uint32_t gidx, uint32_t tt) {
@@ -202,27 +208,36 @@ __global__ void __launch_bounds__(256) k_count(const CountParams p) {
                 }
             }
         } else {  // exact
-            auto slot32 = [&](int q, uint32_t i) -> uint32_t & {
-                return ring32[((uint32_t)q * R + (i & (R - 1))) * T];
-            };
-            auto slot64 = [&](int q, uint32_t i) -> uint2 & {
+            // ring q entry i: single-segment (first, last) cluster, segmented (t, annotation)
+            auto slot = [&](int q, uint32_t i) -> uint2 & {
                 return ring64[((uint32_t)q * R + (i & (R - 1))) * T];
             };
             auto pop_dead = [&](int q) {
                 if (MC) {
-                    while (head[q] != tail[q] && tt - slot64(q, head[q]).x > ep.hi[q]) ++head[q];
+                    while (head[q] != tail[q] && tt - slot(q, head[q]).x > ep.hi[q]) ++head[q];
                 } else {
-                    while (head[q] != tail[q] && tt - slot32(q, head[q]) > ep.hi[q]) ++head[q];
+                    while (head[q] != tail[q] && tt - slot(q, head[q]).y > ep.hi[q]) ++head[q];
                 }
             };
             auto push = [&](int q, uint32_t msv) {
                 pop_dead(q);
+                if (head[q] != tail[q]) {
+                    uint2 &b = slot(q, tail[q] - 1u);
+                    if (MC) {
+                        if (b.x == tt) {  // equal times are one entry; annotations only grow
+                            b.y = max(b.y, msv);
+                            return;
+                        }
+                    } else if (tt - b.y <= ep.hi[q] - ep.lo[q]) {
+                        b.y = tt;
+                        return;
+                    }
+                }
                 if (tail[q] - head[q] == (uint32_t)R) {
                     overflow = true;
                     ++head[q];
                 }
-                if (MC) slot64(q, tail[q]) = make_uint2(tt, msv);
-                else slot32(q, tail[q]) = tt;
+                slot(q, tail[q]) = make_uint2(tt, MC ? msv : tt);
                 ++tail[q];
             };
             if constexpr (k == 0) {
@@ -239,13 +254,13 @@ __global__ void __launch_bounds__(256) k_count(const CountParams p) {
                 uint32_t msv = 0;
                 if (MC) {
                     for (uint32_t i = head[k - 1]; i != tail[k - 1]; ++i) {
-                        const uint2 e = slot64(k - 1, i);
+                        const uint2 e = slot(k - 1, i);
                         if (!(tt - e.x > ep.lo[k - 1])) break;
                         hit = true;
                         msv = max(msv, e.y);
                     }
                 } else {
-                    hit = head[k - 1] != tail[k - 1] && tt - slot32(k - 1, head[k - 1]) > ep.lo[k - 1];
+                    hit = head[k - 1] != tail[k - 1] && tt - slot(k - 1, head[k - 1]).x > ep.lo[k - 1];
                 }
                 if (!hit) return false;
                 if constexpr (k == N - 1) {

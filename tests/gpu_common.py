@@ -27,6 +27,20 @@ def mid_stream(seed=0xFE10, K=32, rate=20.0, T=60.0):
     return ty, t, K, chains
 
 
+def mining_stream(seed=0xFE11, K=24, rate=10.0, T=60.0):
+    """~19k events (10 chunks) with three strong chains (4-6 Hz, lengths 4-6), so that
+    level-wise mining reaches length 6 while chance pairs stay below the thresholds
+    the tests use."""
+    rng = np.random.default_rng(seed)
+    chains = []
+    for L in (4, 5, 6):
+        tys = tuple(int(x) for x in rng.choice(K, L, replace=False))
+        ivs = tuple(int(x) for x in rng.integers(0, 4, L - 1))
+        chains.append((tys, float(rng.uniform(4, 6)), [tuple(I_MS4[i]) for i in ivs]))
+    t, ty = synth.poisson_stream(seed, K, rate, T, chains=chains)
+    return ty, t, K, chains
+
+
 def oracle_counts(ty, t, L, E, iv, I, pass_):
     return oracle.count_batch(ty, t, L, E, iv, I,
                               oracle.RELAXED if pass_ == fem.PASS_RELAXED else oracle.EXACT)

@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_0905_2200_gb300 import fem, synth
-from tests.gpu_common import I_MS4, assert_counts_equal, ctx_fixture, mid_stream
+from tests.gpu_common import I_MS4, assert_counts_equal, ctx_fixture, mining_stream
 
 pytestmark = pytest.mark.gpu
 
@@ -36,16 +36,16 @@ def test_mine_tiny_equals_oracle(ctx):
     assert stats[0]["level"] == 2 and stats[0]["candidates"] == 16 * 15
 
 
-@pytest.mark.parametrize("theta,segments", [(40, 0), (25, 0), (25, 1), (25, 5)])
-def test_mine_mid_equals_oracle(ctx, theta, segments):
-    ty, t, K, chains = mid_stream()
+@pytest.mark.parametrize("theta,segments", [(150, 0), (80, 0), (80, 1), (80, 3), (150, 10)])
+def test_mine_chains_equals_oracle(ctx, theta, segments):
+    ty, t, K, chains = mining_stream()
     sid = fem.fem_load_stream(ctx, ty, t, K)
     if segments:
         fem.fem_set_config(ctx, segments=segments)
     got = fem.fem_mine_levelwise(ctx, sid, I_MS4, theta, 6)
     want = oracle.mine(ty, t, K, I_MS4, theta, 6)
     assert got == want
-    assert max(got) >= 3
+    assert max(got) == 6
     fem.fem_free_stream(ctx, sid)
 
 
