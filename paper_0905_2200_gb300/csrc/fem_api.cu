@@ -4,6 +4,7 @@
 // kernels of fem_stream.cu, fem_count.cu and fem_mine.cu; this file only
 // allocates device memory, launches, and copies results.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <new>
@@ -13,6 +14,11 @@
 #include "fem_internal.cuh"
 
 using namespace fem;
+
+namespace fem {
+static std::atomic<uint64_t> g_launches{0};
+void note_launch(uint32_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace fem
 
 struct fem_result {
     std::vector<std::vector<fem_episode>> eps;    // [level-1]
@@ -38,7 +44,9 @@ struct fem_ctx {
     uint32_t *h_small = nullptr;  // 64 pinned host words
     std::map<std::string, DevBuf> bufs;
     std::vector<fem_level_stats> stats;
+    std::vector<StreamDev> pool;  // buffers of freed streams, reused by later loads
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaEvent_t kev[3] = {nullptr, nullptr, nullptr};  // around the counting kernel and stitch
 };
 
 namespace {
@@ -151,6 +159,7 @@ uint32_t choose_threads(fem_ctx *c, int N, int pass, bool mc, uint32_t R, uint32
 
 struct PassInfo {
     uint32_t segments = 1;
+    float ms_kernel = 0, ms_stitch = 0;
 };
 
 // One counting pass over m candidates (all of length N) -> out[0..m).
@@ -191,12 +200,19 @@ int count_pass(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const u
         RET(dbuf(c, "tables", (size_t)P * m * S_MAX, &p.tables));
     }
     const uint32_t T = choose_threads(c, N, pass, P > 1, R, s.offs);
+    CK(cudaEventRecord(c->kev[0], st));
     CK(launch_count(N, pass, P > 1, R, T, p, st));
+    CK(cudaEventRecord(c->kev[1], st));
     if (P > 1) CK(launch_stitch(p.tables, m, P, out, redo, c->d_err, st));
-    if (info) info->segments = P;
+    CK(cudaEventRecord(c->kev[2], st));
 
     uint32_t e;
     RET(read_err(c, st, &e));
+    if (info) {
+        info->segments = P;
+        cudaEventElapsedTime(&info->ms_kernel, c->kev[0], c->kev[1]);
+        cudaEventElapsedTime(&info->ms_stitch, c->kev[1], c->kev[2]);
+    }
     RET(err_status(e));
     if (!(e & (ERR_RING | ERR_TABLE))) return FEM_OK;
 
@@ -278,10 +294,22 @@ int count_any(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const ui
     return FEM_OK;
 }
 
+void free_stream_buffers(StreamDev &s) {
+    cudaFree(s.t);
+    cudaFree(s.type);
+    cudaFree(s.bev);
+    cudaFree(s.boff);
+    cudaFree(s.cfirst);
+    cudaFree(s.hist);
+    s = StreamDev{};
+}
+
 }  // namespace
 
 // ============================================================================ C ABI
 extern "C" {
+
+uint64_t fem_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 const char *fem_strerror(int s) {
     switch (s) {
@@ -318,7 +346,9 @@ int fem_create(fem_ctx **out, int device) {
         cudaMalloc(&c->d_err, sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&c->d_small, 64 * sizeof(uint32_t)) != cudaSuccess ||
         cudaMallocHost(&c->h_small, 64 * sizeof(uint32_t)) != cudaSuccess ||
-        cudaEventCreate(&c->ev[0]) != cudaSuccess || cudaEventCreate(&c->ev[1]) != cudaSuccess) {
+        cudaEventCreate(&c->ev[0]) != cudaSuccess || cudaEventCreate(&c->ev[1]) != cudaSuccess ||
+        cudaEventCreate(&c->kev[0]) != cudaSuccess || cudaEventCreate(&c->kev[1]) != cudaSuccess ||
+        cudaEventCreate(&c->kev[2]) != cudaSuccess) {
         cudaGetLastError();
         fem_destroy(c);
         return FEM_ECUDA;
@@ -332,21 +362,16 @@ int fem_destroy(fem_ctx *c) {
     if (!c) return FEM_EINVAL;
     cudaSetDevice(c->device);
     if (c->own) cudaStreamSynchronize(c->own);
-    for (auto &kv : c->streams) {
-        StreamDev &s = kv.second;
-        cudaFree(s.t);
-        cudaFree(s.type);
-        cudaFree(s.bev);
-        cudaFree(s.boff);
-        cudaFree(s.cfirst);
-        cudaFree(s.hist);
-    }
+    for (auto &kv : c->streams) free_stream_buffers(kv.second);
     for (auto &kv : c->bufs) cudaFree(kv.second.p);
     if (c->d_err) cudaFree(c->d_err);
     if (c->d_small) cudaFree(c->d_small);
     if (c->h_small) cudaFreeHost(c->h_small);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
+    for (auto &e : c->kev)
+        if (e) cudaEventDestroy(e);
+    for (StreamDev &s : c->pool) free_stream_buffers(s);
     if (c->own) cudaStreamDestroy(c->own);
     delete c;
     return FEM_OK;
@@ -381,19 +406,27 @@ int fem_load_stream(fem_ctx *c, const uint8_t *types, const uint32_t *t_us, uint
     s.offs = offs_stride(n_types);
     const size_t nn = std::max<uint64_t>(n, 1);
     const size_t nc = std::max<uint32_t>(s.n_chunks, 1);
-    bool okm = cudaMalloc(&s.t, nn * 4) == cudaSuccess && cudaMalloc(&s.type, nn) == cudaSuccess &&
-               cudaMalloc(&s.bev, nc * CHUNK * 8) == cudaSuccess &&
-               cudaMalloc(&s.boff, nc * s.offs * 2) == cudaSuccess &&
-               cudaMalloc(&s.cfirst, (nc + 1) * 4) == cudaSuccess &&
-               cudaMalloc(&s.hist, 256 * 4) == cudaSuccess;
-    auto release = [&] {
-        cudaFree(s.t);
-        cudaFree(s.type);
-        cudaFree(s.bev);
-        cudaFree(s.boff);
-        cudaFree(s.cfirst);
-        cudaFree(s.hist);
-    };
+    bool okm = false;
+    for (size_t i = 0; i < c->pool.size(); ++i) {
+        StreamDev &q = c->pool[i];
+        if (q.cap_events >= nn && q.cap_chunks >= nc && q.cap_offs >= nc * s.offs) {
+            s.t = q.t, s.type = q.type, s.bev = q.bev, s.boff = q.boff, s.cfirst = q.cfirst,
+            s.hist = q.hist;
+            s.cap_events = q.cap_events, s.cap_chunks = q.cap_chunks, s.cap_offs = q.cap_offs;
+            c->pool.erase(c->pool.begin() + i);
+            okm = true;
+            break;
+        }
+    }
+    if (!okm) {
+        s.cap_events = nn, s.cap_chunks = nc, s.cap_offs = (uint32_t)(nc * s.offs);
+        okm = cudaMalloc(&s.t, nn * 4) == cudaSuccess && cudaMalloc(&s.type, nn) == cudaSuccess &&
+              cudaMalloc(&s.bev, nc * CHUNK * 8) == cudaSuccess &&
+              cudaMalloc(&s.boff, nc * s.offs * 2) == cudaSuccess &&
+              cudaMalloc(&s.cfirst, (nc + 1) * 4) == cudaSuccess &&
+              cudaMalloc(&s.hist, 256 * 4) == cudaSuccess;
+    }
+    auto release = [&] { free_stream_buffers(s); };
     if (!okm) {
         cudaGetLastError();
         release();
@@ -442,15 +475,15 @@ int fem_free_stream(fem_ctx *c, int32_t id) {
     auto it = c->streams.find(id);
     if (it == c->streams.end()) return FEM_ENOSTREAM;
     cudaSetDevice(c->device);
+    // Keep the buffers for the next load (work already queued that reads them runs
+    // first: every stream of this context is synchronised before reuse).
     cudaDeviceSynchronize();
-    StreamDev &s = it->second;
-    cudaFree(s.t);
-    cudaFree(s.type);
-    cudaFree(s.bev);
-    cudaFree(s.boff);
-    cudaFree(s.cfirst);
-    cudaFree(s.hist);
+    c->pool.push_back(it->second);
     c->streams.erase(it);
+    while (c->pool.size() > 4) {
+        free_stream_buffers(c->pool.front());
+        c->pool.erase(c->pool.begin());
+    }
     return FEM_OK;
 }
 
@@ -632,6 +665,8 @@ int fem_mine_levelwise(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t n
         cudaEventSynchronize(c->ev[1]);
         cudaEventElapsedTime(&ls.ms_relaxed, c->ev[0], c->ev[1]);
         ls.segments = pi.segments;
+        ls.ms_relaxed_kernel = pi.ms_kernel;
+        ls.ms_relaxed_stitch = pi.ms_stitch;
         // eliminate relaxed < theta
         cudaEventRecord(c->ev[0], st);
         CKF(launch_compact(rel, nullptr, theta, m, idx_s, c->d_small + W_COUNT0, scratch, st));
@@ -644,8 +679,11 @@ int fem_mine_levelwise(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t n
         RETF(dbuf(c, "ex", ms, &ex));
         RETF(dbuf(c, "idx_f", ms, &idx_f));
         cudaEventRecord(c->ev[0], st);
+        PassInfo pe;
         RETF(count_pass(c, s, cands, idx_s, ms, (int)N, d_ivl, nI, FEM_PASS_EXACT, ex, true, st,
-                        nullptr));
+                        &pe));
+        ls.ms_exact_kernel = pe.ms_kernel;
+        ls.exact_segments = ms ? pe.segments : 0;
         cudaEventRecord(c->ev[1], st);
         cudaEventSynchronize(c->ev[1]);
         cudaEventElapsedTime(&ls.ms_exact, c->ev[0], c->ev[1]);

@@ -36,6 +36,7 @@ cudaError_t run(const CountParams &p, uint32_t threads, cudaStream_t st) {
     if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
     dim3 grid((p.m + threads - 1) / threads, p.P);
     k_count<N, PASS, MC, R><<<grid, threads, sm, st>>>(p);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -42,6 +42,8 @@ __host__ __device__ inline uint32_t stage_bytes(uint32_t offs) {
 }
 
 struct StreamDev {
+    uint64_t cap_events = 0, cap_chunks = 0;  // allocated capacity (buffers are reused)
+    uint32_t cap_offs = 0;
     uint64_t n = 0;
     uint32_t K = 0, n_chunks = 0, offs = 0;
     uint32_t t_max = 0;
@@ -135,6 +137,9 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 #endif
 
 // ---------------------------------------------------------------- launchers (host side)
+// process-wide count of kernel launches (fem_kernel_launches)
+void note_launch(uint32_t k = 1);
+
 // fem_stream.cu
 cudaError_t launch_load_stream(StreamDev &s, cudaStream_t st, uint32_t *d_err);
 // fem_count.cu

@@ -163,6 +163,7 @@ cudaError_t launch_stitch(const uint4 *tables, uint32_t m, uint32_t P, uint32_t 
     if (m == 0) return cudaSuccess;
     const uint32_t blocks = (uint32_t)(((uint64_t)m * 32 + 255) / 256);
     k_stitch<<<blocks, 256, 0, st>>>(tables, m, P, out, redo, err);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -204,6 +205,7 @@ cudaError_t launch_validate_cands(const fem_episode *c, const uint32_t *gather, 
                                   cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     k_validate_cands<<<(m + 255) / 256, 256, 0, st>>>(c, gather, m, K, n_ivl, info, err);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -217,6 +219,7 @@ cudaError_t launch_len_flags(const fem_episode *c, const uint32_t *gather, uint3
                              uint8_t *flags, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     k_len_flags<<<(m + 255) / 256, 256, 0, st>>>(c, gather, m, N, flags);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -277,8 +280,11 @@ cudaError_t launch_compact(const uint32_t *vals, const uint8_t *flags, uint32_t 
     if (m == 0) return cudaMemsetAsync(count_out, 0, sizeof(uint32_t), st);
     const uint32_t nb = (m + CB - 1) / CB;
     k_keep_count<<<nb, CT, 0, st>>>(vals, flags, theta, m, scratch);
+    note_launch();
     k_scan_small<<<1, 1024, 0, st>>>(scratch, nb, count_out);
+    note_launch();
     k_keep_scatter<<<nb, CT, 0, st>>>(vals, flags, theta, m, scratch, idx_out);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -317,8 +323,11 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t m, uint32_t *out,
     if (m == 0) return cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
     const uint32_t nb = (m + CB - 1) / CB;
     k_sum_blocks<<<nb, CT, 0, st>>>(in, m, scratch);
+    note_launch();
     k_scan_small<<<1, 1024, 0, st>>>(scratch, nb, total);
+    note_launch();
     k_scan_apply<<<nb, CT, 0, st>>>(in, m, scratch, out);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -338,6 +347,7 @@ cudaError_t launch_gather_episodes(const fem_episode *src, const uint32_t *idx, 
                                    cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     k_gather_ep<<<(m + 255) / 256, 256, 0, st>>>(src, idx, m, dst, vals, vals_dst);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -351,6 +361,7 @@ cudaError_t launch_scatter_u32(const uint32_t *src, const uint32_t *idx, uint32_
                                uint32_t *dst, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     k_scatter_u32<<<(m + 255) / 256, 256, 0, st>>>(src, idx, m, dst);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -363,6 +374,7 @@ __global__ void k_fill_flags(const uint32_t *__restrict__ idx, uint32_t m,
 cudaError_t launch_fill_flags(const uint32_t *idx, uint32_t m, uint8_t *flags, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     k_fill_flags<<<(m + 255) / 256, 256, 0, st>>>(idx, m, flags);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -376,6 +388,7 @@ cudaError_t launch_compose_idx(const uint32_t *outer, const uint32_t *inner, uin
                                uint32_t *dst, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     k_compose_idx<<<(m + 255) / 256, 256, 0, st>>>(outer, inner, m, dst);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -394,6 +407,7 @@ __global__ void k_type_filter(const uint32_t *hist, uint32_t K, uint32_t theta, 
 cudaError_t launch_type_filter(const uint32_t *hist, uint32_t K, uint32_t theta, uint32_t *ftypes,
                                uint32_t *fcount, cudaStream_t st) {
     k_type_filter<<<1, 256, 0, st>>>(hist, K, theta, ftypes, fcount);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -424,6 +438,7 @@ cudaError_t launch_level2(const uint32_t *ftypes, uint32_t f, uint32_t n_ivl, fe
     if (f < 2 || n_ivl == 0) return cudaSuccess;
     const uint64_t m = (uint64_t)f * n_ivl * (f - 1);
     k_level2<<<(uint32_t)((m + 255) / 256), 256, 0, st>>>(ftypes, f, n_ivl, out);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -507,6 +522,7 @@ cudaError_t launch_join_count(const fem_episode *F, uint32_t f, uint32_t N, uint
                               cudaStream_t st) {
     if (f == 0) return cudaSuccess;
     k_join_count<<<(f + 127) / 128, 128, 0, st>>>(F, f, N, cnt);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -514,6 +530,7 @@ cudaError_t launch_join_emit(const fem_episode *F, uint32_t f, uint32_t N, const
                              fem_episode *out, cudaStream_t st) {
     if (f == 0) return cudaSuccess;
     k_join_emit<<<(f + 127) / 128, 128, 0, st>>>(F, f, N, off, out);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -47,13 +47,15 @@ class fem_level_stats(ctypes.Structure):
                 ("survivors", ctypes.c_uint32), ("frequent", ctypes.c_uint32),
                 ("segments", ctypes.c_uint32), ("ms_generate", ctypes.c_float),
                 ("ms_relaxed", ctypes.c_float), ("ms_compact", ctypes.c_float),
-                ("ms_exact", ctypes.c_float)]
+                ("ms_exact", ctypes.c_float), ("ms_relaxed_kernel", ctypes.c_float),
+                ("ms_relaxed_stitch", ctypes.c_float), ("ms_exact_kernel", ctypes.c_float),
+                ("exact_segments", ctypes.c_uint32)]
 
 
 EXPORTS = ["fem_create", "fem_destroy", "fem_set_config", "fem_load_stream", "fem_free_stream",
            "fem_type_counts", "fem_count_candidates", "fem_count_two_pass",
            "fem_mine_levelwise", "fem_result_level", "fem_result_max_level", "fem_result_free",
-           "fem_last_mine_stats", "fem_strerror"]
+           "fem_last_mine_stats", "fem_strerror", "fem_kernel_launches"]
 
 _lib = None
 
@@ -88,6 +90,7 @@ def load(path: str | None = None):
         "fem_result_free": (None, [vp]),
         "fem_last_mine_stats": (I, [vp, ctypes.POINTER(fem_level_stats), u32]),
         "fem_strerror": (ctypes.c_char_p, [I]),
+        "fem_kernel_launches": (u64, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -282,6 +285,10 @@ def fem_last_mine_stats(ctx):
     if k < 0:
         raise FemError(k, "fem_last_mine_stats")
     return [{f: getattr(arr[i], f) for f, _ in fem_level_stats._fields_} for i in range(k)]
+
+
+def fem_kernel_launches() -> int:
+    return int(load().fem_kernel_launches())
 
 
 def fem_strerror(status: int) -> str:
