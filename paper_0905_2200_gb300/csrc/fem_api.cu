@@ -132,12 +132,11 @@ int upload_intervals(fem_ctx *c, const fem_interval *I, uint32_t nI, cudaStream_
 }
 
 // Segments per episode for one pass.  One thread per (episode, segment); the
-// aim is about 2048 resident threads per SM, with segments of at least four
-// chunks so the look-back window stays a small fraction of the work.
+// aim is about 2048 threads per SM (segments are whole chunks, so at most one
+// segment per chunk).
 uint32_t choose_segments(fem_ctx *c, const StreamDev &s, uint32_t m, bool distinct) {
     if (s.n_chunks == 0) return 1;
-    uint32_t maxP = std::max<uint32_t>(1, s.n_chunks / 4);
-    maxP = std::min<uint32_t>(maxP, 65535);
+    const uint32_t maxP = std::min<uint32_t>(s.n_chunks, 65535);
     if (c->cfg.segments) return std::min<uint32_t>(c->cfg.segments, s.n_chunks);
     if (!distinct) return 1;
     const uint64_t target = (uint64_t)c->sm_count * 2048;
@@ -146,9 +145,12 @@ uint32_t choose_segments(fem_ctx *c, const StreamDev &s, uint32_t m, bool distin
     return (uint32_t)std::min<uint64_t>(P, maxP);
 }
 
-uint32_t choose_threads(fem_ctx *c, int N, int pass, bool mc, uint32_t R, uint32_t offs) {
+uint32_t choose_threads(fem_ctx *c, int N, int pass, bool mc, uint32_t R, uint32_t offs,
+                        uint32_t m) {
     if (c->cfg.threads_per_block) return c->cfg.threads_per_block;
-    for (uint32_t T : {128u, 64u, 32u}) {
+    for (uint32_t T : {256u, 128u, 64u, 32u}) {
+        if (T > 32 && m <= T / 2) continue;  // few episodes: small blocks, more of them
+        if (T == 256 && (N > 3 || (pass == FEM_PASS_EXACT && mc))) continue;  // register budget
         if (count_smem_bytes(N, pass, mc, R, T, offs) <= 80 * 1024) return T;
     }
     for (uint32_t T : {32u, 16u, 8u}) {
@@ -171,6 +173,7 @@ int count_pass(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const u
     p.bev = s.bev;
     p.boff = s.boff;
     p.cfirst = s.cfirst;
+    p.t = s.t;
     p.offs = s.offs;
     p.n_chunks = s.n_chunks;
     p.n = s.n;
@@ -199,7 +202,7 @@ int count_pass(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const u
     if (P > 1) {
         RET(dbuf(c, "tables", (size_t)P * m * S_MAX, &p.tables));
     }
-    const uint32_t T = choose_threads(c, N, pass, P > 1, R, s.offs);
+    const uint32_t T = choose_threads(c, N, pass, P > 1, R, s.offs, m);
     CK(cudaEventRecord(c->kev[0], st));
     CK(launch_count(N, pass, P > 1, R, T, p, st));
     CK(cudaEventRecord(c->kev[1], st));
@@ -242,7 +245,7 @@ int count_pass(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const u
         RET(dbuf(c, "redo2", r, &q.redo));
         CK(cudaMemsetAsync(q.redo, 0, r, st));
         const uint32_t Rq = pass == FEM_PASS_EXACT ? R2 : 1;
-        const uint32_t T2 = choose_threads(c, N, pass, false, Rq, s.offs);
+        const uint32_t T2 = choose_threads(c, N, pass, false, Rq, s.offs, r);
         CK(launch_count(N, pass, false, Rq, T2, q, st));
         RET(read_err(c, st, &e));
         RET(err_status(e));

@@ -143,59 +143,110 @@ __global__ void __launch_bounds__(256) k_count(const CountParams p) {
     // ---------------------------------------------------------------- machine state
     uint32_t cnt = 0;
     bool overflow = false;
-    uint32_t dl[NE], ms[NE];       // relaxed: deadline, chain start annotation (MC)
-    uint32_t head[NE], tail[NE];   // exact: ring cursors
+    // relaxed: deadline s + hi + 1 of the latest admitted time per node (0 = unset)
+    // and, segmented, the start annotation of that slot
+    uint32_t dl[NE], ms[NE];
+    // exact: ring cursors plus register copies of each ring's front entry (fx, fy)
+    // and back entry (bx, by); the ring itself lives in shared memory
+    uint32_t head[NE], tail[NE], fx[NE], fy[NE], bx[NE], by[NE];
 #pragma unroll
-    for (int k = 0; k < NE; ++k) dl[k] = ms[k] = head[k] = tail[k] = 0;
-    // MapConcatenate classes
-    uint32_t ns = 1;
-    uint32_t c_key[MC ? S_MAX : 1], c_start[MC ? S_MAX : 1], c_cnt[MC ? S_MAX : 1],
-        c_last[MC ? S_MAX : 1], c_lastt[MC ? S_MAX : 1];
+    for (int k = 0; k < NE; ++k) dl[k] = ms[k] = head[k] = tail[k] = fx[k] = fy[k] = bx[k] = by[k] = 0;
+    // MapConcatenate entry classes: class 0 is "none"; class j >= 1 restarts after the
+    // last-node event c_key[j] of the window.  A class that completes at the same
+    // event as class 0 is identical to it from then on: it is merged (its bit in
+    // umask cleared, c_cnt[j] holding its count minus class 0's) and no longer updated.
+    constexpr int SC = MC ? S_MAX : 1;
+    uint32_t ns = 1, umask = 0;
+    uint32_t c_key[SC], c_start[SC], c_cnt[SC];
 #pragma unroll
-    for (int j = 0; j < (MC ? S_MAX : 1); ++j) {
-        c_key[j] = CLS_NONE;
-        c_start[j] = 0;
-        c_cnt[j] = 0;
-        c_last[j] = CLS_NONE;
-        c_lastt[j] = 0;
-    }
+    for (int j = 0; j < SC; ++j) c_key[j] = CLS_NONE, c_start[j] = 0, c_cnt[j] = 0;
 
     uint2 *ring64 = reinterpret_cast<uint2 *>(ring_raw) + tid;
 
-    auto complete = [&](uint32_t msv, uint32_t gidx, uint32_t tt) {
+    // a completion whose chains start no earlier than msv, at event gidx
+    auto complete = [&](uint32_t msv, uint32_t gidx) {
         if constexpr (!MC) {
             ++cnt;
         } else {
+            const uint32_t inc = (uint64_t)gidx >= L ? 1u : 0u;
+            if (c_start[0] <= msv) c_start[0] = gidx + 1, c_cnt[0] += inc;
+            if (umask) {
 #pragma unroll
-            for (int j = 0; j < S_MAX; ++j) {
-                if ((uint32_t)j < ns && c_start[j] <= msv) {
-                    c_start[j] = gidx + 1;
-                    c_last[j] = gidx;
-                    c_lastt[j] = tt;
-                    if ((uint64_t)gidx >= L) ++c_cnt[j];
+                for (int j = 1; j < SC; ++j) {
+                    if ((umask >> j) & 1u) {
+                        if (c_start[j] <= msv) c_start[j] = gidx + 1, c_cnt[j] += inc;
+                        if (c_start[j] == c_start[0]) {
+                            c_cnt[j] -= c_cnt[0];
+                            umask &= ~(1u << j);
+                        }
+                    }
                 }
             }
         }
     };
 
-    // one node of the machine for an event at node k (k static after unrolling);
+    auto slot = [&](int q, uint32_t i) -> uint2 & {
+        return ring64[((uint32_t)q * R + (i & (R - 1))) * T];
+    };
+    // drop ring q's front entries that can no longer match (older than hi)
+    auto pop_dead = [&](int q, uint32_t tt) {
+        // single segment: entry (first, last) cluster, dead when last is too old;
+        // segmented: entry (t, annotation), dead when t is too old
+        while (head[q] != tail[q] && tt - (MC ? fx[q] : fy[q]) > ep.hi[q]) {
+            ++head[q];
+            if (head[q] != tail[q]) {
+                const uint2 e = slot(q, head[q]);
+                fx[q] = e.x, fy[q] = e.y;
+            }
+        }
+    };
+    auto push = [&](int q, uint32_t tt, uint32_t msv) {
+        pop_dead(q, tt);
+        const uint32_t n_in = tail[q] - head[q];
+        if (n_in) {
+            if (MC) {
+                if (bx[q] == tt) {  // equal times are one entry; annotations only grow
+                    by[q] = max(by[q], msv);
+                    slot(q, tail[q] - 1u).y = by[q];
+                    if (n_in == 1) fy[q] = by[q];
+                    return;
+                }
+            } else if (tt - by[q] <= ep.hi[q] - ep.lo[q]) {  // joins the newest cluster
+                by[q] = tt;
+                slot(q, tail[q] - 1u).y = tt;
+                if (n_in == 1) fy[q] = tt;
+                return;
+            }
+        }
+        if (n_in == (uint32_t)R) {
+            overflow = true;
+            ++head[q];
+            const uint2 e = slot(q, head[q]);
+            fx[q] = e.x, fy[q] = e.y;
+        }
+        const uint32_t yv = MC ? msv : tt;
+        slot(q, tail[q]) = make_uint2(tt, yv);
+        ++tail[q];
+        bx[q] = tt, by[q] = yv;
+        if (n_in == 0) fx[q] = tt, fy[q] = yv;
+    };
+
+    // One node of the machine for an event at node k (k static after unrolling);
     // returns true when the event completed an occurrence (stop handling it).
     auto step = [&](auto kc, uint32_t tt, uint32_t gidx) -> bool {
         constexpr int k = decltype(kc)::value;
-        if constexpr (PASS == FEM_PASS_RELAXED) {
+        if constexpr (N == 1) {
+            complete(gidx, gidx);
+            return true;
+        } else if constexpr (PASS == FEM_PASS_RELAXED) {
             if constexpr (k == 0) {
-                if constexpr (N == 1) {
-                    complete(gidx, gidx, tt);
-                    return true;
-                } else {
-                    dl[0] = tt + ep.hi[0] + 1u;
-                    if (MC) ms[0] = gidx;
-                    return false;
-                }
+                dl[0] = tt + ep.hi[0] + 1u;
+                if (MC) ms[0] = gidx;
+                return false;
             } else {
                 if (!(tt < dl[k - 1])) return false;
                 if constexpr (k == N - 1) {
-                    complete(MC ? ms[k - 1] : 0u, gidx, tt);
+                    complete(MC ? ms[k - 1] : 0u, gidx);
                     if (!MC) {
 #pragma unroll
                         for (int q = 0; q < NE; ++q) dl[q] = 0;
@@ -208,70 +259,31 @@ __global__ void __launch_bounds__(256) k_count(const CountParams p) {
                 }
             }
         } else {  // exact
-            // ring q entry i: single-segment (first, last) cluster, segmented (t, annotation)
-            auto slot = [&](int q, uint32_t i) -> uint2 & {
-                return ring64[((uint32_t)q * R + (i & (R - 1))) * T];
-            };
-            auto pop_dead = [&](int q) {
-                if (MC) {
-                    while (head[q] != tail[q] && tt - slot(q, head[q]).x > ep.hi[q]) ++head[q];
-                } else {
-                    while (head[q] != tail[q] && tt - slot(q, head[q]).y > ep.hi[q]) ++head[q];
-                }
-            };
-            auto push = [&](int q, uint32_t msv) {
-                pop_dead(q);
-                if (head[q] != tail[q]) {
-                    uint2 &b = slot(q, tail[q] - 1u);
-                    if (MC) {
-                        if (b.x == tt) {  // equal times are one entry; annotations only grow
-                            b.y = max(b.y, msv);
-                            return;
-                        }
-                    } else if (tt - b.y <= ep.hi[q] - ep.lo[q]) {
-                        b.y = tt;
-                        return;
-                    }
-                }
-                if (tail[q] - head[q] == (uint32_t)R) {
-                    overflow = true;
-                    ++head[q];
-                }
-                slot(q, tail[q]) = make_uint2(tt, MC ? msv : tt);
-                ++tail[q];
-            };
             if constexpr (k == 0) {
-                if constexpr (N == 1) {
-                    complete(gidx, gidx, tt);
-                    return true;
-                } else {
-                    push(0, gidx);
-                    return false;
-                }
+                push(0, tt, gidx);
+                return false;
             } else {
-                pop_dead(k - 1);
-                bool hit = false;
-                uint32_t msv = 0;
+                constexpr int q = k - 1;
+                pop_dead(q, tt);
+                if (!(head[q] != tail[q] && tt - fx[q] > ep.lo[q])) return false;
+                uint32_t msv = fy[q];
                 if (MC) {
-                    for (uint32_t i = head[k - 1]; i != tail[k - 1]; ++i) {
-                        const uint2 e = slot(k - 1, i);
-                        if (!(tt - e.x > ep.lo[k - 1])) break;
-                        hit = true;
-                        msv = max(msv, e.y);
+                    // annotations grow along the ring: take the newest entry older than lo
+                    for (uint32_t i = head[q] + 1u; i != tail[q]; ++i) {
+                        const uint2 e = slot(q, i);
+                        if (!(tt - e.x > ep.lo[q])) break;
+                        msv = e.y;
                     }
-                } else {
-                    hit = head[k - 1] != tail[k - 1] && tt - slot(k - 1, head[k - 1]).x > ep.lo[k - 1];
                 }
-                if (!hit) return false;
                 if constexpr (k == N - 1) {
-                    complete(msv, gidx, tt);
+                    complete(msv, gidx);
                     if (!MC) {
 #pragma unroll
-                        for (int q = 0; q < NE; ++q) head[q] = tail[q];
+                        for (int r = 0; r < NE; ++r) head[r] = tail[r];
                     }
                     return true;
                 } else {
-                    push(k, msv);
+                    push(k, tt, msv);
                     return false;
                 }
             }
@@ -327,38 +339,34 @@ __global__ void __launch_bounds__(256) k_count(const CountParams p) {
                 for (int k = 1; k < N; ++k) mk = min(mk, key[k]);
                 if (mk == KEY_END) break;
                 const uint32_t gidx = (uint32_t)(cbase + mk);
+                const bool last_hit = key[N - 1] == mk;
                 bool done = false;
-                bool last_node = false;
-                uint32_t tt_last = 0;
-for_nodes_desc<N - 1>([&](auto kc) {
+                for_nodes_desc<N - 1>([&](auto kc) {
                     constexpr int k = decltype(kc)::value;
                     if (key[k] == mk) {
                         if (!done) done = step(kc, tv[k], gidx);
-                        if constexpr (k == N - 1) {
-                            last_node = true;
-                            tt_last = tv[k];
-                        }
+                        // next entry of this group; reading one past the group's end stays
+                        // inside the stage buffer and the value is then discarded
                         ++ptr[k];
-                        if (ptr[k] < end[k]) {
-                            const uint2 e = ev[ptr[k]];
-                            tv[k] = e.x;
-                            key[k] = e.y;
-                        } else {
-                            key[k] = KEY_END;
-                        }
+                        const uint2 e = ev[ptr[k]];
+                        tv[k] = e.x;
+                        key[k] = ptr[k] < end[k] ? e.y : KEY_END;
                     }
                 });
-                if (MC && last_node && (uint64_t)gidx < L) {
-                    // register entry class r = gidx: a machine that restarts after r
-                    if (ns < (uint32_t)S_MAX) {
+                if (MC && last_hit && (uint64_t)gidx < L) {
+                    // entry class r = gidx: the serial machine's last completion was r
+                    if (ns < (uint32_t)SC) {
 #pragma unroll
-                        for (int q = 0; q < (MC ? S_MAX : 1); ++q) {
+                        for (int q = 1; q < SC; ++q) {
                             if ((uint32_t)q == ns) {
                                 c_key[q] = gidx;
                                 c_start[q] = gidx + 1;
                                 c_cnt[q] = 0;
-                                c_last[q] = gidx;
-                                c_lastt[q] = tt_last;
+                                umask |= 1u << q;
+                                if (c_start[0] == gidx + 1) {
+                                    c_cnt[q] -= c_cnt[0];
+                                    umask &= ~(1u << q);
+                                }
                             }
                         }
                         ++ns;
@@ -396,12 +404,17 @@ for_nodes_desc<N - 1>([&](auto kc) {
     } else {
         uint4 *tab = p.tables + ((uint64_t)seg * p.m + ci) * S_MAX;
 #pragma unroll
-        for (int q = 0; q < (MC ? S_MAX : 1); ++q) {
+        for (int q = 0; q < S_MAX; ++q) {
             uint4 e = make_uint4(CLS_EMPTY, 0, CLS_NONE, 0);
             if (ok && (uint32_t)q < ns) {
-                uint32_t ex = c_last[q];
-                if (ex != CLS_NONE && !last_seg && c_lastt[q] < Xn) ex = CLS_NONE;
-                e = make_uint4(c_key[q], c_cnt[q], ex, 0);
+                const bool merged = q > 0 && !((umask >> q) & 1u);
+                const uint32_t cntq = merged ? c_cnt[0] + c_cnt[q] : c_cnt[q];
+                const uint32_t st = merged ? c_start[0] : c_start[q];
+                // the last completion (or the class's own event) is st - 1; it is
+                // handed on only if it lies in the next segment's window
+                uint32_t ex = st == 0 ? CLS_NONE : st - 1u;
+                if (ex != CLS_NONE && !last_seg && p.t[ex] < Xn) ex = CLS_NONE;
+                e = make_uint4(c_key[q], cntq, ex, 0);
             }
             tab[q] = e;
         }

@@ -60,6 +60,7 @@ struct CountParams {
     const uint2 *bev;
     const uint16_t *boff;
     const uint32_t *cfirst;
+    const uint32_t *t;          // event times (read only for MapConcatenate exits)
     uint32_t offs, n_chunks;
     uint64_t n;
     uint32_t K;
