@@ -55,7 +55,7 @@ class fem_level_stats(ctypes.Structure):
 EXPORTS = ["fem_create", "fem_destroy", "fem_set_config", "fem_load_stream", "fem_free_stream",
            "fem_type_counts", "fem_count_candidates", "fem_count_two_pass",
            "fem_mine_levelwise", "fem_result_level", "fem_result_max_level", "fem_result_free",
-           "fem_last_mine_stats", "fem_strerror", "fem_kernel_launches"]
+           "fem_last_mine_stats", "fem_strerror", "fem_kernel_launches", "fem_select_noalloc"]
 
 _lib = None
 
@@ -91,6 +91,7 @@ def load(path: str | None = None):
         "fem_last_mine_stats": (I, [vp, ctypes.POINTER(fem_level_stats), u32]),
         "fem_strerror": (ctypes.c_char_p, [I]),
         "fem_kernel_launches": (u64, []),
+        "fem_select_noalloc": (I, [vp, u32, u32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -285,6 +286,18 @@ def fem_last_mine_stats(ctx):
     if k < 0:
         raise FemError(k, "fem_last_mine_stats")
     return [{f: getattr(arr[i], f) for f, _ in fem_level_stats._fields_} for i in range(k)]
+
+
+def fem_select_noalloc(values, theta, idx_out, count_out, stream=None):
+    """Indices i with values[i] >= theta into idx_out, their number into count_out[0]
+    (all CUDA tensors, no allocation by the library).  Asynchronous on the stream."""
+    pv, dv = _ptr(values)
+    pi, di = _ptr(idx_out)
+    pc, dc = _ptr(count_out)
+    if not (dv and di and dc):
+        raise ValueError("values, idx_out and count_out must be device tensors")
+    _check(load().fem_select_noalloc(pv, int(values.shape[0]), int(theta), pi, pc,
+                                     _stream_handle(stream)), "fem_select_noalloc")
 
 
 def fem_kernel_launches() -> int:
