@@ -764,3 +764,301 @@ int fem_last_mine_stats(fem_ctx *c, fem_level_stats *out, uint32_t cap) {
 }
 
 }  // extern "C"
+
+// ============================================================================ batches
+namespace {
+
+constexpr uint32_t kBatchChunksPerItem = 16;  // segment length of batched work items
+
+struct BatchGroup {
+    int N = 0;
+    uint32_t n_jobs = 0, m = 0;
+    std::vector<uint32_t> user_job;  // user job index of each group job
+    std::vector<uint32_t> off;       // host copy of cand_off
+    fem_episode *cands = nullptr;
+    uint32_t *cand_off = nullptr, *theta = nullptr;
+    CountParams *rjobs = nullptr, *xjobs = nullptr;
+    BatchOut *outs = nullptr;
+    uint32_t *rel = nullptr, *ex = nullptr, *idx = nullptr, *scratch = nullptr;
+    uint8_t *flags = nullptr, *redo = nullptr, *xredo = nullptr;
+    uint32_t *item_off_r = nullptr, *item_off_x = nullptr;
+    uint4 *items_r = nullptr, *items_x = nullptr;
+    uint32_t cap_r = 0, cap_x = 0;
+    uint32_t *counters = nullptr;  // n_items_r, n_items_x, queue_r, queue_x, n_idx
+    uint4 *tables = nullptr;
+    uint32_t SB = 0, Tr = 128, Tx = 128, Rx = 16;
+};
+
+}  // namespace
+
+struct fem_batch {
+    fem_ctx *ctx = nullptr;
+    std::vector<fem_job> jobs;
+    std::vector<BatchGroup> groups;
+    std::vector<void *> allocs;
+    uint2 *ivl = nullptr;
+    uint32_t nI = 0;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+template <typename T>
+int balloc(fem_batch *b, size_t count, T **out) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(count * sizeof(T), 256)) != cudaSuccess) {
+        cudaGetLastError();
+        return FEM_ENOMEM;
+    }
+    b->allocs.push_back(p);
+    *out = static_cast<T *>(p);
+    return FEM_OK;
+}
+
+void batch_free(fem_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (void *p : b->allocs) cudaFree(p);
+    delete b;
+}
+
+// The whole two-pass count of the batch, enqueued on st without host round trips.
+int batch_enqueue(fem_batch *b, cudaStream_t st) {
+    fem_ctx *c = b->ctx;
+    for (BatchGroup &g : b->groups) {
+        CK(cudaMemsetAsync(g.counters, 0, 8 * sizeof(uint32_t), st));
+        CK(cudaMemsetAsync(g.redo, 0, g.m, st));
+        CK(cudaMemsetAsync(g.xredo, 0, g.m, st));
+        // first pass: relaxed counts of every candidate (Algorithm 3)
+        CK(launch_batch_items(g.rjobs, g.n_jobs, g.Tr, g.item_off_r, g.counters + 0, g.cap_r,
+                              g.items_r, st));
+        CK(launch_count_batch(g.N, FEM_PASS_RELAXED, 1, g.Tr, g.rjobs, g.items_r, g.counters + 0,
+                              g.counters + 2, g.SB, c->sm_count, st));
+        CK(launch_stitch_batch(g.rjobs, g.cand_off, g.n_jobs, g.m, c->d_err, st));
+        // elimination at each job's theta (Algorithm 4)
+        CK(launch_batch_keep_flags(g.rel, g.cand_off, g.theta, g.n_jobs, g.m, g.flags, st));
+        CK(launch_compact(nullptr, g.flags, 0, g.m, g.idx, g.counters + 4, g.scratch, st));
+        // second pass: exact counts of the survivors (Algorithm 1)
+        CK(launch_batch_exact_jobs(g.xjobs, g.cand_off, g.n_jobs, g.idx, g.counters + 4, g.ex, st));
+        CK(launch_batch_items(g.xjobs, g.n_jobs, g.Tx, g.item_off_x, g.counters + 1, g.cap_x,
+                              g.items_x, st));
+        CK(launch_count_batch(g.N, FEM_PASS_EXACT, g.Rx, g.Tx, g.xjobs, g.items_x, g.counters + 1,
+                              g.counters + 3, g.SB, c->sm_count, st));
+        CK(launch_stitch_batch(g.xjobs, g.cand_off, g.n_jobs, g.m, c->d_err, st));
+        CK(launch_batch_outputs(g.outs, g.cand_off, g.n_jobs, g.m, g.idx, g.counters + 4, g.ex, st));
+    }
+    return FEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fem_batch_create(fem_ctx *c, const fem_job *jobs, uint32_t n_jobs, const fem_interval *I,
+                     uint32_t nI, void *cuda_stream, fem_batch **out) {
+    if (!c || !out || !jobs || n_jobs == 0) return FEM_EINVAL;
+    *out = nullptr;
+    for (uint32_t j = 0; j < n_jobs; ++j) {
+        const StreamDev *s = find_stream(c, jobs[j].stream_id);
+        if (!s) return FEM_ENOSTREAM;
+        if (jobs[j].len < 1 || jobs[j].len > FEM_MAX_LEN) return FEM_EINVAL;
+        if (jobs[j].m && (!jobs[j].cands || !jobs[j].exact_out || !jobs[j].survived_out))
+            return FEM_EINVAL;
+        RET(check_intervals(*s, I, nI));
+    }
+    cudaSetDevice(c->device);
+    cudaStream_t st = pick(c, cuda_stream);
+    fem_batch *b = new (std::nothrow) fem_batch;
+    if (!b) return FEM_ENOMEM;
+    b->ctx = c;
+    b->jobs.assign(jobs, jobs + n_jobs);
+    b->nI = nI;
+    auto fail = [&](int rc) {
+        cudaStreamSynchronize(st);
+        batch_free(b);
+        return rc;
+    };
+#define BRET(x)                           \
+    do {                                  \
+        int r_ = (x);                     \
+        if (r_ != FEM_OK) return fail(r_); \
+    } while (0)
+#define BCK(x)                                          \
+    do {                                                \
+        if ((x) != cudaSuccess) return fail(FEM_ECUDA); \
+    } while (0)
+    BRET(balloc(b, std::max<uint32_t>(nI, 1), &b->ivl));
+    if (nI) BCK(cudaMemcpyAsync(b->ivl, I, nI * sizeof(uint2), cudaMemcpyHostToDevice, st));
+
+    for (int N = 1; N <= FEM_MAX_LEN; ++N) {
+        BatchGroup g;
+        g.N = N;
+        struct Ent {
+            uint32_t j, P, cps;
+        };
+        std::vector<Ent> ents;
+        for (uint32_t j = 0; j < n_jobs; ++j) {
+            if ((int)jobs[j].len != N || jobs[j].m == 0) continue;
+            const StreamDev &s = *find_stream(c, jobs[j].stream_id);
+            const uint32_t nch = std::max<uint32_t>(s.n_chunks, 1);
+            uint32_t P = (nch + kBatchChunksPerItem - 1) / kBatchChunksPerItem;
+            const uint32_t cps = (nch + P - 1) / P;
+            P = (nch + cps - 1) / cps;
+            ents.push_back({j, P, cps});
+        }
+        if (ents.empty()) continue;
+        // longest items first: the persistent blocks then finish together
+        std::stable_sort(ents.begin(), ents.end(),
+                         [](const Ent &a, const Ent &b2) { return a.cps > b2.cps; });
+        g.n_jobs = (uint32_t)ents.size();
+        g.Tr = N <= 3 ? 256 : 128;
+        g.Tx = 128;
+        g.Rx = 16;
+        uint64_t m = 0, tab = 0, cap_r = 0, cap_x = 0;
+        uint32_t max_offs = 8;
+        g.off.push_back(0);
+        for (const Ent &e : ents) {
+            const fem_job &jb = jobs[e.j];
+            g.user_job.push_back(e.j);
+            m += jb.m;
+            g.off.push_back((uint32_t)m);
+            tab += (uint64_t)jb.m * e.P * S_MAX;
+            cap_r += (uint64_t)((jb.m + g.Tr - 1) / g.Tr) * e.P;
+            cap_x += (uint64_t)((jb.m + g.Tx - 1) / g.Tx) * e.P;
+            max_offs = std::max(max_offs, find_stream(c, jb.stream_id)->offs);
+        }
+        if (m > 0xFFFFFFF0ull || cap_r > 0xFFFFFFF0ull) return fail(FEM_ENOMEM);
+        g.m = (uint32_t)m;
+        g.cap_r = (uint32_t)cap_r;
+        g.cap_x = (uint32_t)cap_x;
+        g.SB = stage_bytes(max_offs);
+        const uint32_t n = g.n_jobs;
+        BRET(balloc(b, m, &g.cands));
+        BRET(balloc(b, n + 1, &g.cand_off));
+        BRET(balloc(b, n, &g.theta));
+        BRET(balloc(b, n, &g.rjobs));
+        BRET(balloc(b, n, &g.xjobs));
+        BRET(balloc(b, n, &g.outs));
+        BRET(balloc(b, m, &g.rel));
+        BRET(balloc(b, m, &g.ex));
+        BRET(balloc(b, m, &g.idx));
+        BRET(balloc(b, compact_scratch_words(g.m), &g.scratch));
+        BRET(balloc(b, m, &g.flags));
+        BRET(balloc(b, m, &g.redo));
+        BRET(balloc(b, m, &g.xredo));
+        BRET(balloc(b, n + 1, &g.item_off_r));
+        BRET(balloc(b, n + 1, &g.item_off_x));
+        BRET(balloc(b, cap_r, &g.items_r));
+        BRET(balloc(b, cap_x, &g.items_x));
+        BRET(balloc(b, 8, &g.counters));
+        BRET(balloc(b, tab, &g.tables));
+        std::vector<CountParams> rj(n), xj(n);
+        std::vector<uint32_t> th(n);
+        std::vector<BatchOut> bo(n);
+        uint64_t toff = 0;
+        for (uint32_t k = 0; k < n; ++k) {
+            const fem_job &jb = jobs[ents[k].j];
+            const StreamDev &s = *find_stream(c, jb.stream_id);
+            BCK(cudaMemcpyAsync(g.cands + g.off[k], jb.cands, (size_t)jb.m * sizeof(fem_episode),
+                                cudaMemcpyDeviceToDevice, st));
+            CountParams p{};
+            p.bev = s.bev;
+            p.boff = s.boff;
+            p.cfirst = s.cfirst;
+            p.t = s.t;
+            p.offs = s.offs;
+            p.n_chunks = s.n_chunks;
+            p.n = s.n;
+            p.K = s.K;
+            p.ivl = b->ivl;
+            p.n_ivl = nI;
+            p.cps = ents[k].cps;
+            p.P = ents[k].P;
+            p.tables = g.tables + toff;
+            p.err = c->d_err;
+            toff += (uint64_t)jb.m * ents[k].P * S_MAX;
+            CountParams r = p, x = p;
+            r.cands = g.cands + g.off[k];
+            r.m = jb.m;
+            r.out = g.rel + g.off[k];
+            r.redo = g.redo + g.off[k];
+            x.cands = g.cands;  // gathered through the survivor list at run time
+            x.m = 0;
+            x.redo = g.xredo + g.off[k];
+            rj[k] = r;
+            xj[k] = x;
+            th[k] = jb.theta;
+            bo[k] = BatchOut{jb.exact_out, jb.survived_out};
+        }
+        BCK(cudaMemcpyAsync(g.rjobs, rj.data(), n * sizeof(CountParams), cudaMemcpyHostToDevice, st));
+        BCK(cudaMemcpyAsync(g.xjobs, xj.data(), n * sizeof(CountParams), cudaMemcpyHostToDevice, st));
+        BCK(cudaMemcpyAsync(g.cand_off, g.off.data(), (n + 1) * 4, cudaMemcpyHostToDevice, st));
+        BCK(cudaMemcpyAsync(g.theta, th.data(), n * 4, cudaMemcpyHostToDevice, st));
+        BCK(cudaMemcpyAsync(g.outs, bo.data(), n * sizeof(BatchOut), cudaMemcpyHostToDevice, st));
+        BCK(cudaStreamSynchronize(st));  // host staging vectors go out of scope
+        b->groups.push_back(std::move(g));
+    }
+    // one eager run (sets kernel attributes, checks the inputs), then capture
+    BRET(fem_batch_run(b, cuda_stream));
+    BCK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+    BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = batch_enqueue(b, b->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &graph);
+    if (rc != FEM_OK) return fail(rc);
+    if (ce != cudaSuccess) return fail(FEM_ECUDA);
+    b->graph = graph;
+    BCK(cudaGraphInstantiate(&b->exec, graph, 0));
+    *out = b;
+    return FEM_OK;
+#undef BRET
+#undef BCK
+}
+
+int fem_batch_run(fem_batch *b, void *cuda_stream) {
+    if (!b) return FEM_EINVAL;
+    fem_ctx *c = b->ctx;
+    cudaSetDevice(c->device);
+    cudaStream_t st = pick(c, cuda_stream);
+    CK(cudaMemsetAsync(c->d_err, 0, 4, st));
+    if (b->exec) {
+        CK(cudaGraphLaunch(b->exec, st));
+    } else {
+        RET(batch_enqueue(b, st));
+    }
+    uint32_t e;
+    RET(read_err(c, st, &e));
+    RET(err_status(e));
+    if (!(e & (ERR_RING | ERR_TABLE))) return FEM_OK;
+    // A capacity guard tripped somewhere: recount the affected jobs one at a time
+    // with the single-recording path, which widens rings as needed.
+    std::vector<fem_interval> I(b->nI);
+    if (b->nI) CK(cudaMemcpy(I.data(), b->ivl, b->nI * sizeof(uint2), cudaMemcpyDeviceToHost));
+    for (BatchGroup &g : b->groups) {
+        std::vector<uint8_t> r(g.m), x(g.m);
+        CK(cudaMemcpy(r.data(), g.redo, g.m, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(x.data(), g.xredo, g.m, cudaMemcpyDeviceToHost));
+        for (uint32_t k = 0; k < g.n_jobs; ++k) {
+            bool hit = false;
+            for (uint32_t i = g.off[k]; i < g.off[k + 1] && !hit; ++i) hit = r[i] || x[i];
+            if (!hit) continue;
+            const fem_job &jb = b->jobs[g.user_job[k]];
+            RET(fem_count_two_pass(c, jb.stream_id, jb.cands, jb.m, 1, I.data(), b->nI, jb.theta,
+                                   jb.exact_out, jb.survived_out, 1, st));
+        }
+    }
+    return FEM_OK;
+}
+
+int fem_batch_destroy(fem_batch *b) {
+    if (!b) return FEM_EINVAL;
+    cudaSetDevice(b->ctx->device);
+    cudaDeviceSynchronize();
+    batch_free(b);
+    return FEM_OK;
+}
+
+}  // extern "C"

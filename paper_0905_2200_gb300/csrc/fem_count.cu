@@ -1,4 +1,5 @@
 // fem_count.cu -- instantiation and launch of the counting kernels.
+#include <algorithm>
 #include <mutex>
 #include <type_traits>
 
@@ -22,6 +23,56 @@ bool count_config_supported(int N, int pass, bool mc, uint32_t ring_cap) {
 }
 
 namespace {
+
+struct BatchArgs {
+    const CountParams *jobs;
+    const uint4 *items;
+    const uint32_t *n_items;
+    uint32_t *queue;
+    uint32_t SB;
+    uint32_t blocks;  // 0: one wave of resident blocks
+};
+
+template <int N, int PASS, bool MC, int R>
+cudaError_t run_batch(const BatchArgs &a, uint32_t threads, int sm_count, cudaStream_t st) {
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [] {
+        attr_err = cudaFuncSetAttribute(k_count_batch<N, PASS, MC, R>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    size_t sm = 2 * (size_t)a.SB + 128;
+    if (PASS == FEM_PASS_EXACT && N > 1) sm += (size_t)(N - 1) * R * threads * 8u;
+    if (sm > 200 * 1024) return cudaErrorInvalidConfiguration;
+    uint32_t blocks = a.blocks;
+    if (!blocks) {
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, k_count_batch<N, PASS, MC, R>, (int)threads, sm);
+        if (e != cudaSuccess) return e;
+        blocks = (uint32_t)std::max(1, per_sm) * (uint32_t)sm_count;
+    }
+    k_count_batch<N, PASS, MC, R><<<blocks, threads, sm, st>>>(a.jobs, a.items, a.n_items,
+                                                               a.queue, a.SB);
+    note_launch();
+    return cudaGetLastError();
+}
+
+template <int N, int PASS>
+cudaError_t run_batch_r(uint32_t R, const BatchArgs &a, uint32_t threads, int sm_count,
+                        cudaStream_t st) {
+    if constexpr (PASS == FEM_PASS_RELAXED) {
+        return run_batch<N, PASS, true, 1>(a, threads, sm_count, st);
+    } else {
+        switch (R) {
+            case 8: return run_batch<N, PASS, true, 8>(a, threads, sm_count, st);
+            case 16: return run_batch<N, PASS, true, 16>(a, threads, sm_count, st);
+            case 32: return run_batch<N, PASS, true, 32>(a, threads, sm_count, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+}
 
 template <int N, int PASS, bool MC, int R>
 cudaError_t run(const CountParams &p, uint32_t threads, cudaStream_t st) {
@@ -67,7 +118,33 @@ cudaError_t run_n(int pass, bool mc, uint32_t R, const CountParams &p, uint32_t 
               : run_r<N, FEM_PASS_EXACT, false>(R, p, threads, st);
 }
 
+template <int N>
+cudaError_t run_batch_n(int pass, uint32_t R, const BatchArgs &a, uint32_t threads, int sm_count,
+                        cudaStream_t st) {
+    return pass == FEM_PASS_RELAXED
+               ? run_batch_r<N, FEM_PASS_RELAXED>(R, a, threads, sm_count, st)
+               : run_batch_r<N, FEM_PASS_EXACT>(R, a, threads, sm_count, st);
+}
+
 }  // namespace
+
+cudaError_t launch_count_batch(int N, int pass, uint32_t ring_cap, uint32_t threads,
+                               const CountParams *jobs, const uint4 *items,
+                               const uint32_t *n_items, uint32_t *queue, uint32_t SB,
+                               int sm_count, cudaStream_t st) {
+    const BatchArgs a{jobs, items, n_items, queue, SB, 0};
+    switch (N) {
+        case 1: return run_batch_n<1>(pass, ring_cap, a, threads, sm_count, st);
+        case 2: return run_batch_n<2>(pass, ring_cap, a, threads, sm_count, st);
+        case 3: return run_batch_n<3>(pass, ring_cap, a, threads, sm_count, st);
+        case 4: return run_batch_n<4>(pass, ring_cap, a, threads, sm_count, st);
+        case 5: return run_batch_n<5>(pass, ring_cap, a, threads, sm_count, st);
+        case 6: return run_batch_n<6>(pass, ring_cap, a, threads, sm_count, st);
+        case 7: return run_batch_n<7>(pass, ring_cap, a, threads, sm_count, st);
+        case 8: return run_batch_n<8>(pass, ring_cap, a, threads, sm_count, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_count(int N, int pass, bool mc, uint32_t ring_cap, uint32_t threads,
                          const CountParams &p, cudaStream_t st) {

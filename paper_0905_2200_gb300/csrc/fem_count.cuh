@@ -60,18 +60,27 @@ struct EpRegs {
     uint32_t lo[NE], hi[NE];
 };
 
+// Shared memory of a counting block: two chunk stages of SB bytes each, then two
+// mbarriers and a scratch word, then the exact pass's rings.
+__device__ __forceinline__ uint64_t *stage_bars(uint8_t *smem, uint32_t SB) {
+    return reinterpret_cast<uint64_t *>(smem + 2 * SB);
+}
+
+// Count one work item: the block's T threads take episodes tile*T .. tile*T+T-1 of
+// the candidate set over segment `seg`.  `q` is the block's running number of
+// consumed chunk stages (it selects the stage and mbarrier phase of each chunk and
+// carries over to the block's next item).  Returns false if a bounded wait gave up;
+// the caller must then stop using the block's shared memory.
 template <int N, int PASS, bool MC, int R>
-__global__ void __launch_bounds__(256) k_count(const CountParams p) {
-    extern __shared__ __align__(128) uint8_t smem[];
+__device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, uint32_t seg,
+                                           uint8_t *smem, uint32_t SB, uint32_t &q) {
     constexpr int NE = EpRegs<N>::NE;
     const uint32_t T = blockDim.x, tid = threadIdx.x;
-    const uint32_t SB = stage_bytes(p.offs);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * SB);
+    uint64_t *bar = stage_bars(smem, SB);
     uint32_t *s_minc = reinterpret_cast<uint32_t *>(smem + 2 * SB + 16);
     uint8_t *ring_raw = smem + 2 * SB + 128;
 
-    const uint32_t ci = blockIdx.x * T + tid;
-    const uint32_t seg = blockIdx.y;
+    const uint32_t ci = tile * T + tid;
 
     // ---------------------------------------------------------------- episode
     EpRegs<N> ep;
@@ -131,14 +140,10 @@ __global__ void __launch_bounds__(256) k_count(const CountParams p) {
         if (tid == 0) *s_minc = c_seg0;
         __syncthreads();
         if (ok) atomicMin(s_minc, c_w);
+        __syncthreads();
     }
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
     const uint32_t c_first = MC ? *s_minc : c_seg0;
+    const uint32_t q0 = q;
 
     // ---------------------------------------------------------------- machine state
     uint32_t cnt = 0;
@@ -300,14 +305,14 @@ __global__ void __launch_bounds__(256) k_count(const CountParams p) {
         bulk_g2s(dst + chunk_ev_bytes, p.boff + (uint64_t)c * p.offs, chunk_off_bytes, &bar[s]);
     };
     if (tid == 0) {
-        if (c_first < c_end) issue(c_first, 0);
-        if (c_first + 1 < c_end) issue(c_first + 1, 1);
+        if (c_first < c_end) issue(c_first, q0 & 1u);
+        if (c_first + 1 < c_end) issue(c_first + 1, (q0 + 1) & 1u);
     }
 
     bool bail = false;
     uint32_t c = c_first;
     for (; c < c_end; ++c) {
-        const uint32_t j = c - c_first, s = j & 1u, par = (j >> 1) & 1u;
+        const uint32_t j = q0 + (c - c_first), s = j & 1u, par = (j >> 1) & 1u;
         const bool waited = mbar_wait_bounded(&bar[s], par, p.err);
         if (!__syncthreads_and(waited)) {
             bail = true;
@@ -386,15 +391,16 @@ __global__ void __launch_bounds__(256) k_count(const CountParams p) {
         // drain the copies still in flight before the block's shared memory goes away
         if (tid == 0) {
             for (uint32_t cc = c; cc < min(c + 2, c_end); ++cc) {
-                const uint32_t j = cc - c_first;
+                const uint32_t j = q0 + (cc - c_first);
                 mbar_wait_bounded(&bar[j & 1u], (j >> 1) & 1u, p.err);
             }
         }
-        return;
+        return false;
     }
+    q = q0 + (c_end > c_first ? c_end - c_first : 0u);
 
     // ---------------------------------------------------------------- results
-    if (ci >= p.m) return;
+    if (ci >= p.m) return true;
     if (overflow) {
         atomicOr(p.err, ERR_RING);
         p.redo[ci] = 1;
@@ -418,6 +424,54 @@ __global__ void __launch_bounds__(256) k_count(const CountParams p) {
             }
             tab[q] = e;
         }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void init_stage_bars(uint8_t *smem, uint32_t SB) {
+    if (threadIdx.x == 0) {
+        uint64_t *bar = stage_bars(smem, SB);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+// One block per (episode tile, segment) of one candidate set.
+template <int N, int PASS, bool MC, int R>
+__global__ void __launch_bounds__(256) k_count(const CountParams p) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const uint32_t SB = stage_bytes(p.offs);
+    init_stage_bars(smem, SB);
+    uint32_t q = 0;
+    count_item<N, PASS, MC, R>(p, blockIdx.x, blockIdx.y, smem, SB, q);
+}
+
+// Persistent form for a batch of candidate sets over several streams: each block
+// takes (job, tile, segment) items from a device queue until the list is
+// exhausted.  Items come longest first; `jobs` and the item list are device
+// resident, so a captured graph can replay the launch with new sizes.
+template <int N, int PASS, bool MC, int R>
+__global__ void __launch_bounds__(256) k_count_batch(const CountParams *__restrict__ jobs,
+                                                     const uint4 *__restrict__ items,
+                                                     const uint32_t *n_items, uint32_t *queue,
+                                                     uint32_t SB) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ CountParams s_job;
+    __shared__ uint32_t s_item;
+    init_stage_bars(smem, SB);
+    uint32_t q = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1u);
+        __syncthreads();
+        const uint32_t it = s_item;
+        if (it >= *n_items) break;
+        const uint4 d = items[it];
+        if (threadIdx.x == 0) s_job = jobs[d.x];
+        __syncthreads();
+        if (!count_item<N, PASS, MC, R>(s_job, d.y, d.z, smem, SB, q)) break;
+        __syncthreads();
     }
 }
 

@@ -77,6 +77,12 @@ struct CountParams {
     uint32_t *err;
 };
 
+// Per-job output arrays of a batch (device pointers owned by the caller).
+struct BatchOut {
+    uint32_t *exact;
+    uint8_t *survived;
+};
+
 // ---------------------------------------------------------------- PTX helpers
 #ifdef __CUDACC__
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -149,8 +155,17 @@ cudaError_t launch_count(int N, int pass, bool mc, uint32_t ring_cap, uint32_t t
 size_t count_smem_bytes(int N, int pass, bool mc, uint32_t ring_cap, uint32_t threads,
                         uint32_t offs);
 bool count_config_supported(int N, int pass, bool mc, uint32_t ring_cap);
+// persistent batched counting (segmented form for every job; ring_cap 8/16/32 for exact)
+cudaError_t launch_count_batch(int N, int pass, uint32_t ring_cap, uint32_t threads,
+                               const CountParams *jobs, const uint4 *items,
+                               const uint32_t *n_items, uint32_t *queue, uint32_t SB,
+                               int sm_count, cudaStream_t st);
 cudaError_t count_set_smem_limits();
 // fem_mine.cu
+// stitch of a batch: job_base[j] = first global episode slot of job j (n_jobs + 1
+// entries); slots >= a job's current m are skipped
+cudaError_t launch_stitch_batch(const CountParams *jobs, const uint32_t *job_base,
+                                uint32_t n_jobs, uint32_t slots, uint32_t *err, cudaStream_t st);
 cudaError_t launch_stitch(const uint4 *tables, uint32_t m, uint32_t P, uint32_t *out,
                           uint8_t *redo, uint32_t *err, cudaStream_t st);
 // info[0] |= 1 << len of every candidate; info[1] += candidates with a repeated type
@@ -181,6 +196,19 @@ cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t m, uint32_t *out,
                                   uint32_t *total, uint32_t *scratch, cudaStream_t st);
 cudaError_t launch_join_emit(const fem_episode *F, uint32_t f, uint32_t N, const uint32_t *off,
                              fem_episode *out, cudaStream_t st);
+// fem_batch.cu
+cudaError_t launch_batch_items(const CountParams *jobs, uint32_t n_jobs, uint32_t T,
+                               uint32_t *item_off, uint32_t *n_items, uint32_t cap, uint4 *items,
+                               cudaStream_t st);
+cudaError_t launch_batch_keep_flags(const uint32_t *rel, const uint32_t *cand_off,
+                                    const uint32_t *theta, uint32_t n_jobs, uint32_t m,
+                                    uint8_t *flags, cudaStream_t st);
+cudaError_t launch_batch_exact_jobs(CountParams *xjobs, const uint32_t *cand_off, uint32_t n_jobs,
+                                    const uint32_t *idx, const uint32_t *n_idx, uint32_t *ex,
+                                    cudaStream_t st);
+cudaError_t launch_batch_outputs(const BatchOut *outs, const uint32_t *cand_off, uint32_t n_jobs,
+                                 uint32_t m, const uint32_t *idx, const uint32_t *n_idx,
+                                 const uint32_t *ex, cudaStream_t st);
 cudaError_t launch_type_filter(const uint32_t *hist, uint32_t K, uint32_t theta,
                                uint32_t *ftypes, uint32_t *fcount, cudaStream_t st);
 

@@ -69,12 +69,9 @@ __device__ __forceinline__ bool keep_at(const uint32_t *vals, const uint8_t *fla
 // run of segments (for every entry class of the run's first segment); the 32
 // partial functions are then composed pairwise in log2(32) shuffle rounds, the
 // tree of Concatenate steps; lane 0 evaluates the result at class "none".
-__global__ void __launch_bounds__(256) k_stitch(const uint4 *__restrict__ tables, uint32_t m,
-                                                uint32_t P, uint32_t *__restrict__ out,
-                                                uint8_t *__restrict__ redo, uint32_t *err) {
-    const uint32_t ci = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ void stitch_one(const uint4 *__restrict__ tables, uint32_t m, uint32_t P, uint32_t ci,
+                           uint32_t *__restrict__ out, uint8_t *__restrict__ redo, uint32_t *err) {
     const uint32_t lane = threadIdx.x & 31;
-    if (ci >= m) return;
     if (redo[ci]) return;  // the host recounts this episode
     const uint32_t a = (uint32_t)(((uint64_t)P * lane) >> 5);
     const uint32_t b = (uint32_t)(((uint64_t)P * (lane + 1)) >> 5);
@@ -156,6 +153,40 @@ __global__ void __launch_bounds__(256) k_stitch(const uint4 *__restrict__ tables
             out[ci] = total;
         }
     }
+}
+
+__global__ void __launch_bounds__(256) k_stitch(const uint4 *__restrict__ tables, uint32_t m,
+                                                uint32_t P, uint32_t *__restrict__ out,
+                                                uint8_t *__restrict__ redo, uint32_t *err) {
+    const uint32_t ci = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (ci < m) stitch_one(tables, m, P, ci, out, redo, err);
+}
+
+// One warp per episode slot of a batch of jobs (each job its own tables and outputs).
+__global__ void __launch_bounds__(256) k_stitch_batch(const CountParams *__restrict__ jobs,
+                                                      const uint32_t *__restrict__ job_base,
+                                                      uint32_t n_jobs, uint32_t slots,
+                                                      uint32_t *err) {
+    const uint32_t e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (e >= slots) return;
+    uint32_t lo = 0, hi = n_jobs;  // last j with job_base[j] <= e
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (job_base[mid] <= e) lo = mid;
+        else hi = mid;
+    }
+    const CountParams &p = jobs[lo];
+    const uint32_t ci = e - job_base[lo];
+    if (ci < p.m && p.P > 0) stitch_one(p.tables, p.m, p.P, ci, p.out, p.redo, err);
+}
+
+cudaError_t launch_stitch_batch(const CountParams *jobs, const uint32_t *job_base,
+                                uint32_t n_jobs, uint32_t slots, uint32_t *err, cudaStream_t st) {
+    if (slots == 0 || n_jobs == 0) return cudaSuccess;
+    const uint32_t blocks = (uint32_t)(((uint64_t)slots * 32 + 255) / 256);
+    k_stitch_batch<<<blocks, 256, 0, st>>>(jobs, job_base, n_jobs, slots, err);
+    note_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_stitch(const uint4 *tables, uint32_t m, uint32_t P, uint32_t *out,

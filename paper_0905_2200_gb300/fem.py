@@ -52,10 +52,17 @@ class fem_level_stats(ctypes.Structure):
                 ("exact_segments", ctypes.c_uint32)]
 
 
+class fem_job(ctypes.Structure):
+    _fields_ = [("stream_id", ctypes.c_int32), ("len", ctypes.c_uint32), ("m", ctypes.c_uint32),
+                ("cands", ctypes.c_void_p), ("theta", ctypes.c_uint32),
+                ("exact_out", ctypes.c_void_p), ("survived_out", ctypes.c_void_p)]
+
+
 EXPORTS = ["fem_create", "fem_destroy", "fem_set_config", "fem_load_stream", "fem_free_stream",
            "fem_type_counts", "fem_count_candidates", "fem_count_two_pass",
            "fem_mine_levelwise", "fem_result_level", "fem_result_max_level", "fem_result_free",
-           "fem_last_mine_stats", "fem_strerror", "fem_kernel_launches", "fem_select_noalloc"]
+           "fem_last_mine_stats", "fem_strerror", "fem_kernel_launches", "fem_select_noalloc",
+           "fem_batch_create", "fem_batch_run", "fem_batch_destroy"]
 
 _lib = None
 
@@ -92,6 +99,10 @@ def load(path: str | None = None):
         "fem_strerror": (ctypes.c_char_p, [I]),
         "fem_kernel_launches": (u64, []),
         "fem_select_noalloc": (I, [vp, u32, u32, vp, vp, vp]),
+        "fem_batch_create": (I, [vp, ctypes.POINTER(fem_job), u32, ctypes.POINTER(fem_interval),
+                                 u32, vp, ctypes.POINTER(vp)]),
+        "fem_batch_run": (I, [vp, vp]),
+        "fem_batch_destroy": (I, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -298,6 +309,35 @@ def fem_select_noalloc(values, theta, idx_out, count_out, stream=None):
         raise ValueError("values, idx_out and count_out must be device tensors")
     _check(load().fem_select_noalloc(pv, int(values.shape[0]), int(theta), pi, pc,
                                      _stream_handle(stream)), "fem_select_noalloc")
+
+
+def fem_batch_create(ctx, jobs, intervals, stream=None):
+    """jobs: iterable of dicts with stream_id, len, cands ([m,16] uint8 CUDA tensor),
+    theta, exact_out (int32/uint32 CUDA tensor [m]), survived_out (uint8 CUDA tensor [m]).
+    Returns a batch handle; the tensors must outlive it."""
+    lib = load()
+    jobs = list(jobs)
+    arr = (fem_job * max(len(jobs), 1))()
+    for i, j in enumerate(jobs):
+        for key in ("cands", "exact_out", "survived_out"):
+            if not (_is_torch(j[key]) and j[key].is_cuda):
+                raise ValueError(f"job {i}: {key} must be a CUDA tensor")
+        arr[i] = fem_job(int(j["stream_id"]), int(j["len"]), int(j["cands"].shape[0]),
+                         j["cands"].data_ptr(), int(j["theta"]), j["exact_out"].data_ptr(),
+                         j["survived_out"].data_ptr())
+    iv, nI = _intervals(intervals)
+    h = ctypes.c_void_p()
+    _check(lib.fem_batch_create(ctx, arr, len(jobs), iv, nI, _stream_handle(stream),
+                                ctypes.byref(h)), "fem_batch_create")
+    return h
+
+
+def fem_batch_run(batch, stream=None):
+    _check(load().fem_batch_run(batch, _stream_handle(stream)), "fem_batch_run")
+
+
+def fem_batch_destroy(batch):
+    _check(load().fem_batch_destroy(batch), "fem_batch_destroy")
 
 
 def fem_kernel_launches() -> int:

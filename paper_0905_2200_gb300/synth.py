@@ -141,19 +141,48 @@ def large_stream(seed=0xFE04, n_candidates=100_000, duration_s=3600.0):
 
 
 def random_candidates(seed, m, n_types, lens, n_int, distinct=True):
-    """m random episodes: (len uint8[m], types uint8[m,8], ivl uint8[m,7])."""
+    """m random episodes: (len uint8[m], types uint8[m,8], ivl uint8[m,7]); lengths drawn
+    from `lens`, types distinct within an episode (unless distinct=False), interval
+    indices uniform."""
     rng = _rng(seed)
     L = rng.choice(np.asarray(lens), size=m).astype(np.uint8)
     E = np.zeros((m, LMAX), np.uint8)
     iv = np.zeros((m, LMAX - 1), np.uint8)
-    for c in range(m):
-        k = int(L[c])
+    for a in range(0, m, 65536):
+        b = min(m, a + 65536)
         if distinct:
-            E[c, :k] = rng.choice(n_types, size=k, replace=False)
+            pick = np.argsort(rng.random((b - a, n_types)), axis=1)[:, :LMAX]
         else:
-            E[c, :k] = rng.integers(0, n_types, size=k)
-        iv[c, : k - 1] = rng.integers(0, n_int, size=k - 1)
+            pick = rng.integers(0, n_types, size=(b - a, LMAX))
+        E[a:b, : pick.shape[1]] = pick
+        iv[a:b] = rng.integers(0, n_int, size=(b - a, LMAX - 1))
+    pos = np.arange(LMAX)[None, :]
+    E[pos >= L[:, None]] = 0
+    iv[pos[:, : LMAX - 1] >= (L[:, None] - 1)] = 0
     return L, E, iv
+
+
+def batched_recordings(seed=0xFE03, n_rec=256, t_range=(10.0, 600.0), m_range=(100, 20000),
+                       lens=(2, 3, 4, 5, 6, 7, 8)):
+    """Many recordings of uneven length with candidate sets of uneven size and length:
+    per recording T log-uniform in t_range s, K uniform in 16..64, per-type rates uniform
+    in [5, 50] Hz, 4 chains (lengths 4-6, 1-3 Hz, delays inside I_MS4 intervals); m
+    log-uniform in m_range candidates with lengths drawn from `lens`; threshold 5x the
+    chance count at the recording's mean rate and a 2 ms window."""
+    rng = _rng(seed)
+    recs = []
+    for r in range(n_rec):
+        T = float(np.exp(rng.uniform(np.log(t_range[0]), np.log(t_range[1]))))
+        K = int(rng.integers(16, 65))
+        rates = rng.uniform(5.0, 50.0, size=K)
+        ch = _chains(rng, 4, K, [4, 5, 6], len(I_MS4), 1.0, 3.0)
+        spec = [(tys, rate, [tuple(I_MS4[i]) for i in ivs]) for tys, ivs, rate in ch]
+        t, ty = poisson_stream(seed * 1000 + r, K, rates, T, chains=spec)
+        m = int(np.exp(rng.uniform(np.log(m_range[0]), np.log(m_range[1]))))
+        cands = random_candidates(seed * 1000 + r + 500_000, m, K, list(lens), len(I_MS4))
+        theta = chance_theta(float(rates.mean()), T, 0.002)
+        recs.append(dict(stream=Stream(ty, t, K, ch), candidates=cands, theta=theta))
+    return dict(name=f"batched_{n_rec}_recordings", recordings=recs, intervals=I_MS4.copy())
 
 
 def level2_candidates(frequent_types, n_intervals):
