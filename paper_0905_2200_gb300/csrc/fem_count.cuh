@@ -118,7 +118,11 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
     const uint32_t c_seg0 = seg * p.cps;
     const uint32_t c_end = min(c_seg0 + p.cps, p.n_chunks);
     const uint64_t L = (uint64_t)c_seg0 * CHUNK;
-    uint32_t X = 0, Xn = 0, c_w = c_seg0;
+    // X: start time of the window whose last-node events are the entry classes;
+    // X2 = X - W: processing starts there, so that every chain ending inside the
+    // window is seen and only window events that can complete an occurrence become
+    // classes (the serial machine's last completion before L is one of those).
+    uint32_t X = 0, X2 = 0, Xn = 0, c_w = c_seg0;
     bool last_seg = c_end >= p.n_chunks;
     if (MC) {
         uint64_t W = 0;
@@ -127,10 +131,11 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
         if (ok && seg > 0) {
             const uint32_t tL = p.cfirst[c_seg0];
             X = (uint64_t)tL >= W ? (uint32_t)(tL - W) : 0u;
+            X2 = (uint64_t)tL >= 2 * W ? (uint32_t)(tL - 2 * W) : 0u;
             uint32_t c = c_seg0;
-            if (X == 0) c = 0;
+            if (X2 == 0) c = 0;
             else
-                while (c > 0 && p.cfirst[c] >= X) --c;
+                while (c > 0 && p.cfirst[c] >= X2) --c;
             c_w = c;
         }
         if (!last_seg) {
@@ -165,6 +170,11 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
     uint32_t c_key[SC], c_start[SC], c_cnt[SC];
 #pragma unroll
     for (int j = 0; j < SC; ++j) c_key[j] = CLS_NONE, c_start[j] = 0, c_cnt[j] = 0;
+    // Class "none" is a fresh machine at the window start w: it sees chains whose
+    // first event is at index >= w, i.e. whose first node's time is >= X.  Until the
+    // first node-0 event at or after X its start is unknown and nothing is visible.
+    if (MC) c_start[0] = X == 0 ? 0u : 0xFFFFFFFFu;
+    bool c0_done = false, capable = false;
 
     uint2 *ring64 = reinterpret_cast<uint2 *>(ring_raw) + tid;
 
@@ -174,7 +184,8 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
             ++cnt;
         } else {
             const uint32_t inc = (uint64_t)gidx >= L ? 1u : 0u;
-            if (c_start[0] <= msv) c_start[0] = gidx + 1, c_cnt[0] += inc;
+            capable = true;
+            if (c_start[0] <= msv) c_start[0] = gidx + 1, c_cnt[0] += inc, c0_done = true;
             if (umask) {
 #pragma unroll
                 for (int j = 1; j < SC; ++j) {
@@ -240,6 +251,9 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
     // returns true when the event completed an occurrence (stop handling it).
     auto step = [&](auto kc, uint32_t tt, uint32_t gidx) -> bool {
         constexpr int k = decltype(kc)::value;
+        if constexpr (MC && k == 0) {
+            if (c_start[0] == 0xFFFFFFFFu && tt >= X) c_start[0] = gidx;
+        }
         if constexpr (N == 1) {
             complete(gidx, gidx);
             return true;
@@ -327,8 +341,8 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
             for (int k = 0; k < N; ++k) {
                 ptr[k] = off[ep.E[k]];
                 end[k] = off[ep.E[k] + 1];
-                if (MC && c == c_w && X > 0)
-                    while (ptr[k] < end[k] && ev[ptr[k]].x < X) ++ptr[k];
+                if (MC && c == c_w && X2 > 0)
+                    while (ptr[k] < end[k] && ev[ptr[k]].x < X2) ++ptr[k];
                 if (ptr[k] < end[k]) {
                     const uint2 e = ev[ptr[k]];
                     tv[k] = e.x;
@@ -345,6 +359,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                 if (mk == KEY_END) break;
                 const uint32_t gidx = (uint32_t)(cbase + mk);
                 const bool last_hit = key[N - 1] == mk;
+                capable = false;
                 bool done = false;
                 for_nodes_desc<N - 1>([&](auto kc) {
                     constexpr int k = decltype(kc)::value;
@@ -358,7 +373,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                         key[k] = ptr[k] < end[k] ? e.y : KEY_END;
                     }
                 });
-                if (MC && last_hit && (uint64_t)gidx < L) {
+                if (MC && last_hit && capable && (uint64_t)gidx < L) {
                     // entry class r = gidx: the serial machine's last completion was r
                     if (ns < (uint32_t)SC) {
 #pragma unroll
@@ -418,7 +433,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                 const uint32_t st = merged ? c_start[0] : c_start[q];
                 // the last completion (or the class's own event) is st - 1; it is
                 // handed on only if it lies in the next segment's window
-                uint32_t ex = st == 0 ? CLS_NONE : st - 1u;
+                uint32_t ex = (q == 0 && !c0_done) ? CLS_NONE : st - 1u;
                 if (ex != CLS_NONE && !last_seg && p.t[ex] < Xn) ex = CLS_NONE;
                 e = make_uint4(c_key[q], cntq, ex, 0);
             }
