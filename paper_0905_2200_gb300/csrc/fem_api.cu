@@ -312,6 +312,15 @@ void free_stream_buffers(StreamDev &s) {
 // ============================================================================ C ABI
 extern "C" {
 
+}  // extern "C"
+
+namespace fem {
+int fem_ctx_device(const fem_ctx *c) { return c->device; }
+int fem_ctx_sms(const fem_ctx *c) { return c->sm_count; }
+}  // namespace fem
+
+extern "C" {
+
 uint64_t fem_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 const char *fem_strerror(int s) {

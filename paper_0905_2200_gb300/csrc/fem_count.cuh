@@ -81,10 +81,13 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
     uint8_t *ring_raw = smem + 2 * SB + 128;
 
     const uint32_t ci = tile * T + tid;
+    // candidate count: fixed, or produced on the device by an earlier kernel
+    const uint32_t m_cur = p.m_dev ? *p.m_dev : p.m;
+    if (tile * T >= m_cur) return true;  // the whole block is past the end (uniform)
 
     // ---------------------------------------------------------------- episode
     EpRegs<N> ep;
-    bool ok = ci < p.m;
+    bool ok = ci < m_cur;
     if (ok) {
         const fem_episode rec = p.cands[p.gather ? p.gather[ci] : ci];
         ok = rec.len == N;
@@ -115,8 +118,14 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
     }
 
     // ---------------------------------------------------------------- segment and window
-    const uint32_t c_seg0 = seg * p.cps;
-    const uint32_t c_end = min(c_seg0 + p.cps, p.n_chunks);
+    // A ranged count (single segment) covers events [ev_begin, ev_end) only.
+    const uint32_t c_seg0 = p.ranged ? (uint32_t)(p.ev_begin / CHUNK) : seg * p.cps;
+    const uint32_t c_end = p.ranged ? (uint32_t)((p.ev_end + CHUNK - 1) / CHUNK)
+                                    : min(c_seg0 + p.cps, p.n_chunks);
+    const uint32_t lo_local = p.ranged ? (uint32_t)(p.ev_begin - (uint64_t)c_seg0 * CHUNK) : 0u;
+    const uint32_t hi_local = p.ranged && c_end > 0
+                                  ? (uint32_t)(p.ev_end - (uint64_t)(c_end - 1) * CHUNK)
+                                  : KEY_END;
     const uint64_t L = (uint64_t)c_seg0 * CHUNK;
     // X: start time of the window whose last-node events are the entry classes;
     // X2 = X - W: processing starts there, so that every chain ending inside the
@@ -309,6 +318,31 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
         }
     };
 
+    // ---------------------------------------------------------------- carried state
+    // (single segment only) count and machine state of a count resumed where an
+    // earlier call on the same episode stopped
+    uint32_t *stw = (!MC && p.state && ok) ? p.state + (uint64_t)ci * p.state_stride : nullptr;
+    if (!MC && stw) {
+        cnt = stw[0];
+        if constexpr (PASS == FEM_PASS_RELAXED) {
+#pragma unroll
+            for (int k = 0; k < NE; ++k) dl[k] = stw[1 + k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < NE; ++k) {
+                const uint32_t *w = stw + 1 + k * (1 + 2 * R);
+                const uint32_t nq = min(w[0], (uint32_t)R);
+                for (uint32_t i = 0; i < nq; ++i) slot(k, i) = make_uint2(w[1 + 2 * i], w[2 + 2 * i]);
+                head[k] = 0;
+                tail[k] = nq;
+                if (nq) {
+                    fx[k] = w[1], fy[k] = w[2];
+                    bx[k] = w[2 * nq - 1], by[k] = w[2 * nq];
+                }
+            }
+        }
+    }
+
     // ---------------------------------------------------------------- chunk pipeline
     const uint32_t chunk_ev_bytes = CHUNK * 8u;
     const uint32_t chunk_off_bytes = p.offs * 2u;
@@ -343,6 +377,8 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                 end[k] = off[ep.E[k] + 1];
                 if (MC && c == c_w && X2 > 0)
                     while (ptr[k] < end[k] && ev[ptr[k]].x < X2) ++ptr[k];
+                if (c == c_first && lo_local > 0)
+                    while (ptr[k] < end[k] && ev[ptr[k]].y < lo_local) ++ptr[k];
                 if (ptr[k] < end[k]) {
                     const uint2 e = ev[ptr[k]];
                     tv[k] = e.x;
@@ -352,11 +388,12 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                     tv[k] = 0;
                 }
             }
+            const uint32_t lim = c + 1 == c_end ? hi_local : KEY_END;
             for (;;) {
                 uint32_t mk = key[0];
 #pragma unroll
                 for (int k = 1; k < N; ++k) mk = min(mk, key[k]);
-                if (mk == KEY_END) break;
+                if (mk >= lim) break;
                 const uint32_t gidx = (uint32_t)(cbase + mk);
                 const bool last_hit = key[N - 1] == mk;
                 capable = false;
@@ -415,10 +452,29 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
     q = q0 + (c_end > c_first ? c_end - c_first : 0u);
 
     // ---------------------------------------------------------------- results
-    if (ci >= p.m) return true;
+    if (ci >= m_cur) return true;
     if (overflow) {
         atomicOr(p.err, ERR_RING);
         p.redo[ci] = 1;
+    }
+    if (!MC && stw) {
+        stw[0] = cnt;
+        if constexpr (PASS == FEM_PASS_RELAXED) {
+#pragma unroll
+            for (int k = 0; k < NE; ++k) stw[1 + k] = dl[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < NE; ++k) {
+                uint32_t *w = stw + 1 + k * (1 + 2 * R);
+                const uint32_t nq = tail[k] - head[k];
+                w[0] = nq;
+                for (uint32_t i = 0; i < nq; ++i) {
+                    const uint2 e = slot(k, head[k] + i);
+                    w[1 + 2 * i] = e.x;
+                    w[2 + 2 * i] = e.y;
+                }
+            }
+        }
     }
     if (!MC) {
         p.out[ci] = ok ? cnt : 0u;

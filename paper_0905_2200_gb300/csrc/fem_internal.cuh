@@ -75,6 +75,12 @@ struct CountParams {
     uint4 *tables;              // [P][m][S_MAX] (key, count, exit, 0) when P > 1
     uint8_t *redo;              // [m] set to 1 when a candidate must be recounted
     uint32_t *err;
+    // optional (single segment only):
+    const uint32_t *m_dev;      // candidate count read on the device (overrides m)
+    uint32_t ranged;            // count events [ev_begin, ev_end) only
+    uint64_t ev_begin, ev_end;
+    uint32_t *state;            // per-candidate carried state (count, machine), in and out
+    uint32_t state_stride;      // words per candidate: 1 + (N-1) relaxed, 1 + (N-1)(1 + 2R) exact
 };
 
 // Per-job output arrays of a batch (device pointers owned by the caller).
@@ -149,6 +155,13 @@ void note_launch(uint32_t k = 1);
 
 // fem_stream.cu
 cudaError_t launch_load_stream(StreamDev &s, cudaStream_t st, uint32_t *d_err);
+// regroup chunks [c0, c1) of a stream that grew to s.n events (type histogram untouched)
+cudaError_t launch_bucket_chunks(StreamDev &s, uint32_t c0, uint32_t c1, cudaStream_t st);
+// dst[idx[i]] = src[i] and flags[idx[i]] = 1 for i < *m_dev (grid sized for m_max)
+cudaError_t launch_scatter_dev(const uint32_t *src, const uint32_t *idx, const uint32_t *m_dev,
+                               uint32_t m_max, uint32_t *dst, uint8_t *flags, cudaStream_t st);
+int fem_ctx_device(const fem_ctx *c);
+int fem_ctx_sms(const fem_ctx *c);
 // fem_count.cu
 cudaError_t launch_count(int N, int pass, bool mc, uint32_t ring_cap, uint32_t threads,
                          const CountParams &p, cudaStream_t st);

@@ -396,6 +396,25 @@ cudaError_t launch_scatter_u32(const uint32_t *src, const uint32_t *idx, uint32_
     return cudaGetLastError();
 }
 
+__global__ void k_scatter_dev(const uint32_t *__restrict__ src, const uint32_t *__restrict__ idx,
+                              const uint32_t *__restrict__ m_dev, uint32_t m_max,
+                              uint32_t *__restrict__ dst, uint8_t *__restrict__ flags) {
+    const uint32_t m = min(*m_dev, m_max);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        dst[idx[i]] = src[i];
+        if (flags) flags[idx[i]] = 1;
+    }
+}
+
+cudaError_t launch_scatter_dev(const uint32_t *src, const uint32_t *idx, const uint32_t *m_dev,
+                               uint32_t m_max, uint32_t *dst, uint8_t *flags, cudaStream_t st) {
+    if (m_max == 0) return cudaSuccess;
+    const uint32_t blocks = (m_max + 255) / 256 < 2048 ? (m_max + 255) / 256 : 2048;
+    k_scatter_dev<<<blocks, 256, 0, st>>>(src, idx, m_dev, m_max, dst, flags);
+    note_launch();
+    return cudaGetLastError();
+}
+
 __global__ void k_fill_flags(const uint32_t *__restrict__ idx, uint32_t m,
                              uint8_t *__restrict__ flags) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -31,11 +31,11 @@ __global__ void __launch_bounds__(256) k_bucket(const uint32_t *__restrict__ t,
                                                 uint2 *__restrict__ bev,
                                                 uint16_t *__restrict__ boff,
                                                 uint32_t *__restrict__ cfirst,
-                                                uint32_t *__restrict__ hist) {
+                                                uint32_t *__restrict__ hist, uint32_t c0) {
     __shared__ uint16_t wcnt[8][256];
     __shared__ uint32_t tbase[257];
     __shared__ uint32_t wsum[8];
-    const uint32_t c = blockIdx.x;
+    const uint32_t c = c0 + blockIdx.x;
     const uint64_t base = (uint64_t)c * CHUNK;
     const uint32_t cnt = (uint32_t)min((uint64_t)CHUNK, n - base);
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) k_bucket(const uint32_t *__restrict__ t,
     for (uint32_t ww = 0; ww < w; ++ww) woff += wsum[ww];
     tbase[tv] = woff + inc - tot;
     if (tv == 255) tbase[256] = woff + inc;
-    if (tv < K && tot) atomicAdd(&hist[tv], tot);
+    if (hist && tv < K && tot) atomicAdd(&hist[tv], tot);
     __syncthreads();
 
 #pragma unroll
@@ -115,7 +115,15 @@ cudaError_t launch_load_stream(StreamDev &s, cudaStream_t st, uint32_t *d_err) {
     e = cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * s.K, st);
     if (e != cudaSuccess) return e;
     k_bucket<<<s.n_chunks, 256, 0, st>>>(s.t, s.type, s.n, s.K, s.offs, s.n_chunks, s.bev, s.boff,
-                                         s.cfirst, s.hist);
+                                         s.cfirst, s.hist, 0);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_chunks(StreamDev &s, uint32_t c0, uint32_t c1, cudaStream_t st) {
+    if (c1 <= c0) return cudaSuccess;
+    k_bucket<<<c1 - c0, 256, 0, st>>>(s.t, s.type, s.n, s.K, s.offs, s.n_chunks, s.bev, s.boff,
+                                      s.cfirst, nullptr, c0);
     note_launch();
     return cudaGetLastError();
 }

@@ -58,11 +58,21 @@ class fem_job(ctypes.Structure):
                 ("exact_out", ctypes.c_void_p), ("survived_out", ctypes.c_void_p)]
 
 
+class fem_server_config(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_uint32),
+                ("n_lanes", ctypes.c_uint32)]
+
+
+REQ_ONESHOT, REQ_STANDING = 0, 1
+
 EXPORTS = ["fem_create", "fem_destroy", "fem_set_config", "fem_load_stream", "fem_free_stream",
            "fem_type_counts", "fem_count_candidates", "fem_count_two_pass",
            "fem_mine_levelwise", "fem_result_level", "fem_result_max_level", "fem_result_free",
            "fem_last_mine_stats", "fem_strerror", "fem_kernel_launches", "fem_select_noalloc",
-           "fem_batch_create", "fem_batch_run", "fem_batch_destroy"]
+           "fem_batch_create", "fem_batch_run", "fem_batch_destroy",
+           "fem_server_create", "fem_server_destroy", "fem_server_open_stream",
+           "fem_server_append", "fem_server_submit", "fem_server_poll", "fem_server_result",
+           "fem_server_release", "fem_server_drain"]
 
 _lib = None
 
@@ -103,6 +113,16 @@ def load(path: str | None = None):
                                  u32, vp, ctypes.POINTER(vp)]),
         "fem_batch_run": (I, [vp, vp]),
         "fem_batch_destroy": (I, [vp]),
+        "fem_server_create": (I, [vp, ctypes.POINTER(fem_server_config), ctypes.POINTER(vp)]),
+        "fem_server_destroy": (I, [vp]),
+        "fem_server_open_stream": (I, [vp, u32, u64, ctypes.POINTER(i32)]),
+        "fem_server_append": (I, [vp, i32, vp, vp, u32]),
+        "fem_server_submit": (I, [vp, i32, vp, u32, ctypes.POINTER(fem_interval), u32, u32, I, u32,
+                                  ctypes.POINTER(u64)]),
+        "fem_server_poll": (I, [vp, ctypes.POINTER(u64), u32, ctypes.POINTER(u32)]),
+        "fem_server_result": (I, [vp, u64, vp, vp, ctypes.POINTER(u64)]),
+        "fem_server_release": (I, [vp, u64]),
+        "fem_server_drain": (I, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -338,6 +358,70 @@ def fem_batch_run(batch, stream=None):
 
 def fem_batch_destroy(batch):
     _check(load().fem_batch_destroy(batch), "fem_batch_destroy")
+
+
+def fem_server_create(ctx, mem_budget_bytes=0, max_active=0, n_lanes=0):
+    cfg = fem_server_config(int(mem_budget_bytes), int(max_active), int(n_lanes))
+    h = ctypes.c_void_p()
+    _check(load().fem_server_create(ctx, ctypes.byref(cfg), ctypes.byref(h)), "fem_server_create")
+    return h
+
+
+def fem_server_destroy(srv):
+    _check(load().fem_server_destroy(srv), "fem_server_destroy")
+
+
+def fem_server_open_stream(srv, n_types, capacity_events) -> int:
+    sid = ctypes.c_int32()
+    _check(load().fem_server_open_stream(srv, int(n_types), int(capacity_events),
+                                         ctypes.byref(sid)), "fem_server_open_stream")
+    return sid.value
+
+
+def fem_server_append(srv, sid, types, t_us):
+    types = np.ascontiguousarray(types, dtype=np.uint8)
+    t_us = np.ascontiguousarray(t_us, dtype=np.uint32)
+    if types.shape != t_us.shape:
+        raise ValueError("types and t_us differ in length")
+    _check(load().fem_server_append(srv, int(sid), types.ctypes.data_as(ctypes.c_void_p),
+                                    t_us.ctypes.data_as(ctypes.c_void_p), int(types.shape[0])),
+           "fem_server_append")
+
+
+def fem_server_submit(srv, sid, cands, intervals, theta, mode=REQ_ONESHOT, window_us=0):
+    """Returns the request id; raises FemError (status -6, FEM_EADMIT) if not admitted."""
+    cands = np.ascontiguousarray(cands, dtype=np.uint8).reshape(-1, 16)
+    iv, nI = _intervals(intervals)
+    rid = ctypes.c_uint64()
+    _check(load().fem_server_submit(srv, int(sid), cands.ctypes.data_as(ctypes.c_void_p),
+                                    int(cands.shape[0]), iv, nI, int(theta), int(mode),
+                                    int(window_us), ctypes.byref(rid)), "fem_server_submit")
+    return rid.value
+
+
+def fem_server_poll(srv, cap=4096):
+    ids = (ctypes.c_uint64 * cap)()
+    n = ctypes.c_uint32()
+    _check(load().fem_server_poll(srv, ids, cap, ctypes.byref(n)), "fem_server_poll")
+    return [int(ids[i]) for i in range(n.value)]
+
+
+def fem_server_result(srv, rid, m):
+    """(counts uint32[m], flags uint8[m], events covered, status)."""
+    counts = np.zeros(m, np.uint32)
+    flags = np.zeros(m, np.uint8)
+    ev = ctypes.c_uint64()
+    rc = load().fem_server_result(srv, int(rid), counts.ctypes.data_as(ctypes.c_void_p),
+                                  flags.ctypes.data_as(ctypes.c_void_p), ctypes.byref(ev))
+    return counts, flags, int(ev.value), int(rc)
+
+
+def fem_server_release(srv, rid):
+    _check(load().fem_server_release(srv, int(rid)), "fem_server_release")
+
+
+def fem_server_drain(srv):
+    _check(load().fem_server_drain(srv), "fem_server_drain")
 
 
 def fem_kernel_launches() -> int:
