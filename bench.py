@@ -406,6 +406,148 @@ def run_batched(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+# --------------------------------------------------------------------------- serving form
+def run_serving(args, rank, world, local):
+    """32 live streams appended in 100 ms chunks at real-time pace after a 60 s
+    resident history; Poisson-arriving requests (one-shot over the last 60 s, or
+    standing) admitted by memory and slots, retried while they wait.  Reports p50/p99
+    latency (one-shot: arrival -> result; standing: chunk append -> updated counts)
+    beside throughput."""
+    import torch
+
+    from paper_0905_2200_gb300 import build as fembuild
+    from paper_0905_2200_gb300 import fem, synth
+
+    fembuild.build()
+    torch.cuda.set_device(local)
+    hist_s, sess, tick = 60.0, args.session_s, 0.1
+    streams = synth.serving_streams(seed=0xFE05 + rank, n_streams=32, duration_s=hist_s + sess)
+    types_of = [x["stream"].n_types for x in streams]
+    reqs = synth.serving_requests(0xFE05 + 17 * rank, args.req_rate, sess, 32, types_of)
+    I = synth.I_MS4
+    for r in reqs:
+        L, E, iv = synth.random_candidates(r["seed"], r["m"], r["K"], list(r["lens"]), len(I))
+        r["rec"] = fem.pack_episodes(L, E, iv)
+        rate = streams[r["stream"]]["rate"]
+        r["theta"] = synth.chance_theta(rate, 60.0, 0.002)
+    ctx = fem.fem_create(local)
+    srv = fem.fem_server_create(ctx, mem_budget_bytes=args.serve_budget_gb << 30, max_active=64,
+                                n_lanes=8)
+    sids, edges = [], []
+    for x in streams:
+        s = x["stream"]
+        sids.append(fem.fem_server_open_stream(srv, s.n_types, s.n + 16))
+        b = np.searchsorted(s.t, np.arange(0, hist_s + sess + tick, tick) * 1e6)
+        edges.append(b)
+        h = int(np.searchsorted(s.t, hist_s * 1e6))
+        fem.fem_server_append(srv, sids[-1], s.types[:h], s.t[:h])
+    fem.fem_server_drain(srv)
+    n_fed = [int(np.searchsorted(x["stream"].t, hist_s * 1e6)) for x in streams]
+    append_log = [[(n_fed[i], 0.0)] for i in range(32)]  # (events after append, wall time)
+    pending, live = [], {}
+    lat_one, lat_stand, units = [], [], 0.0
+    rejected_final, admitted, retries = 0, 0, 0
+    nxt = 0
+    k0 = int(round(hist_s / tick))
+    n_ticks = int(round(sess / tick))
+    t0 = time.perf_counter()
+
+    def poll(now):
+        nonlocal units
+        for rid in fem.fem_server_poll(srv):
+            info = live[rid]
+            c, f, ev, st = fem.fem_server_result(srv, rid, info["m"])
+            if info["standing"]:
+                end = info["first"] + ev
+                if ev and end > info["seen"]:
+                    log = append_log[info["stream"]]
+                    w = next((wt for n, wt in log if n >= end), log[-1][1])
+                    lat_stand.append(now - w)
+                    units += float(info["m"]) * (end - info["seen"])
+                    info["seen"] = end
+            else:
+                lat_one.append(now - info["arrival"])
+                units += float(info["m"]) * ev
+                fem.fem_server_release(srv, rid)
+
+    def admit_pending():
+        nonlocal pending, nxt, retries, rejected_final, admitted
+        now = time.perf_counter()
+        while nxt < len(reqs) and t0 + reqs[nxt]["t"] <= now:
+            r = reqs[nxt]
+            r["arrival"] = t0 + r["t"]
+            pending.append(r)
+            nxt += 1
+        still = []
+        for r in pending:
+            mode = fem.REQ_STANDING if r["standing"] else fem.REQ_ONESHOT
+            try:
+                rid = fem.fem_server_submit(srv, sids[r["stream"]], r["rec"], I, r["theta"], mode,
+                                            60_000_000)
+            except fem.FemError as e:
+                if e.status != -6:
+                    raise
+                retries += 1
+                if time.perf_counter() - r["arrival"] > 5.0:
+                    rejected_final += 1
+                else:
+                    still.append(r)
+                continue
+            admitted += 1
+            live[rid] = dict(m=r["m"], standing=r["standing"], arrival=r["arrival"],
+                             stream=r["stream"], first=n_fed[r["stream"]], seen=n_fed[r["stream"]])
+        pending = still
+
+    for k in range(n_ticks):
+        due = t0 + k * tick
+        while time.perf_counter() < due:
+            admit_pending()
+            poll(time.perf_counter())
+            time.sleep(0.0002)
+        now = time.perf_counter()
+        for i in range(32):
+            a, b = int(edges[i][k0 + k]), int(edges[i][k0 + k + 1])
+            if b > a:
+                s = streams[i]["stream"]
+                fem.fem_server_append(srv, sids[i], s.types[a:b], s.t[a:b])
+                n_fed[i] = b
+                append_log[i].append((b, time.perf_counter()))
+        admit_pending()
+        poll(time.perf_counter())
+    while time.perf_counter() < t0 + n_ticks * tick:
+        admit_pending()
+        poll(time.perf_counter())
+    wall = time.perf_counter() - t0
+    fem.fem_server_drain(srv)
+    poll(time.perf_counter())
+    fem.fem_server_destroy(srv)
+    fem.fem_destroy(ctx)
+
+    def pct(xs, q):
+        return float(np.percentile(np.asarray(xs) * 1e3, q)) if xs else None
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": units / wall, "unit": UNIT, "n_gpus": world,
+        "steps": n_ticks, "warmup": 0, "ms_per_step": wall * 1e3 / n_ticks,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded Poisson spike trains with embedded cascades)",
+        "config": {"workload": "serving_32_streams", "history_s": hist_s, "session_s": sess,
+                   "chunk_ms": tick * 1e3, "request_rate_per_s": args.req_rate,
+                   "requests": len(reqs), "m_range": [1000, 50000], "lengths": [2, 6],
+                   "standing_fraction": 0.1, "window_s": 60,
+                   "budget_gb": args.serve_budget_gb},
+        "serving": {"oneshot_p50_ms": pct(lat_one, 50), "oneshot_p99_ms": pct(lat_one, 99),
+                    "standing_update_p50_ms": pct(lat_stand, 50),
+                    "standing_update_p99_ms": pct(lat_stand, 99),
+                    "oneshot_done": len(lat_one), "standing_updates": len(lat_stand),
+                    "admitted": admitted, "admission_retries": retries,
+                    "rejected_after_5s": rejected_final},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------------------------- reference arm
 def run_reference(args, rank, world, local):
     if rank != 0:
@@ -455,8 +597,11 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["single_recording", "batched"],
+    ap.add_argument("--workload", choices=["single_recording", "batched", "serving"],
                     default="single_recording")
+    ap.add_argument("--session-s", type=float, default=20.0)
+    ap.add_argument("--req-rate", type=float, default=10.0)
+    ap.add_argument("--serve-budget-gb", type=int, default=16)
     ap.add_argument("--recordings", type=int, default=256)
     args = ap.parse_args(argv)
     if args.warmup < 3:
@@ -467,6 +612,8 @@ def main(argv=None):
             run_reference(args, rank, world, local)
         elif args.workload == "batched":
             run_batched(args, rank, world, local)
+        elif args.workload == "serving":
+            run_serving(args, rank, world, local)
         else:
             run_ours(args, rank, world, local)
     finally:

@@ -208,3 +208,36 @@ def tiny_stream(seed, n, n_types, max_gap_us, tie_prob=0.2):
     t = np.cumsum(gaps).astype(np.uint32)
     ty = rng.integers(0, n_types, size=n).astype(np.uint8)
     return ty, t
+
+
+def serving_streams(seed=0xFE05, n_streams=32, duration_s=90.0):
+    """Simulated live recordings: per stream K uniform in 16..128 types, per-type rate
+    uniform in [10, 100] Hz shared by the stream's types, 4 chains (lengths 4-6, 1-3 Hz,
+    delays inside I_MS4 intervals)."""
+    rng = _rng(seed)
+    out = []
+    for k in range(n_streams):
+        K = int(rng.integers(16, 129))
+        rate = float(rng.uniform(10.0, 100.0))
+        ch = _chains(rng, 4, K, [4, 5, 6], len(I_MS4), 1.0, 3.0)
+        spec = [(tys, r, [tuple(I_MS4[i]) for i in ivs]) for tys, ivs, r in ch]
+        t, ty = poisson_stream(seed * 1000 + k, K, rate, duration_s, chains=spec)
+        out.append(dict(stream=Stream(ty, t, K, ch), rate=rate))
+    return out
+
+
+def serving_requests(seed, rate_per_s, duration_s, n_streams, stream_types, m_range=(1000, 50000),
+                     lens=(2, 3, 4, 5, 6), standing_frac=0.1):
+    """Poisson request arrivals: (arrival s, stream, mode, candidate records seed, m)."""
+    rng = _rng(seed)
+    n = rng.poisson(rate_per_s * duration_s)
+    arr = np.sort(rng.random(n) * duration_s)
+    reqs = []
+    for a in arr:
+        sidx = int(rng.integers(0, n_streams))
+        m = int(np.exp(rng.uniform(np.log(m_range[0]), np.log(m_range[1]))))
+        standing = bool(rng.random() < standing_frac)
+        reqs.append(dict(t=float(a), stream=sidx, m=m, standing=standing,
+                         seed=int(rng.integers(0, 2**31)), K=stream_types[sidx], lens=lens))
+    return reqs
+
