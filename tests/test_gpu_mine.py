@@ -111,3 +111,36 @@ def test_single_recording_mining_sampled(ctx, single_recording):
     want = oracle.count_batch(s.types, s.t, L[pick], E[pick], iv[pick], cfg["intervals"],
                               oracle.EXACT)
     assert np.all(want < theta)
+
+
+def test_large_stream_two_pass_sampled(ctx):
+    """One hour at 50 Hz x 64 types (11.5M events), 100k candidates: Algorithm 4 on the
+    device (autotuned mapping and one segment per chunk agree); 24 sampled candidates
+    checked against the oracle, Theorem 5.1 on all."""
+    torch = pytest.importorskip("torch")
+    cfg = synth.large_stream()
+    s = cfg["stream"]
+    I, theta = cfg["intervals"], cfg["theta"]
+    L, E, iv = cfg["candidates"]
+    sid = fem.fem_load_stream(ctx, s.types, s.t, s.n_types)
+    rec = torch.from_numpy(fem.pack_episodes(L, E, iv)).cuda()
+    rel = torch.zeros(len(L), dtype=torch.int32, device="cuda")
+    fem.fem_count_candidates(ctx, sid, rec, I, fem.PASS_RELAXED, out=rel)
+    ex, sv = fem.fem_count_two_pass(ctx, sid, rec.cpu().numpy(), I, theta)
+    fem.fem_set_config(ctx, segments=(s.n + 2047) // 2048)
+    ex2, sv2 = fem.fem_count_two_pass(ctx, sid, rec.cpu().numpy(), I, theta)
+    assert_counts_equal(ex2, ex, "one segment per chunk")
+    assert_counts_equal(sv2, sv, "one segment per chunk survived")
+    rel = rel.cpu().numpy().view(np.uint32)
+    assert np.all((rel >= theta) == (sv != 0))
+    rng = np.random.default_rng(3)
+    surv = np.nonzero(sv)[0]
+    pick = np.concatenate([rng.choice(len(L), 20, replace=False), surv[:4]]).astype(np.int64)
+    want_r = oracle.count_batch(s.types, s.t, L[pick], E[pick], iv[pick], I, oracle.RELAXED)
+    want_e = oracle.count_batch(s.types, s.t, L[pick], E[pick], iv[pick], I, oracle.EXACT)
+    assert_counts_equal(rel[pick], want_r, "sampled relaxed")
+    assert np.all(want_r >= want_e)
+    for j, c in enumerate(pick):
+        if sv[c]:
+            assert ex[c] == want_e[j]
+    fem.fem_free_stream(ctx, sid)
