@@ -88,6 +88,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
     // ---------------------------------------------------------------- episode
     EpRegs<N> ep;
     bool ok = ci < m_cur;
+    bool distinct = true;  // no type repeats: exactly one node matches any event
     if (ok) {
         const fem_episode rec = p.cands[p.gather ? p.gather[ci] : ci];
         ok = rec.len == N;
@@ -108,12 +109,11 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                 ep.hi[k] = b.y;
             }
         }
-        if (MC) {
 #pragma unroll
-            for (int a = 0; a < N; ++a)
+        for (int a = 0; a < N; ++a)
 #pragma unroll
-                for (int b = a + 1; b < N; ++b) ok = ok && ep.E[a] != ep.E[b];
-        }
+            for (int b = a + 1; b < N; ++b) distinct = distinct && ep.E[a] != ep.E[b];
+        if (MC) ok = ok && distinct;
         if (!ok) atomicOr(p.err, ERR_BADEP);
     }
 
@@ -318,6 +318,67 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
         }
     };
 
+    // The same machine step for the common case -- distinct types, event inside the
+    // segment proper, every entry class merged into class "none" -- with the class
+    // bookkeeping reduced to class "none" alone.
+    auto step_lean = [&](auto kc, uint32_t tt, uint32_t gidx) {
+        constexpr int k = decltype(kc)::value;
+        auto done_lean = [&](uint32_t msv) {
+            if constexpr (MC) {
+                if (c_start[0] <= msv) c_start[0] = gidx + 1, ++c_cnt[0], c0_done = true;
+            } else {
+                ++cnt;
+            }
+        };
+        if constexpr (N == 1) {
+            done_lean(gidx);
+        } else if constexpr (PASS == FEM_PASS_RELAXED) {
+            if constexpr (k == 0) {
+                dl[0] = tt + ep.hi[0] + 1u;
+                if (MC) ms[0] = gidx;
+            } else if constexpr (k == N - 1) {
+                if (tt < dl[k - 1]) {
+                    done_lean(MC ? ms[k - 1] : 0u);
+                    if (!MC) {
+#pragma unroll
+                        for (int q = 0; q < NE; ++q) dl[q] = 0;
+                    }
+                }
+            } else {
+                if (tt < dl[k - 1]) {
+                    dl[k] = tt + ep.hi[k] + 1u;
+                    if (MC) ms[k] = ms[k - 1];
+                }
+            }
+        } else {
+            if constexpr (k == 0) {
+                push(0, tt, gidx);
+            } else {
+                constexpr int q = k - 1;
+                pop_dead(q, tt);
+                if (head[q] != tail[q] && tt - fx[q] > ep.lo[q]) {
+                    uint32_t msv = fy[q];
+                    if (MC) {
+                        for (uint32_t i = head[q] + 1u; i != tail[q]; ++i) {
+                            const uint2 e = slot(q, i);
+                            if (!(tt - e.x > ep.lo[q])) break;
+                            msv = e.y;
+                        }
+                    }
+                    if constexpr (k == N - 1) {
+                        done_lean(msv);
+                        if (!MC) {
+#pragma unroll
+                            for (int r = 0; r < NE; ++r) head[r] = tail[r];
+                        }
+                    } else {
+                        push(k, tt, msv);
+                    }
+                }
+            }
+        }
+    };
+
     // ---------------------------------------------------------------- carried state
     // (single segment only) count and machine state of a count resumed where an
     // earlier call on the same episode stopped
@@ -389,6 +450,27 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                 }
             }
             const uint32_t lim = c + 1 == c_end ? hi_local : KEY_END;
+            const bool lean =
+                distinct && (!MC || (c >= c_seg0 && umask == 0 && c_start[0] != 0xFFFFFFFFu));
+            if (lean) {
+                for (;;) {
+                    uint32_t mk = key[0];
+#pragma unroll
+                    for (int k = 1; k < N; ++k) mk = min(mk, key[k]);
+                    if (mk >= lim) break;
+                    const uint32_t gidx = (uint32_t)(cbase + mk);
+                    for_nodes_desc<N - 1>([&](auto kc) {
+                        constexpr int k = decltype(kc)::value;
+                        if (key[k] == mk) {
+                            step_lean(kc, tv[k], gidx);
+                            ++ptr[k];
+                            const uint2 e = ev[ptr[k]];
+                            tv[k] = e.x;
+                            key[k] = ptr[k] < end[k] ? e.y : KEY_END;
+                        }
+                    });
+                }
+            } else
             for (;;) {
                 uint32_t mk = key[0];
 #pragma unroll
