@@ -5,6 +5,8 @@
 // allocates device memory, launches, and copies results.
 #include <algorithm>
 #include <atomic>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -150,7 +152,7 @@ uint32_t choose_threads(fem_ctx *c, int N, int pass, bool mc, uint32_t R, uint32
     if (c->cfg.threads_per_block) return c->cfg.threads_per_block;
     for (uint32_t T : {256u, 128u, 64u, 32u}) {
         if (T > 32 && m <= T / 2) continue;  // few episodes: small blocks, more of them
-        if (T == 256 && (N > 3 || (pass == FEM_PASS_EXACT && mc))) continue;  // register budget
+        if (T == 256 && N > 3) continue;  // register budget
         if (count_smem_bytes(N, pass, mc, R, T, offs) <= 80 * 1024) return T;
     }
     for (uint32_t T : {32u, 16u, 8u}) {
@@ -192,7 +194,7 @@ int count_pass(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const u
 
     uint32_t P = choose_segments(c, s, m, distinct);
     uint32_t R = 1;
-    if (pass == FEM_PASS_EXACT) R = c->cfg.ring_capacity ? c->cfg.ring_capacity : (P > 1 ? 16 : 8);
+    if (pass == FEM_PASS_EXACT) R = c->cfg.ring_capacity ? c->cfg.ring_capacity : 8;
     if (P > 1 && pass == FEM_PASS_EXACT && R > 32) R = 32;
     if (!count_config_supported(N, pass, P > 1, R)) return FEM_EINVAL;
     const uint32_t cps = P > 1 ? (s.n_chunks + P - 1) / P : std::max<uint32_t>(s.n_chunks, 1);
@@ -217,7 +219,7 @@ int count_pass(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const u
         cudaEventElapsedTime(&info->ms_stitch, c->kev[1], c->kev[2]);
     }
     RET(err_status(e));
-    if (!(e & (ERR_RING | ERR_TABLE))) return FEM_OK;
+    if (!(e & (ERR_RING | ERR_TABLE | ERR_CLASS))) return FEM_OK;
 
     // Recount the flagged episodes with one segment and larger rings.
     uint32_t *ridx, *rg, *rout, *scratch;
@@ -226,30 +228,49 @@ int count_pass(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const u
     CK(launch_compact(nullptr, redo, 0, m, ridx, c->d_small + W_COUNT2, scratch, st));
     uint32_t r;
     RET(read_words(c, c->d_small + W_COUNT2, 1, &r, st));
+    if (std::getenv("FEM_DEBUG"))
+        std::fprintf(stderr, "fem: pass %d N=%d m=%u P=%u R=%u: %u episodes recounted (err %#x)\n",
+                     pass, N, m, P, R, r, e);
     if (r == 0) return FEM_OK;
     RET(dbuf(c, "redo_gather", r, &rg));
     RET(dbuf(c, "redo_out", r, &rout));
     CK(launch_compose_idx(gather, ridx, r, rg, st));
-    const uint32_t caps[] = {16, 32, 128};
-    for (uint32_t R2 : caps) {
-        if (pass == FEM_PASS_EXACT && R2 <= R && R2 != 128) continue;
-        if (pass == FEM_PASS_RELAXED && R2 != 16) continue;
+    // First retry: the flagged episodes alone, one chunk per segment (short items, so
+    // the retry costs about one chunk of work) with the largest segmented rings.
+    // Last resort: one segment per episode with the largest rings.
+    struct Try {
+        bool mc;
+        uint32_t R;
+    };
+    const Try tries[] = {{true, 32u}, {false, 32u}, {false, 128u}};
+    for (const Try &tr : tries) {
+        if (tr.mc && !distinct) continue;
         CK(cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), st));
         CountParams q = p;
         q.gather = rg;
         q.m = r;
         q.out = rout;
-        q.P = 1;
-        q.cps = std::max<uint32_t>(s.n_chunks, 1);
-        q.tables = nullptr;
         RET(dbuf(c, "redo2", r, &q.redo));
         CK(cudaMemsetAsync(q.redo, 0, r, st));
-        const uint32_t Rq = pass == FEM_PASS_EXACT ? R2 : 1;
-        const uint32_t T2 = choose_threads(c, N, pass, false, Rq, s.offs, r);
-        CK(launch_count(N, pass, false, Rq, T2, q, st));
+        const uint32_t Rq = pass == FEM_PASS_EXACT ? tr.R : 1;
+        if (tr.mc && s.n_chunks > 1) {
+            q.P = s.n_chunks;
+            q.cps = 1;
+            RET(dbuf(c, "redo_tables", (size_t)q.P * r * S_MAX, &q.tables));
+        } else {
+            q.P = 1;
+            q.cps = std::max<uint32_t>(s.n_chunks, 1);
+            q.tables = nullptr;
+        }
+        const bool mc2 = q.P > 1;
+        const uint32_t T2 = choose_threads(c, N, pass, mc2, Rq, s.offs, r);
+        CK(launch_count(N, pass, mc2, Rq, T2, q, st));
+        if (mc2) CK(launch_stitch(q.tables, r, q.P, rout, q.redo, c->d_err, st));
         RET(read_err(c, st, &e));
         RET(err_status(e));
-        if (!(e & ERR_RING)) {
+        if (std::getenv("FEM_DEBUG"))
+            std::fprintf(stderr, "fem:   retry P=%u R=%u: err %#x\n", q.P, Rq, e);
+        if (!(e & (ERR_RING | ERR_TABLE | ERR_CLASS))) {
             CK(launch_scatter_u32(rout, ridx, r, out, st));
             return FEM_OK;
         }
@@ -1041,7 +1062,7 @@ int fem_batch_run(fem_batch *b, void *cuda_stream) {
     uint32_t e;
     RET(read_err(c, st, &e));
     RET(err_status(e));
-    if (!(e & (ERR_RING | ERR_TABLE))) return FEM_OK;
+    if (!(e & (ERR_RING | ERR_TABLE | ERR_CLASS))) return FEM_OK;
     // A capacity guard tripped somewhere: recount the affected jobs one at a time
     // with the single-recording path, which widens rings as needed.
     std::vector<fem_interval> I(b->nI);

@@ -161,7 +161,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
 
     // ---------------------------------------------------------------- machine state
     uint32_t cnt = 0;
-    bool overflow = false;
+    bool overflow = false, class_overflow = false;
     // relaxed: deadline s + hi + 1 of the latest admitted time per node (0 = unset)
     // and, segmented, the start annotation of that slot
     uint32_t dl[NE], ms[NE];
@@ -175,7 +175,10 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
     // event as class 0 is identical to it from then on: it is merged (its bit in
     // umask cleared, c_cnt[j] holding its count minus class 0's) and no longer updated.
     constexpr int SC = MC ? S_MAX : 1;
-    uint32_t ns = 1, umask = 0;
+    // used: slots (>= 1) holding a class.  A class that merges into class "none"
+    // before the segment starts has the same count and exit as class "none", so its
+    // slot is freed: the stitch reads class "none" for any class key not listed.
+    uint32_t used = 0, umask = 0;
     uint32_t c_key[SC], c_start[SC], c_cnt[SC];
 #pragma unroll
     for (int j = 0; j < SC; ++j) c_key[j] = CLS_NONE, c_start[j] = 0, c_cnt[j] = 0;
@@ -199,7 +202,16 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
 #pragma unroll
                 for (int j = 1; j < SC; ++j) {
                     if ((umask >> j) & 1u) {
-                        if (c_start[j] <= msv) c_start[j] = gidx + 1, c_cnt[j] += inc;
+                        if (c_start[j] <= msv) {
+                            if (!inc) {
+                                // class j says "the serial machine's last completion before
+                                // the segment was c_key[j]"; a completion before the segment
+                                // refutes it, so it is never handed in: drop it
+                                used &= ~(1u << j), umask &= ~(1u << j), c_key[j] = CLS_NONE;
+                                continue;
+                            }
+                            c_start[j] = gidx + 1, c_cnt[j] += inc;
+                        }
                         if (c_start[j] == c_start[0]) {
                             c_cnt[j] -= c_cnt[0];
                             umask &= ~(1u << j);
@@ -214,10 +226,13 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
         return ring64[((uint32_t)q * R + (i & (R - 1))) * T];
     };
     // drop ring q's front entries that can no longer match (older than hi)
-    auto pop_dead = [&](int q, uint32_t tt) {
-        // single segment: entry (first, last) cluster, dead when last is too old;
-        // segmented: entry (t, annotation), dead when t is too old
-        while (head[q] != tail[q] && tt - (MC ? fx[q] : fy[q]) > ep.hi[q]) {
+    // Ring entries come in two forms: clusters (first, last) of admitted times whose
+    // neighbours are at most hi - lo apart (single-segment machine, and the lean step),
+    // or single times with their start annotation (segmented machine before its
+    // classes merge).  `cl` selects the form at compile time.
+    auto pop_dead_f = [&](auto cl, int q, uint32_t tt) {
+        constexpr bool CL = decltype(cl)::value;
+        while (head[q] != tail[q] && tt - (CL ? fy[q] : fx[q]) > ep.hi[q]) {
             ++head[q];
             if (head[q] != tail[q]) {
                 const uint2 e = slot(q, head[q]);
@@ -225,11 +240,12 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
             }
         }
     };
-    auto push = [&](int q, uint32_t tt, uint32_t msv) {
-        pop_dead(q, tt);
+    auto push_f = [&](auto cl, int q, uint32_t tt, uint32_t msv) {
+        constexpr bool CL = decltype(cl)::value;
+        pop_dead_f(cl, q, tt);
         const uint32_t n_in = tail[q] - head[q];
         if (n_in) {
-            if (MC) {
+            if (!CL) {
                 if (bx[q] == tt) {  // equal times are one entry; annotations only grow
                     by[q] = max(by[q], msv);
                     slot(q, tail[q] - 1u).y = by[q];
@@ -249,12 +265,16 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
             const uint2 e = slot(q, head[q]);
             fx[q] = e.x, fy[q] = e.y;
         }
-        const uint32_t yv = MC ? msv : tt;
+        const uint32_t yv = CL ? tt : msv;
         slot(q, tail[q]) = make_uint2(tt, yv);
         ++tail[q];
         bx[q] = tt, by[q] = yv;
         if (n_in == 0) fx[q] = tt, fy[q] = yv;
     };
+    using Clusters = std::integral_constant<bool, true>;
+    using Singles = std::integral_constant<bool, !MC>;  // the general step's form
+    auto pop_dead = [&](int q, uint32_t tt) { pop_dead_f(Singles{}, q, tt); };
+    auto push = [&](int q, uint32_t tt, uint32_t msv) { push_f(Singles{}, q, tt, msv); };
 
     // One node of the machine for an event at node k (k static after unrolling);
     // returns true when the event completed an occurrence (stop handling it).
@@ -319,61 +339,131 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
     };
 
     // The same machine step for the common case -- distinct types, event inside the
-    // segment proper, every entry class merged into class "none" -- with the class
-    // bookkeeping reduced to class "none" alone.
+    // segment proper, every entry class merged into class "none".  With a single class
+    // left, an entry is visible iff it was admitted after that class's last
+    // completion, so (after purging the entries it cannot see, once) a completion
+    // simply empties the state, as in the single-segment machine, and the start
+    // annotations are no longer needed.
+    auto clear_state = [&]() {
+        if constexpr (PASS == FEM_PASS_RELAXED) {
+#pragma unroll
+            for (int q = 0; q < NE; ++q) dl[q] = 0;
+        } else {
+#pragma unroll
+            for (int q = 0; q < NE; ++q) head[q] = tail[q];
+        }
+    };
     auto step_lean = [&](auto kc, uint32_t tt, uint32_t gidx) {
         constexpr int k = decltype(kc)::value;
-        auto done_lean = [&](uint32_t msv) {
+        auto done_lean = [&]() {
             if constexpr (MC) {
-                if (c_start[0] <= msv) c_start[0] = gidx + 1, ++c_cnt[0], c0_done = true;
+                c_start[0] = gidx + 1, ++c_cnt[0], c0_done = true;
             } else {
                 ++cnt;
             }
         };
         if constexpr (N == 1) {
-            done_lean(gidx);
+            done_lean();
         } else if constexpr (PASS == FEM_PASS_RELAXED) {
             if constexpr (k == 0) {
                 dl[0] = tt + ep.hi[0] + 1u;
-                if (MC) ms[0] = gidx;
-            } else if constexpr (k == N - 1) {
-                if (tt < dl[k - 1]) {
-                    done_lean(MC ? ms[k - 1] : 0u);
-                    if (!MC) {
-#pragma unroll
-                        for (int q = 0; q < NE; ++q) dl[q] = 0;
-                    }
-                }
-            } else {
-                if (tt < dl[k - 1]) {
+            } else if (tt < dl[k - 1]) {
+                if constexpr (k == N - 1) {
+                    done_lean();
+                    clear_state();
+                } else {
                     dl[k] = tt + ep.hi[k] + 1u;
-                    if (MC) ms[k] = ms[k - 1];
                 }
             }
         } else {
             if constexpr (k == 0) {
-                push(0, tt, gidx);
+                push_f(Clusters{}, 0, tt, 0u);
             } else {
                 constexpr int q = k - 1;
-                pop_dead(q, tt);
+                pop_dead_f(Clusters{}, q, tt);
                 if (head[q] != tail[q] && tt - fx[q] > ep.lo[q]) {
-                    uint32_t msv = fy[q];
-                    if (MC) {
-                        for (uint32_t i = head[q] + 1u; i != tail[q]; ++i) {
-                            const uint2 e = slot(q, i);
-                            if (!(tt - e.x > ep.lo[q])) break;
-                            msv = e.y;
-                        }
-                    }
                     if constexpr (k == N - 1) {
-                        done_lean(msv);
-                        if (!MC) {
-#pragma unroll
-                            for (int r = 0; r < NE; ++r) head[r] = tail[r];
-                        }
+                        done_lean();
+                        clear_state();
                     } else {
-                        push(k, tt, msv);
+                        push_f(Clusters{}, k, tt, 0u);
                     }
+                }
+            }
+        }
+    };
+    // entering the lean step in the segmented form: drop what class "none" cannot see
+    bool purged = !MC;
+    auto purge_invisible = [&]() {
+        if constexpr (MC) {
+            const uint32_t st0 = c_start[0];
+            if constexpr (PASS == FEM_PASS_RELAXED) {
+#pragma unroll
+                for (int q = 0; q < NE; ++q)
+                    if (ms[q] < st0) dl[q] = 0;
+            } else {
+                // annotations grow along each ring: the invisible entries are a prefix;
+                // the visible single times are then regrouped into clusters in place
+#pragma unroll
+                for (int q = 0; q < NE; ++q) {
+                    while (head[q] != tail[q] && fy[q] < st0) {
+                        ++head[q];
+                        if (head[q] != tail[q]) {
+                            const uint2 e = slot(q, head[q]);
+                            fx[q] = e.x, fy[q] = e.y;
+                        }
+                    }
+                    uint32_t w = head[q];
+                    for (uint32_t i = head[q]; i != tail[q]; ++i) {
+                        const uint32_t tv2 = slot(q, i).x;
+                        if (w != head[q] && tv2 - slot(q, w - 1u).y <= ep.hi[q] - ep.lo[q]) {
+                            slot(q, w - 1u).y = tv2;
+                        } else {
+                            slot(q, w) = make_uint2(tv2, tv2);
+                            ++w;
+                        }
+                    }
+                    tail[q] = w;
+                    if (head[q] != tail[q]) {
+                        const uint2 a = slot(q, head[q]), b = slot(q, tail[q] - 1u);
+                        fx[q] = a.x, fy[q] = a.y, bx[q] = b.x, by[q] = b.y;
+                    }
+                }
+            }
+        }
+    };
+
+    // Two classes whose visible live entries are the same have the same future, even
+    // if their starts differ: merge class j into class "none" when no entry that can
+    // still match an event at or after time T is visible to one and not the other.
+    // Done only while the next segment's window is still more than W ahead (T < Xn),
+    // so that both classes hand on the same (normalised) exit.
+    auto try_merge = [&](uint32_t T, bool window) {
+        if constexpr (MC) {
+            if (c_start[0] == 0xFFFFFFFFu || (!last_seg && T >= Xn)) return;
+#pragma unroll
+            for (int j = 1; j < SC; ++j) {
+                if (!((umask >> j) & 1u)) continue;
+                const uint32_t lo_s = min(c_start[0], c_start[j]);
+                const uint32_t hi_s = max(c_start[0], c_start[j]);
+                bool differ = false;
+                if constexpr (PASS == FEM_PASS_RELAXED) {
+#pragma unroll
+                    for (int q = 0; q < NE; ++q)
+                        differ |= dl[q] > T && ms[q] >= lo_s && ms[q] < hi_s;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NE; ++q) {
+                        for (uint32_t i = head[q]; i != tail[q] && !differ; ++i) {
+                            const uint2 e = slot(q, i);
+                            differ = (T < e.x || T - e.x <= ep.hi[q]) && e.y >= lo_s && e.y < hi_s;
+                        }
+                    }
+                }
+                if (!differ) {
+                    c_cnt[j] -= c_cnt[0];
+                    umask &= ~(1u << j);
+                    if (window) used &= ~(1u << j), c_key[j] = CLS_NONE;
                 }
             }
         }
@@ -452,6 +542,10 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
             const uint32_t lim = c + 1 == c_end ? hi_local : KEY_END;
             const bool lean =
                 distinct && (!MC || (c >= c_seg0 && umask == 0 && c_start[0] != 0xFFFFFFFFu));
+            if (lean && !purged) {
+                purge_invisible();
+                purged = true;
+            }
             if (lean) {
                 for (;;) {
                     uint32_t mk = key[0];
@@ -492,28 +586,29 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                         key[k] = ptr[k] < end[k] ? e.y : KEY_END;
                     }
                 });
-                if (MC && last_hit && capable && (uint64_t)gidx < L) {
-                    // entry class r = gidx: the serial machine's last completion was r
-                    if (ns < (uint32_t)SC) {
+                if (MC && last_hit && capable && (uint64_t)gidx < L &&
+                    c_start[0] != gidx + 1) {
+                    // entry class r = gidx (the serial machine's last completion was r);
+                    // when class "none" completed at r too, it is that class: no slot
+                    const uint32_t free_slots = ~used & (((1u << SC) - 1u) & ~1u);
+                    if (free_slots) {
+                        const int q0 = __ffs(free_slots) - 1;
 #pragma unroll
                         for (int q = 1; q < SC; ++q) {
-                            if ((uint32_t)q == ns) {
+                            if (q == q0) {
                                 c_key[q] = gidx;
                                 c_start[q] = gidx + 1;
                                 c_cnt[q] = 0;
-                                umask |= 1u << q;
-                                if (c_start[0] == gidx + 1) {
-                                    c_cnt[q] -= c_cnt[0];
-                                    umask &= ~(1u << q);
-                                }
                             }
                         }
-                        ++ns;
+                        used |= 1u << q0;
+                        umask |= 1u << q0;
                     } else {
-                        overflow = true;
+                        class_overflow = true;
                     }
                 }
             }
+            if (MC && umask) try_merge(p.cfirst[c + 1], c < c_seg0);
         }
         __syncthreads();
         if (tid == 0 && c + 2 < c_end) {
@@ -535,8 +630,8 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
 
     // ---------------------------------------------------------------- results
     if (ci >= m_cur) return true;
-    if (overflow) {
-        atomicOr(p.err, ERR_RING);
+    if (overflow || class_overflow) {
+        atomicOr(p.err, (overflow ? ERR_RING : 0u) | (class_overflow ? ERR_CLASS : 0u));
         p.redo[ci] = 1;
     }
     if (!MC && stw) {
@@ -565,7 +660,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
 #pragma unroll
         for (int q = 0; q < S_MAX; ++q) {
             uint4 e = make_uint4(CLS_EMPTY, 0, CLS_NONE, 0);
-            if (ok && (uint32_t)q < ns) {
+            if (ok && (q == 0 || ((used >> q) & 1u))) {
                 const bool merged = q > 0 && !((umask >> q) & 1u);
                 const uint32_t cntq = merged ? c_cnt[0] + c_cnt[q] : c_cnt[q];
                 const uint32_t st = merged ? c_start[0] : c_start[q];

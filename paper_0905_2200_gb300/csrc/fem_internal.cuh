@@ -33,6 +33,7 @@ constexpr uint32_t ERR_BADEP = 4u;         // malformed candidate (type/len/inte
 constexpr uint32_t ERR_UNSORTED = 8u;
 constexpr uint32_t ERR_TYPE = 16u;
 constexpr uint32_t ERR_TABLE = 32u;        // transfer table missing a class (internal)
+constexpr uint32_t ERR_CLASS = 64u;        // more entry classes than table slots (host retries)
 
 constexpr uint64_t WAIT_NS = 2000000000ull; // bound on any single device wait (2 s)
 

@@ -97,14 +97,17 @@ __device__ void stitch_one(const uint4 *__restrict__ tables, uint32_t m, uint32_
 #pragma unroll
             for (int j = 0; j < S_MAX; ++j) {
                 if (fk[j] == CLS_EMPTY) continue;
-                bool hit = false;
-                uint32_t nc = 0, ne = CLS_NONE;
+                // a class key without its own entry behaves as class "none"
+                bool hit = false, hitn = false;
+                uint32_t nc = 0, ne = CLS_NONE, ncn = 0, nen = CLS_NONE;
 #pragma unroll
-                for (int i = 0; i < S_MAX; ++i)
+                for (int i = 0; i < S_MAX; ++i) {
                     if (!hit && gk[i] == fe[j]) hit = true, nc = gc[i], ne = ge[i];
-                if (!hit) bad = true;
-                fc[j] += nc;
-                fe[j] = ne;
+                    if (!hitn && gk[i] == CLS_NONE) hitn = true, ncn = gc[i], nen = ge[i];
+                }
+                if (!hit && !hitn) bad = true;
+                fc[j] += hit ? nc : ncn;
+                fe[j] = hit ? ne : nen;
             }
         }
     }
@@ -127,14 +130,16 @@ __device__ void stitch_one(const uint4 *__restrict__ tables, uint32_t m, uint32_
 #pragma unroll
                 for (int j = 0; j < S_MAX; ++j) {
                     if (fk[j] == CLS_EMPTY) continue;
-                    bool hit = false;
-                    uint32_t nc = 0, ne = CLS_NONE;
+                    bool hit = false, hitn = false;
+                    uint32_t nc = 0, ne = CLS_NONE, ncn = 0, nen = CLS_NONE;
 #pragma unroll
-                    for (int i = 0; i < S_MAX; ++i)
+                    for (int i = 0; i < S_MAX; ++i) {
                         if (!hit && pk[i] == fe[j]) hit = true, nc = pc[i], ne = pe[i];
-                    if (!hit) bad = true;
-                    fc[j] += nc;
-                    fe[j] = ne;
+                        if (!hitn && pk[i] == CLS_NONE) hitn = true, ncn = pc[i], nen = pe[i];
+                    }
+                    if (!hit && !hitn) bad = true;
+                    fc[j] += hit ? nc : ncn;
+                    fe[j] = hit ? ne : nen;
                 }
             }
         }
