@@ -23,6 +23,8 @@
 //    that would overflow sets ERR_RING and the host recounts the episode with a
 //    larger ring.  The segmented variant keeps single times (with equal times
 //    merged), because it needs the annotation of the newest matching entry.
+//    When every edge has hi >= 2 lo at most two clusters are live, and the lean
+//    step keeps both in registers instead of the ring.
 //
 // MapConcatenate (Section 5.2.2), exact form (template flag MC): the thread
 // counting segment p starts at the window start w_p (first event with
@@ -494,6 +496,40 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
         }
     }
 
+    // ---------------------------------------------------------------- register rings
+    // When every edge of the episode has hi >= 2 lo, consecutive clusters of a list
+    // are more than hi - lo >= hi / 2 apart, so a cluster two places behind the
+    // newest one ended more than hi before any event that can still come: at most
+    // two clusters of each list are live.  The exact pass's lean step then keeps
+    // each list as its front (fx, fy) and back (bx, by) cluster plus a count in
+    // tail[] (head[] = 0), all in registers: no shared-memory ring traffic.
+    constexpr bool EXN = PASS == FEM_PASS_EXACT && N > 1;
+    bool ring2 = EXN, in_regs2 = false;
+#pragma unroll
+    for (int q = 0; q < NE; ++q) ring2 = ring2 && ep.hi[q] - ep.lo[q] >= ep.lo[q];
+    auto to_regs2 = [&]() {
+#pragma unroll
+        for (int q = 0; q < NE; ++q) {
+            uint32_t n = tail[q] - head[q];
+            if (n > 2) {  // the older clusters have ended (see above)
+                const uint2 a = slot(q, tail[q] - 2u);
+                fx[q] = a.x, fy[q] = a.y;
+                n = 2;
+            }
+            if (n == 1) bx[q] = fx[q], by[q] = fy[q];
+            head[q] = 0, tail[q] = n;
+        }
+        in_regs2 = true;
+    };
+    auto from_regs2 = [&]() {
+#pragma unroll
+        for (int q = 0; q < NE; ++q) {
+            if (tail[q] >= 1) slot(q, 0) = make_uint2(fx[q], fy[q]);
+            if (tail[q] == 2) slot(q, 1) = make_uint2(bx[q], by[q]);
+        }
+        in_regs2 = false;
+    };
+
     // ---------------------------------------------------------------- chunk pipeline
     const uint32_t chunk_ev_bytes = CHUNK * 8u;
     const uint32_t chunk_off_bytes = p.offs * 2u;
@@ -546,7 +582,67 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                 purge_invisible();
                 purged = true;
             }
-            if (lean) {
+            if (EXN && lean && ring2) {
+                if (!in_regs2) to_regs2();
+                for (;;) {
+                    uint32_t mk = key[0];
+#pragma unroll
+                    for (int k = 1; k < N; ++k) mk = min(mk, key[k]);
+                    if (mk >= lim) break;
+                    for_nodes_desc<N - 1>([&](auto kc) {
+                        constexpr int k = decltype(kc)::value;
+                        if (key[k] == mk) {
+                            const uint32_t tt = tv[k];
+                            // drop list q's clusters that ended more than hi before tt
+                            auto pop2 = [&](int q) {
+                                if (tail[q] > 0 && tt - fy[q] > ep.hi[q])
+                                    fx[q] = bx[q], fy[q] = by[q], --tail[q];
+                                if (tail[q] > 0 && tt - fy[q] > ep.hi[q]) tail[q] = 0;
+                            };
+                            // append tt to list q (tail = number of live clusters)
+                            auto push2 = [&](int q) {
+                                pop2(q);
+                                const uint32_t n = tail[q];
+                                if (n > 0 && tt - by[q] <= ep.hi[q] - ep.lo[q]) {
+                                    by[q] = tt;
+                                    if (n == 1) fy[q] = tt;
+                                } else if (n == 0) {
+                                    fx[q] = fy[q] = bx[q] = by[q] = tt, tail[q] = 1;
+                                } else if (n == 1) {
+                                    bx[q] = by[q] = tt, tail[q] = 2;
+                                } else {  // cannot happen when hi >= 2 lo; reported
+                                    overflow = true;
+                                    fx[q] = bx[q], fy[q] = by[q], bx[q] = by[q] = tt;
+                                }
+                            };
+                            if constexpr (k == 0) {
+                                push2(0);
+                            } else {
+                                constexpr int q = k - 1;
+                                pop2(q);
+                                if (tail[q] > 0 && tt - fx[q] > ep.lo[q]) {
+                                    if constexpr (k == N - 1) {
+                                        if constexpr (MC) {
+                                            c_start[0] = (uint32_t)(cbase + mk) + 1, ++c_cnt[0],
+                                            c0_done = true;
+                                        } else {
+                                            ++cnt;
+                                        }
+#pragma unroll
+                                        for (int r = 0; r < NE; ++r) tail[r] = 0;
+                                    } else {
+                                        push2(k);
+                                    }
+                                }
+                            }
+                            ++ptr[k];
+                            const uint2 e = ev[ptr[k]];
+                            tv[k] = e.x;
+                            key[k] = ptr[k] < end[k] ? e.y : KEY_END;
+                        }
+                    });
+                }
+            } else if (lean) {
                 for (;;) {
                     uint32_t mk = key[0];
 #pragma unroll
@@ -564,7 +660,8 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                         }
                     });
                 }
-            } else
+            } else {
+            if (in_regs2) from_regs2();
             for (;;) {
                 uint32_t mk = key[0];
 #pragma unroll
@@ -608,6 +705,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                     }
                 }
             }
+            }
             if (MC && umask) try_merge(p.cfirst[c + 1], c < c_seg0);
         }
         __syncthreads();
@@ -634,6 +732,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
         atomicOr(p.err, (overflow ? ERR_RING : 0u) | (class_overflow ? ERR_CLASS : 0u));
         p.redo[ci] = 1;
     }
+    if (in_regs2) from_regs2();
     if (!MC && stw) {
         stw[0] = cnt;
         if constexpr (PASS == FEM_PASS_RELAXED) {

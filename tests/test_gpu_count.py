@@ -71,6 +71,20 @@ def test_segmented_equals_oracle(ctx, mid, pass_, segments):
 
 
 @pytest.mark.parametrize("pass_", PASSES)
+@pytest.mark.parametrize("segments", [1, 5])
+def test_mixed_interval_widths(ctx, mid, pass_, segments):
+    """Edges with hi >= 2 lo (two live clusters per list at most: register lists) next
+    to edges with hi < 2 lo (more live clusters: shared-memory rings), in one warp."""
+    ty, t, K, chains, sid = mid
+    I = np.array([[0, 2000], [4000, 6000], [2000, 5000], [9000, 11000], [5000, 10000]],
+                 np.uint32)
+    L, E, iv = synth.random_candidates(0x31 + segments, 900, K, [2, 3, 4, 5], len(I))
+    fem.fem_set_config(ctx, segments=segments)
+    got = fem.fem_count_candidates(ctx, sid, fem.pack_episodes(L, E, iv), I, pass_)
+    assert_counts_equal(got, oracle_counts(ty, t, L, E, iv, I, pass_), f"mixed P={segments}")
+
+
+@pytest.mark.parametrize("pass_", PASSES)
 def test_autotuned_launch_level2_mid(ctx, mid, pass_):
     ty, t, K, chains, sid = mid
     L, E, iv = synth.level2_candidates(range(K), 4)
