@@ -35,15 +35,19 @@ sys.path.insert(0, ROOT)
 METRIC = "episode-events counted/sec (candidates x stream events / s), exact; level-wise mine time"
 UNIT = "candidate-events/s"
 L2_FLUSH_BYTES = 256 << 20
-# Integer lane-operations per touched (episode, matching event) update of the
-# relaxed machine: subtract-compare against the predecessor deadline, select,
-# deadline add, store/count.
-OPS_PER_TOUCHED = 4
-# DRAM bytes per launch of the level-2 relaxed counting kernel from one ncu capture,
-# keyed by the SHA-256 of the kernel source it was taken on (None when stale).
+# Integer lane-operations per touched (episode, matching event) update: relaxed
+# machine (Algorithm 3) subtract-compare against the predecessor deadline, select,
+# deadline add, store/count; exact machine (Algorithm 1) pop test, window compare,
+# push (two more).
+OPS_PER_TOUCHED = {"relaxed": 4, "exact": 6}
+# DRAM bytes per launch of each counting launch of the mining step ("level/pass")
+# from one ncu capture, keyed by the SHA-256 of the kernel source it was taken on
+# (no entry: stale, reported as null).
 NCU_TRAFFIC = {
-    # prof_count_v2: dram__bytes_read.sum 4.167936 MB + dram__bytes_write.sum 0.041216 MB
-    "eed9655bf9fb754d": 4209152,
+    # counting kernels of commit 6fde740 (device code unchanged since), ncu --set full
+    # of the first mining step: dram__bytes_read.sum + dram__bytes_write.sum per launch
+    "02eb35fb5593365f": {"2/relaxed": 4230400, "2/exact": 3986432, "3/relaxed": 3883008,
+                    "3/exact": 3727360},
 }
 
 
@@ -155,15 +159,6 @@ def workload(rank: int):
     return cfg
 
 
-def level2_touched(hist, theta, n_intervals):
-    """Sum over level-2 candidates of the events of their two types (the updates the
-    relaxed machines must make): every ordered pair of distinct frequent types, once
-    per interval."""
-    f = np.asarray(hist, dtype=np.float64)[np.asarray(hist) >= theta]
-    k = f.size
-    return float(n_intervals * (k - 1) * 2 * f.sum()) if k > 1 else 0.0
-
-
 def cpu_baseline(cfg, budget_s=12.0, seed=0):
     """The oracle, as it stands, on a bounded sample of the level-2 two-pass count."""
     import oracle
@@ -203,6 +198,8 @@ def run_ours(args, rank, world, local):
     I, theta, max_len = cfg["intervals"], cfg["theta"], cfg["max_len"]
     n = s.n
     ctx = fem.fem_create(local)
+    if not args.no_tune:
+        fem.fem_tune_enable(ctx, True)  # launch shapes measured during the warm-up steps
     d_types = torch.from_numpy(s.types.copy()).to(dev)
     d_t = torch.from_numpy(s.t.view(np.int32).copy()).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -245,16 +242,29 @@ def run_ours(args, rank, world, local):
                                      device=dev if world > 1 else "cpu")
     value = units_all / (tmax * args.steps / 1e3)
 
-    # dominant kernel: the level-2 relaxed counter
-    k_ms = [st[0]["ms_relaxed_kernel"] for st in stats_all if st and st[0]["level"] == 2]
-    k_avg = sum(k_ms) / len(k_ms)
-    hist = fem.fem_type_counts(ctx, fem.fem_load_stream(ctx, s.types, s.t, s.n_types), s.n_types)
-    touched = level2_touched(hist, theta, len(I))
+    # dominant kernel: the counting launch (level, pass) with the largest average
+    # duration over the timed steps; its work is the touched (episode, event) updates
+    # the library reports for that launch
+    launches_ms, touched = {}, {}
+    for st in stats_all:
+        for lv in st:
+            for ps in ("relaxed", "exact"):
+                key = (lv["level"], ps)
+                launches_ms.setdefault(key, []).append(lv[f"ms_{ps}_kernel"])
+                touched[key] = lv[f"touched_{ps}"]
+    avg_ms = {k: sum(v) / len(v) for k, v in launches_ms.items()}
+    dom = max(avg_ms, key=avg_ms.get)
+    dom_lv = next(lv for lv in stats_all[-1] if lv["level"] == dom[0])
+    dom_seg = dom_lv["segments" if dom[1] == "relaxed" else "exact_segments"]
     sm_mhz = clk["sm_mhz"] or 2070.0
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = n_sm * 128 * sm_mhz * 1e6 / 1e12
-    achieved = touched * OPS_PER_TOUCHED / (k_avg * 1e-3) / 1e12
-    traffic = NCU_TRAFFIC.get(kernel_source_hash())
+    ops = OPS_PER_TOUCHED[dom[1]]
+    achieved = touched[dom] * ops / (avg_ms[dom] * 1e-3) / 1e12
+    all_ops = sum(touched[k] * OPS_PER_TOUCHED[k[1]] for k in avg_ms)
+    all_ach = all_ops / (sum(avg_ms.values()) * 1e-3) / 1e12
+    traffic = NCU_TRAFFIC.get(kernel_source_hash(), {}).get(f"{dom[0]}/{dom[1]}")
+    kname = f"k_count<{dom[0]}, {dom[1]}{', MapConcatenate' if dom_seg > 1 else ''}>"
 
     # end to end through the public API with host (pinned) buffers
     h_types = torch.from_numpy(s.types.copy()).pin_memory()
@@ -278,6 +288,7 @@ def run_ours(args, rank, world, local):
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline(cfg)
+    tuned = fem.fem_tune_size(ctx)
     fem.fem_destroy(ctx)
     if rank != 0:
         return
@@ -294,15 +305,20 @@ def run_ours(args, rank, world, local):
                    "l2": "flushed between steps (256 MiB device write outside the step events)",
                    "step": "device staging of the resident stream + two-pass level-wise mining "
                            "+ frequent sets copied to host",
-                   "parallelism": f"{world} independent recordings (one per GPU)"},
+                   "parallelism": f"{world} independent recordings (one per GPU)",
+                   "mapping": ("rule (segments for ~2048 threads per SM)" if args.no_tune else
+                               "measured: launch shapes tuned during the warm-up steps, "
+                               f"{tuned} classes cached")},
         "levels": per_level,
-        "roofline": {"bound": "alu", "kernel": "k_count<2, relaxed, MapConcatenate>",
+        "roofline": {"bound": "alu", "kernel": f"{kname} (level {dom[0]} {dom[1]} pass)",
                      "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                      "traffic": traffic,
-                     "basis": (f"{touched:.4g} touched (episode, matching event) updates x "
-                               f"{OPS_PER_TOUCHED} int ops / {k_avg:.4f} ms avg launch; peak = "
+                     "basis": (f"{touched[dom]:.4g} touched (episode, matching event) updates x "
+                               f"{ops} int ops / {avg_ms[dom]:.4f} ms avg launch; peak = "
                                f"{n_sm} SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock "
-                               f"sampled during the timed steps)")},
+                               f"sampled during the timed steps)"),
+                     "all_counting_launches": {"achieved": all_ach, "frac": all_ach / peak,
+                                               "ms_per_step": sum(avg_ms.values())}},
         "cpu_baseline": base,
         "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_max,
                 "h2d_bytes_per_step": int(5 * n + 8 * len(I)), "d2h_bytes_per_step": int(d2h)},
@@ -659,6 +675,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="launch shapes from the fixed rule instead of measured ones")
     ap.add_argument("--workload", choices=["single_recording", "batched", "serving", "large"],
                     default="single_recording")
     ap.add_argument("--session-s", type=float, default=20.0)

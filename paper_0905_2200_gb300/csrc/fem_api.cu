@@ -49,6 +49,15 @@ struct fem_ctx {
     std::vector<StreamDev> pool;  // buffers of freed streams, reused by later loads
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaEvent_t kev[3] = {nullptr, nullptr, nullptr};  // around the counting kernel and stitch
+    // measured mapping choice: launch shape per (N, pass, distinct, log2 m,
+    // log2 chunks, K) class
+    struct Shape {
+        uint32_t P, T;
+        float ms;
+    };
+    std::map<std::string, Shape> tune;
+    bool tune_on = false, tuning = false;
+    cudaEvent_t tev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -166,11 +175,102 @@ struct PassInfo {
     float ms_kernel = 0, ms_stitch = 0;
 };
 
-// One counting pass over m candidates (all of length N) -> out[0..m).
+uint32_t ceil_log2(uint64_t v) {
+    uint32_t r = 0;
+    while ((1ull << r) < v) ++r;
+    return r;
+}
+
+// The class a measured launch shape is kept for: counts of the same length,
+// pass and type structure, with m and the stream length in the same power-of-two
+// range and the same type count, map alike.
+std::string tune_key(int N, int pass, bool distinct, uint32_t m, uint32_t n_chunks, uint32_t K) {
+    char b[96];
+    std::snprintf(b, sizeof(b), "%d/%d/%d/%u/%u/%u", N, pass, distinct ? 1 : 0, ceil_log2(m),
+                  ceil_log2(n_chunks), K);
+    return b;
+}
+
 int count_pass(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const uint32_t *gather,
                uint32_t m, int N, const uint2 *d_ivl, uint32_t nI, int pass, uint32_t *out,
-               bool distinct, cudaStream_t st, PassInfo *info) {
+               bool distinct, cudaStream_t st, PassInfo *info);
+
+// Mapping choice by measurement (it replaces the fixed crossover rule of
+// Algorithm 2): time the rule's launch shape and its neighbours (half and twice
+// the segments per episode, the other block size) on the real inputs and keep the
+// fastest for the class.  Every trial is a complete, correct count.
+int tune_pass(fem_ctx *c, const std::string &key, const StreamDev &s, const fem_episode *cands,
+              const uint32_t *gather, uint32_t m, int N, const uint2 *d_ivl, uint32_t nI,
+              int pass, uint32_t *out, bool distinct, cudaStream_t st) {
+    const uint32_t P0 = choose_segments(c, s, m, distinct);
+    std::vector<uint32_t> Ps{P0};
+    if (distinct) {
+        if (P0 > 1) Ps.push_back(std::max<uint32_t>(1, P0 / 2));
+        if (P0 * 2 <= s.n_chunks) Ps.push_back(P0 * 2);
+    }
+    const uint32_t R0 = pass == FEM_PASS_EXACT ? (c->cfg.ring_capacity ? c->cfg.ring_capacity : 8) : 1;
+    fem_ctx::Shape best{0, 0, 0};
+    const fem_config saved = c->cfg;
+    c->tuning = true;
+    int rc = FEM_OK;
+    for (uint32_t P : Ps) {
+        const uint32_t R = (P > 1 && R0 > 32) ? 32 : R0;
+        const uint32_t T0 = choose_threads(c, N, pass, P > 1, R, s.offs, m);
+        std::vector<uint32_t> Ts{T0};
+        for (uint32_t T : {128u, 256u})
+            if (T != T0 && m > T / 2 && count_smem_bytes(N, pass, P > 1, R, T, s.offs) <= 100 * 1024)
+                Ts.push_back(T);
+        for (uint32_t T : Ts) {
+            c->cfg.segments = P;
+            c->cfg.threads_per_block = T;
+            cudaEventRecord(c->tev[0], st);
+            rc = count_pass(c, s, cands, gather, m, N, d_ivl, nI, pass, out, distinct, st, nullptr);
+            cudaEventRecord(c->tev[1], st);
+            if (rc != FEM_OK) break;
+            float ms = 0;
+            if (cudaEventSynchronize(c->tev[1]) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, c->tev[0], c->tev[1]) != cudaSuccess) {
+                rc = FEM_ECUDA;
+                break;
+            }
+            if (!best.P || ms < best.ms) best = fem_ctx::Shape{P, T, ms};
+        }
+        if (rc != FEM_OK) break;
+    }
+    c->cfg = saved;
+    c->tuning = false;
+    if (rc == FEM_OK && best.P) c->tune[key] = best;
+    return rc;
+}
+
+// A counting pass that has been launched: what its completion check needs.
+struct PassLaunch {
+    CountParams p{};
+    int N = 0, pass = 0;
+    bool distinct = true;
+    uint32_t R = 1;
+};
+
+// Launch one counting pass over m candidates (all of length N) -> out[0..m)
+// (kernel, then the stitch when segmented), without waiting for it.  The pass is
+// complete only after count_finish has seen the error word.
+int count_launch(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const uint32_t *gather,
+                 uint32_t m, int N, const uint2 *d_ivl, uint32_t nI, int pass, uint32_t *out,
+                 bool distinct, cudaStream_t st, PassLaunch *pl) {
+    pl->p = CountParams{};
+    pl->N = N, pl->pass = pass, pl->distinct = distinct;
     if (m == 0) return FEM_OK;
+    // a measured shape for this class, if any (explicit configuration wins)
+    uint32_t P_t = 0, T_t = 0;
+    if (!c->cfg.segments && !c->cfg.threads_per_block && !c->tuning) {
+        const std::string key = tune_key(N, pass, distinct, m, s.n_chunks, s.K);
+        auto it = c->tune.find(key);
+        if (it == c->tune.end() && c->tune_on) {
+            RET(tune_pass(c, key, s, cands, gather, m, N, d_ivl, nI, pass, out, distinct, st));
+            it = c->tune.find(key);
+        }
+        if (it != c->tune.end()) P_t = it->second.P, T_t = it->second.T;
+    }
     CountParams p{};
     p.bev = s.bev;
     p.boff = s.boff;
@@ -192,7 +292,9 @@ int count_pass(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const u
     CK(cudaMemsetAsync(redo, 0, m, st));
     p.redo = redo;
 
-    uint32_t P = choose_segments(c, s, m, distinct);
+    uint32_t P = P_t ? std::min<uint32_t>(P_t, std::max<uint32_t>(s.n_chunks, 1))
+                     : choose_segments(c, s, m, distinct);
+    if (!distinct) P = 1;
     uint32_t R = 1;
     if (pass == FEM_PASS_EXACT) R = c->cfg.ring_capacity ? c->cfg.ring_capacity : 8;
     if (P > 1 && pass == FEM_PASS_EXACT && R > 32) R = 32;
@@ -204,22 +306,40 @@ int count_pass(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const u
     if (P > 1) {
         RET(dbuf(c, "tables", (size_t)P * m * S_MAX, &p.tables));
     }
-    const uint32_t T = choose_threads(c, N, pass, P > 1, R, s.offs, m);
+    uint32_t T = choose_threads(c, N, pass, P > 1, R, s.offs, m);
+    if (T_t && count_smem_bytes(N, pass, P > 1, R, T_t, s.offs) <= 100 * 1024) T = T_t;
     CK(cudaEventRecord(c->kev[0], st));
     CK(launch_count(N, pass, P > 1, R, T, p, st));
     CK(cudaEventRecord(c->kev[1], st));
     if (P > 1) CK(launch_stitch(p.tables, m, P, out, redo, c->d_err, st));
     CK(cudaEventRecord(c->kev[2], st));
+    pl->p = p;
+    pl->R = R;
+    return FEM_OK;
+}
 
-    uint32_t e;
-    RET(read_err(c, st, &e));
-    if (info) {
-        info->segments = P;
-        cudaEventElapsedTime(&info->ms_kernel, c->kev[0], c->kev[1]);
-        cudaEventElapsedTime(&info->ms_stitch, c->kev[1], c->kev[2]);
-    }
+// Kernel and stitch times of the last launched pass (its events have completed).
+void pass_info(fem_ctx *c, const PassLaunch &pl, PassInfo *info) {
+    info->segments = pl.p.m ? pl.p.P : 0;
+    info->ms_kernel = info->ms_stitch = 0;
+    if (!pl.p.m) return;
+    cudaEventElapsedTime(&info->ms_kernel, c->kev[0], c->kev[1]);
+    cudaEventElapsedTime(&info->ms_stitch, c->kev[1], c->kev[2]);
+}
+
+// Complete a launched pass given the error word read after it: report hard errors,
+// and recount the episodes whose rings or class tables overflowed.
+int count_finish(fem_ctx *c, const StreamDev &s, const PassLaunch &pl, uint32_t e,
+                 cudaStream_t st) {
     RET(err_status(e));
-    if (!(e & (ERR_RING | ERR_TABLE | ERR_CLASS))) return FEM_OK;
+    if (!pl.p.m || !(e & (ERR_RING | ERR_TABLE | ERR_CLASS))) return FEM_OK;
+    const CountParams &p = pl.p;
+    const uint32_t m = p.m, P = p.P, R = pl.R;
+    const int N = pl.N, pass = pl.pass;
+    const bool distinct = pl.distinct;
+    const uint32_t *gather = p.gather;
+    uint32_t *out = p.out;
+    uint8_t *redo = p.redo;
 
     // Recount the flagged episodes with one segment and larger rings.
     uint32_t *ridx, *rg, *rout, *scratch;
@@ -276,6 +396,19 @@ int count_pass(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const u
         }
     }
     return FEM_EOVERFLOW;
+}
+
+// One counting pass, waited for and completed.
+int count_pass(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const uint32_t *gather,
+               uint32_t m, int N, const uint2 *d_ivl, uint32_t nI, int pass, uint32_t *out,
+               bool distinct, cudaStream_t st, PassInfo *info) {
+    if (m == 0) return FEM_OK;
+    PassLaunch pl;
+    RET(count_launch(c, s, cands, gather, m, N, d_ivl, nI, pass, out, distinct, st, &pl));
+    uint32_t e;
+    RET(read_err(c, st, &e));
+    if (info) pass_info(c, pl, info);
+    return count_finish(c, s, pl, e, st);
 }
 
 // Validate a candidate set (optionally gathered) and count it with `pass`,
@@ -357,6 +490,7 @@ const char *fem_strerror(int s) {
         case FEM_ECUDA: return "CUDA runtime error";
         case FEM_EOVERFLOW: return "internal capacity exceeded";
         case FEM_ENOSTREAM: return "unknown stream id";
+        case FEM_EIO: return "file could not be opened, read or written";
         default: return "unknown status";
     }
 }
@@ -381,7 +515,8 @@ int fem_create(fem_ctx **out, int device) {
         cudaMallocHost(&c->h_small, 64 * sizeof(uint32_t)) != cudaSuccess ||
         cudaEventCreate(&c->ev[0]) != cudaSuccess || cudaEventCreate(&c->ev[1]) != cudaSuccess ||
         cudaEventCreate(&c->kev[0]) != cudaSuccess || cudaEventCreate(&c->kev[1]) != cudaSuccess ||
-        cudaEventCreate(&c->kev[2]) != cudaSuccess) {
+        cudaEventCreate(&c->kev[2]) != cudaSuccess || cudaEventCreate(&c->tev[0]) != cudaSuccess ||
+        cudaEventCreate(&c->tev[1]) != cudaSuccess) {
         cudaGetLastError();
         fem_destroy(c);
         return FEM_ECUDA;
@@ -404,6 +539,8 @@ int fem_destroy(fem_ctx *c) {
         if (e) cudaEventDestroy(e);
     for (auto &e : c->kev)
         if (e) cudaEventDestroy(e);
+    for (auto &e : c->tev)
+        if (e) cudaEventDestroy(e);
     for (StreamDev &s : c->pool) free_stream_buffers(s);
     if (c->own) cudaStreamDestroy(c->own);
     delete c;
@@ -422,6 +559,57 @@ int fem_set_config(fem_ctx *c, const fem_config *cfg) {
     if (cfg->ring_capacity && !count_config_supported(2, FEM_PASS_EXACT, false, cfg->ring_capacity))
         return FEM_EINVAL;
     c->cfg = *cfg;
+    return FEM_OK;
+}
+
+int fem_tune_enable(fem_ctx *c, int on) {
+    if (!c) return FEM_EINVAL;
+    c->tune_on = on != 0;
+    return FEM_OK;
+}
+
+int fem_tune_size(fem_ctx *c, uint32_t *n_out) {
+    if (!c || !n_out) return FEM_EINVAL;
+    *n_out = (uint32_t)c->tune.size();
+    return FEM_OK;
+}
+
+// One JSON object per line: {"key": "N/pass/distinct/log2m/log2chunks/K", "segments": P,
+// "threads": T, "ms": t}
+int fem_tune_save(fem_ctx *c, const char *path) {
+    if (!c || !path) return FEM_EINVAL;
+    FILE *f = std::fopen(path, "w");
+    if (!f) return FEM_EIO;
+    for (const auto &kv : c->tune)
+        std::fprintf(f, "{\"key\": \"%s\", \"segments\": %u, \"threads\": %u, \"ms\": %.6f}\n",
+                     kv.first.c_str(), kv.second.P, kv.second.T, kv.second.ms);
+    const bool ok = std::fclose(f) == 0;
+    return ok ? FEM_OK : FEM_EIO;
+}
+
+int fem_tune_load(fem_ctx *c, const char *path) {
+    if (!c || !path) return FEM_EINVAL;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return FEM_EIO;
+    std::map<std::string, fem_ctx::Shape> got;
+    char line[512];
+    int rc = FEM_OK;
+    while (std::fgets(line, sizeof(line), f)) {
+        if (line[0] == '\n' || line[0] == 0) continue;
+        char key[96];
+        unsigned P = 0, T = 0;
+        float ms = 0;
+        if (std::sscanf(line, " {\"key\": \"%95[0-9/]\", \"segments\": %u, \"threads\": %u, \"ms\": %f}",
+                        key, &P, &T, &ms) != 4 ||
+            P == 0 || T == 0 || T > 256 || T % 8 != 0) {
+            rc = FEM_EINVAL;
+            break;
+        }
+        got[key] = fem_ctx::Shape{P, T, ms};
+    }
+    std::fclose(f);
+    if (rc != FEM_OK) return rc;
+    for (auto &kv : got) c->tune[kv.first] = kv.second;
     return FEM_OK;
 }
 
@@ -643,6 +831,10 @@ int fem_mine_levelwise(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t n
 
     uint2 *d_ivl;
     RETF(upload_intervals(c, I, nI, st, &d_ivl));
+    // per level, the (episode, event) pairs each pass visits (statistics only)
+    unsigned long long *touched;
+    RETF(dbuf(c, "touched", 2 * (FEM_MAX_LEN + 1), &touched));
+    CKF(cudaMemsetAsync(touched, 0, 2 * (FEM_MAX_LEN + 1) * sizeof(unsigned long long), st));
     // level 1: the count of a one-node episode is the number of events of its type
     uint32_t *ftypes;
     RETF(dbuf(c, "ftypes", 256, &ftypes));
@@ -695,6 +887,7 @@ int fem_mine_levelwise(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t n
         RETF(count_pass(c, s, cands, nullptr, m, (int)N, d_ivl, nI, FEM_PASS_RELAXED, rel, true,
                         st, &pi));
         cudaEventRecord(c->ev[1], st);
+        CKF(launch_touched(cands, nullptr, m, s.hist, touched + 2 * N, st));
         cudaEventSynchronize(c->ev[1]);
         cudaEventElapsedTime(&ls.ms_relaxed, c->ev[0], c->ev[1]);
         ls.segments = pi.segments;
@@ -718,6 +911,7 @@ int fem_mine_levelwise(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t n
         ls.ms_exact_kernel = pe.ms_kernel;
         ls.exact_segments = ms ? pe.segments : 0;
         cudaEventRecord(c->ev[1], st);
+        CKF(launch_touched(cands, idx_s, ms, s.hist, touched + 2 * N + 1, st));
         cudaEventSynchronize(c->ev[1]);
         cudaEventElapsedTime(&ls.ms_exact, c->ev[0], c->ev[1]);
         CKF(launch_compact(ex, nullptr, theta, ms, idx_f, c->d_small + W_COUNT1, scratch, st));
@@ -757,7 +951,13 @@ int fem_mine_levelwise(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t n
         cudaEventRecord(c->ev[1], st);
         m = mn;
     }
+    unsigned long long tv[2 * (FEM_MAX_LEN + 1)];
+    CKF(cudaMemcpyAsync(tv, touched, sizeof(tv), cudaMemcpyDeviceToHost, st));
     CKF(cudaStreamSynchronize(st));
+    for (fem_level_stats &ls : c->stats) {
+        ls.touched_relaxed = tv[2 * ls.level];
+        ls.touched_exact = tv[2 * ls.level + 1];
+    }
     uint32_t e;
     RETF(read_err(c, st, &e));
     RETF(err_status(e));

@@ -189,6 +189,8 @@ cudaError_t launch_validate_cands(const fem_episode *c, const uint32_t *gather, 
 cudaError_t launch_len_flags(const fem_episode *c, const uint32_t *gather, uint32_t m, uint32_t N,
                              uint8_t *flags, cudaStream_t st);
 // dst[i] = outer ? outer[inner[i]] : inner[i]
+cudaError_t launch_touched(const fem_episode *cands, const uint32_t *gather, uint32_t m,
+                           const uint32_t *hist, unsigned long long *out, cudaStream_t st);
 cudaError_t launch_compose_idx(const uint32_t *outer, const uint32_t *inner, uint32_t m,
                                uint32_t *dst, cudaStream_t st);
 // stable compaction: keep[i] = (vals[i] >= theta) (or flags[i] != 0 if vals == NULL)

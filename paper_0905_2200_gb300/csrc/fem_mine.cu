@@ -447,6 +447,30 @@ cudaError_t launch_compose_idx(const uint32_t *outer, const uint32_t *inner, uin
     return cudaGetLastError();
 }
 
+// Work measure of a counting pass: sum over the (gathered) candidates of the events
+// of their types, from the type histogram; one 64-bit atomic per warp.
+__global__ void k_touched(const fem_episode *__restrict__ cands, const uint32_t *__restrict__ gather,
+                          uint32_t m, const uint32_t *__restrict__ hist,
+                          unsigned long long *out) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long v = 0;
+    if (i < m) {
+        const fem_episode e = cands[gather ? gather[i] : i];
+        for (uint32_t k = 0; k < e.len && k < FEM_MAX_LEN; ++k) v += hist[e.types[k]];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    if ((threadIdx.x & 31u) == 0 && v) atomicAdd(out, v);
+}
+
+cudaError_t launch_touched(const fem_episode *cands, const uint32_t *gather, uint32_t m,
+                           const uint32_t *hist, unsigned long long *out, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    k_touched<<<(m + 255) / 256, 256, 0, st>>>(cands, gather, m, hist, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ level-wise generation
 // Frequent types: hist[a] >= theta, in increasing type order (one block, K <= 256).
 __global__ void k_type_filter(const uint32_t *hist, uint32_t K, uint32_t theta, uint32_t *ftypes,

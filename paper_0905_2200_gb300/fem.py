@@ -20,7 +20,7 @@ MAX_LEN = 8
 PASS_RELAXED, PASS_EXACT = 0, 1
 STATUS = {0: "FEM_OK", -1: "FEM_EINVAL", -2: "FEM_EUNSORTED", -3: "FEM_ETYPE",
           -4: "FEM_ERANGE", -5: "FEM_ENOMEM", -6: "FEM_EADMIT", -7: "FEM_ETIMEOUT",
-          -8: "FEM_ECUDA", -9: "FEM_EOVERFLOW", -10: "FEM_ENOSTREAM"}
+          -8: "FEM_ECUDA", -9: "FEM_EOVERFLOW", -10: "FEM_ENOSTREAM", -11: "FEM_EIO"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libfem.so")
@@ -49,7 +49,8 @@ class fem_level_stats(ctypes.Structure):
                 ("ms_relaxed", ctypes.c_float), ("ms_compact", ctypes.c_float),
                 ("ms_exact", ctypes.c_float), ("ms_relaxed_kernel", ctypes.c_float),
                 ("ms_relaxed_stitch", ctypes.c_float), ("ms_exact_kernel", ctypes.c_float),
-                ("exact_segments", ctypes.c_uint32)]
+                ("exact_segments", ctypes.c_uint32), ("touched_relaxed", ctypes.c_uint64),
+                ("touched_exact", ctypes.c_uint64)]
 
 
 class fem_job(ctypes.Structure):
@@ -72,7 +73,8 @@ EXPORTS = ["fem_create", "fem_destroy", "fem_set_config", "fem_load_stream", "fe
            "fem_batch_create", "fem_batch_run", "fem_batch_destroy",
            "fem_server_create", "fem_server_destroy", "fem_server_open_stream",
            "fem_server_append", "fem_server_submit", "fem_server_poll", "fem_server_result",
-           "fem_server_release", "fem_server_drain"]
+           "fem_server_release", "fem_server_drain", "fem_tune_enable", "fem_tune_size",
+           "fem_tune_save", "fem_tune_load"]
 
 _lib = None
 
@@ -107,6 +109,10 @@ def load(path: str | None = None):
         "fem_result_free": (None, [vp]),
         "fem_last_mine_stats": (I, [vp, ctypes.POINTER(fem_level_stats), u32]),
         "fem_strerror": (ctypes.c_char_p, [I]),
+        "fem_tune_enable": (I, [vp, I]),
+        "fem_tune_size": (I, [vp, ctypes.POINTER(u32)]),
+        "fem_tune_save": (I, [vp, ctypes.c_char_p]),
+        "fem_tune_load": (I, [vp, ctypes.c_char_p]),
         "fem_kernel_launches": (u64, []),
         "fem_select_noalloc": (I, [vp, u32, u32, vp, vp, vp]),
         "fem_batch_create": (I, [vp, ctypes.POINTER(fem_job), u32, ctypes.POINTER(fem_interval),
@@ -211,6 +217,25 @@ def fem_set_config(ctx, segments=0, threads_per_block=0, ring_capacity=0, reset=
         return
     cfg = fem_config(int(segments), int(threads_per_block), int(ring_capacity))
     _check(lib.fem_set_config(ctx, ctypes.byref(cfg)), "fem_set_config")
+
+
+def fem_tune_enable(ctx, on=True):
+    """Measured mapping choice on (or off) for counts whose class is not cached."""
+    _check(load().fem_tune_enable(ctx, 1 if on else 0), "fem_tune_enable")
+
+
+def fem_tune_size(ctx) -> int:
+    n = ctypes.c_uint32()
+    _check(load().fem_tune_size(ctx, ctypes.byref(n)), "fem_tune_size")
+    return int(n.value)
+
+
+def fem_tune_save(ctx, path):
+    _check(load().fem_tune_save(ctx, os.fsencode(path)), "fem_tune_save")
+
+
+def fem_tune_load(ctx, path):
+    _check(load().fem_tune_load(ctx, os.fsencode(path)), "fem_tune_load")
 
 
 def fem_load_stream(ctx, types, t_us, n_types, stream=None) -> int:
