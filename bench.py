@@ -153,9 +153,9 @@ def reduce_max_sum(world, tmax: float, tsum: float, device="cpu"):
 
 
 # --------------------------------------------------------------------------- workload
-def workload(rank: int):
+def workload(rank: int, deep: bool = False):
     from paper_0905_2200_gb300 import synth
-    cfg = synth.single_recording(seed=0xFE02 + rank)
+    cfg = synth.single_recording(seed=0xFE02 + rank, deep=deep)
     return cfg
 
 
@@ -193,7 +193,7 @@ def run_ours(args, rank, world, local):
     fembuild.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg = workload(rank)
+    cfg = workload(rank, deep=args.workload == "deep")
     s = cfg["stream"]
     I, theta, max_len = cfg["intervals"], cfg["theta"], cfg["max_len"]
     n = s.n
@@ -677,8 +677,10 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="launch shapes from the fixed rule instead of measured ones")
-    ap.add_argument("--workload", choices=["single_recording", "batched", "serving", "large"],
-                    default="single_recording")
+    ap.add_argument("--workload",
+                    choices=["single_recording", "deep", "batched", "serving", "large"],
+                    default="single_recording",
+                    help="deep: the same recording mined at theta = 300 (levels 3-6 reached)")
     ap.add_argument("--session-s", type=float, default=20.0)
     ap.add_argument("--req-rate", type=float, default=10.0)
     ap.add_argument("--serve-budget-gb", type=int, default=16)

@@ -47,7 +47,14 @@ struct fem_ctx {
     std::map<std::string, DevBuf> bufs;
     std::vector<fem_level_stats> stats;
     std::vector<StreamDev> pool;  // buffers of freed streams, reused by later loads
-    cudaEvent_t ev[2] = {nullptr, nullptr};
+    // mining timings: [0,1] generation, [2,3] relaxed pass, [4,5] compaction, [6,7] exact
+    cudaEvent_t ev[8] = {};
+    // pinned host staging of each level's frequent set (copied out after the last sync)
+    struct PinBuf {
+        void *p = nullptr;
+        size_t cap = 0;
+    };
+    PinBuf pin[FEM_MAX_LEN + 1];
     cudaEvent_t kev[3] = {nullptr, nullptr, nullptr};  // around the counting kernel and stitch
     // measured mapping choice: launch shape per (N, pass, distinct, log2 m,
     // log2 chunks, K) class
@@ -98,6 +105,26 @@ int dbuf(fem_ctx *c, const char *name, size_t count, T **out) {
 
 cudaStream_t pick(fem_ctx *c, void *s) { return s ? static_cast<cudaStream_t>(s) : c->own; }
 
+// Pinned host buffer `slot` of at least `bytes` (contents are not kept on growth; the
+// stream is drained first, so no copy into the old buffer is in flight).
+int pinbuf(fem_ctx *c, uint32_t slot, size_t bytes, cudaStream_t st, void **out) {
+    fem_ctx::PinBuf &b = c->pin[slot];
+    if (b.cap < bytes) {
+        CK(cudaStreamSynchronize(st));
+        if (b.p) cudaFreeHost(b.p);
+        b.p = nullptr;
+        b.cap = 0;
+        const size_t nb = (std::max(bytes, (size_t)4096) + 4095) & ~(size_t)4095;
+        if (cudaMallocHost(&b.p, nb) != cudaSuccess) {
+            cudaGetLastError();
+            return FEM_ENOMEM;
+        }
+        b.cap = nb;
+    }
+    *out = b.p;
+    return FEM_OK;
+}
+
 int read_words(fem_ctx *c, const uint32_t *d, uint32_t n, uint32_t *h, cudaStream_t st) {
     CK(cudaMemcpyAsync(c->h_small, d, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -107,6 +134,17 @@ int read_words(fem_ctx *c, const uint32_t *d, uint32_t n, uint32_t *h, cudaStrea
 
 int read_err(fem_ctx *c, cudaStream_t st, uint32_t *err) {
     return read_words(c, c->d_err, 1, err, st);
+}
+
+// A device count and the error word, in one round trip.
+int read_count_err(fem_ctx *c, const uint32_t *d_count, uint32_t *count, uint32_t *err,
+                   cudaStream_t st) {
+    CK(cudaMemcpyAsync(c->h_small, d_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->h_small + 1, c->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *count = c->h_small[0];
+    *err = c->h_small[1];
+    return FEM_OK;
 }
 
 int err_status(uint32_t e) {
@@ -513,13 +551,19 @@ int fem_create(fem_ctx **out, int device) {
         cudaMalloc(&c->d_err, sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&c->d_small, 64 * sizeof(uint32_t)) != cudaSuccess ||
         cudaMallocHost(&c->h_small, 64 * sizeof(uint32_t)) != cudaSuccess ||
-        cudaEventCreate(&c->ev[0]) != cudaSuccess || cudaEventCreate(&c->ev[1]) != cudaSuccess ||
         cudaEventCreate(&c->kev[0]) != cudaSuccess || cudaEventCreate(&c->kev[1]) != cudaSuccess ||
         cudaEventCreate(&c->kev[2]) != cudaSuccess || cudaEventCreate(&c->tev[0]) != cudaSuccess ||
         cudaEventCreate(&c->tev[1]) != cudaSuccess) {
         cudaGetLastError();
         fem_destroy(c);
         return FEM_ECUDA;
+    }
+    for (auto &e : c->ev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            fem_destroy(c);
+            return FEM_ECUDA;
+        }
     }
     cudaMemset(c->d_err, 0, sizeof(uint32_t));
     *out = c;
@@ -542,6 +586,8 @@ int fem_destroy(fem_ctx *c) {
     for (auto &e : c->tev)
         if (e) cudaEventDestroy(e);
     for (StreamDev &s : c->pool) free_stream_buffers(s);
+    for (auto &b : c->pin)
+        if (b.p) cudaFreeHost(b.p);
     if (c->own) cudaStreamDestroy(c->own);
     delete c;
     return FEM_OK;
@@ -839,11 +885,15 @@ int fem_mine_levelwise(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t n
     uint32_t *ftypes;
     RETF(dbuf(c, "ftypes", 256, &ftypes));
     CKF(launch_type_filter(s.hist, s.K, theta, ftypes, c->d_small + W_COUNT0, st));
-    std::vector<uint32_t> hist(s.K), ft(256);
-    CKF(cudaMemcpyAsync(hist.data(), s.hist, s.K * 4, cudaMemcpyDeviceToHost, st));
-    CKF(cudaMemcpyAsync(ft.data(), ftypes, 256 * 4, cudaMemcpyDeviceToHost, st));
-    uint32_t f1;
-    RETF(read_words(c, c->d_small + W_COUNT0, 1, &f1, st));
+    // histogram, frequent types and their number in one round trip (pinned staging)
+    void *h1;
+    RETF(pinbuf(c, 1, (2 * 256 + 1) * sizeof(uint32_t), st, &h1));
+    uint32_t *hist = static_cast<uint32_t *>(h1), *ft = hist + 256;
+    CKF(cudaMemcpyAsync(hist, s.hist, s.K * 4, cudaMemcpyDeviceToHost, st));
+    CKF(cudaMemcpyAsync(ft, ftypes, 256 * 4, cudaMemcpyDeviceToHost, st));
+    CKF(cudaMemcpyAsync(ft + 256, c->d_small + W_COUNT0, 4, cudaMemcpyDeviceToHost, st));
+    CKF(cudaStreamSynchronize(st));
+    const uint32_t f1 = ft[256];
     for (uint32_t i = 0; i < f1; ++i) {
         fem_episode e;
         std::memset(&e, 0, sizeof(e));
@@ -867,56 +917,70 @@ int fem_mine_levelwise(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t n
     cudaEventRecord(c->ev[0], st);
     CKF(launch_level2(ftypes, f1, nI, cands, st));
     cudaEventRecord(c->ev[1], st);
-    float ms_gen = 0;
+    // Per level the host waits three times: for the survivor count, the frequent
+    // count and the next level's candidate count (each read together with the error
+    // word; capacity recounts, when flagged, run before the count is used).
+    // Timings are read from events after those waits; frequent sets are copied to
+    // pinned staging and moved into the result after the last wait.
+    uint32_t staged_f[FEM_MAX_LEN + 1] = {};
+    auto compact_and_read = [&](const uint32_t *vals, uint32_t mm, uint32_t *idx, uint32_t word,
+                                uint32_t *scratch, const PassLaunch &pl, uint32_t *kept,
+                                cudaEvent_t done) -> int {
+        CK(launch_compact(vals, nullptr, theta, mm, idx, c->d_small + word, scratch, st));
+        if (done) CK(cudaEventRecord(done, st));
+        uint32_t e;
+        RET(read_count_err(c, c->d_small + word, kept, &e, st));
+        if (e & (ERR_RING | ERR_TABLE | ERR_CLASS)) {
+            RET(count_finish(c, s, pl, e, st));
+            CK(launch_compact(vals, nullptr, theta, mm, idx, c->d_small + word, scratch, st));
+            RET(read_count_err(c, c->d_small + word, kept, &e, st));
+        }
+        return err_status(e);
+    };
     for (uint32_t N = 2; N <= max_len && m > 0; ++N) {
         fem_level_stats ls{};
         ls.level = N;
         ls.candidates = m;
-        ls.ms_generate = 0;
-        cudaEventSynchronize(c->ev[1]);
-        cudaEventElapsedTime(&ms_gen, c->ev[0], c->ev[1]);
-        ls.ms_generate = ms_gen;
         uint32_t *rel, *idx_s, *ex, *idx_f, *fidx, *fcnt, *scratch;
         fem_episode *F;
         RETF(dbuf(c, "rel", m, &rel));
         RETF(dbuf(c, "idx_s", m, &idx_s));
         RETF(dbuf(c, "scratch", compact_scratch_words(m), &scratch));
-        // first pass (Algorithm 3) on every candidate
-        PassInfo pi;
-        cudaEventRecord(c->ev[0], st);
-        RETF(count_pass(c, s, cands, nullptr, m, (int)N, d_ivl, nI, FEM_PASS_RELAXED, rel, true,
-                        st, &pi));
-        cudaEventRecord(c->ev[1], st);
+        // first pass (Algorithm 3) on every candidate, then eliminate relaxed < theta
+        PassLaunch plr;
+        cudaEventRecord(c->ev[2], st);
+        RETF(count_launch(c, s, cands, nullptr, m, (int)N, d_ivl, nI, FEM_PASS_RELAXED, rel, true,
+                          st, &plr));
+        cudaEventRecord(c->ev[3], st);
         CKF(launch_touched(cands, nullptr, m, s.hist, touched + 2 * N, st));
-        cudaEventSynchronize(c->ev[1]);
-        cudaEventElapsedTime(&ls.ms_relaxed, c->ev[0], c->ev[1]);
+        cudaEventRecord(c->ev[4], st);
+        uint32_t ms;
+        RETF(compact_and_read(rel, m, idx_s, W_COUNT0, scratch, plr, &ms, c->ev[5]));
+        PassInfo pi;
+        pass_info(c, plr, &pi);
+        cudaEventElapsedTime(&ls.ms_generate, c->ev[0], c->ev[1]);
+        cudaEventElapsedTime(&ls.ms_relaxed, c->ev[2], c->ev[3]);
         ls.segments = pi.segments;
         ls.ms_relaxed_kernel = pi.ms_kernel;
         ls.ms_relaxed_stitch = pi.ms_stitch;
-        // eliminate relaxed < theta
-        cudaEventRecord(c->ev[0], st);
-        CKF(launch_compact(rel, nullptr, theta, m, idx_s, c->d_small + W_COUNT0, scratch, st));
-        cudaEventRecord(c->ev[1], st);
-        uint32_t ms;
-        RETF(read_words(c, c->d_small + W_COUNT0, 1, &ms, st));
-        cudaEventElapsedTime(&ls.ms_compact, c->ev[0], c->ev[1]);
         ls.survivors = ms;
-        // second pass (Algorithm 1) on the survivors
+        // second pass (Algorithm 1) on the survivors, then keep exact >= theta
         RETF(dbuf(c, "ex", ms, &ex));
         RETF(dbuf(c, "idx_f", ms, &idx_f));
-        cudaEventRecord(c->ev[0], st);
+        PassLaunch plx;
+        cudaEventRecord(c->ev[6], st);
+        RETF(count_launch(c, s, cands, idx_s, ms, (int)N, d_ivl, nI, FEM_PASS_EXACT, ex, true, st,
+                          &plx));
+        cudaEventRecord(c->ev[7], st);
+        CKF(launch_touched(cands, idx_s, ms, s.hist, touched + 2 * N + 1, st));
+        uint32_t f = 0;
+        if (ms) RETF(compact_and_read(ex, ms, idx_f, W_COUNT1, scratch, plx, &f, nullptr));
         PassInfo pe;
-        RETF(count_pass(c, s, cands, idx_s, ms, (int)N, d_ivl, nI, FEM_PASS_EXACT, ex, true, st,
-                        &pe));
+        pass_info(c, plx, &pe);
+        cudaEventElapsedTime(&ls.ms_compact, c->ev[4], c->ev[5]);
+        cudaEventElapsedTime(&ls.ms_exact, c->ev[6], c->ev[7]);
         ls.ms_exact_kernel = pe.ms_kernel;
         ls.exact_segments = ms ? pe.segments : 0;
-        cudaEventRecord(c->ev[1], st);
-        CKF(launch_touched(cands, idx_s, ms, s.hist, touched + 2 * N + 1, st));
-        cudaEventSynchronize(c->ev[1]);
-        cudaEventElapsedTime(&ls.ms_exact, c->ev[0], c->ev[1]);
-        CKF(launch_compact(ex, nullptr, theta, ms, idx_f, c->d_small + W_COUNT1, scratch, st));
-        uint32_t f;
-        RETF(read_words(c, c->d_small + W_COUNT1, 1, &f, st));
         ls.frequent = f;
         c->stats.push_back(ls);
         if (f == 0) break;
@@ -926,16 +990,13 @@ int fem_mine_levelwise(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t n
         CKF(launch_compose_idx(idx_s, idx_f, f, fidx, st));
         CKF(launch_gather_episodes(cands, fidx, f, F, nullptr, nullptr, st));
         CKF(launch_gather_episodes(nullptr, idx_f, f, nullptr, ex, fcnt, st));
-        res->eps[N - 1].resize(f);
-        res->counts[N - 1].resize(f);
-        CKF(cudaMemcpyAsync(res->eps[N - 1].data(), F, (size_t)f * sizeof(fem_episode),
-                            cudaMemcpyDeviceToHost, st));
-        CKF(cudaMemcpyAsync(res->counts[N - 1].data(), fcnt, (size_t)f * 4,
-                            cudaMemcpyDeviceToHost, st));
-        if (N == max_len) {
-            CKF(cudaStreamSynchronize(st));
-            break;
-        }
+        void *h;
+        RETF(pinbuf(c, N, (size_t)f * (sizeof(fem_episode) + 4), st, &h));
+        CKF(cudaMemcpyAsync(h, F, (size_t)f * sizeof(fem_episode), cudaMemcpyDeviceToHost, st));
+        CKF(cudaMemcpyAsync(static_cast<uint8_t *>(h) + (size_t)f * sizeof(fem_episode), fcnt,
+                            (size_t)f * 4, cudaMemcpyDeviceToHost, st));
+        staged_f[N] = f;
+        if (N == max_len) break;
         // join level N -> N + 1
         uint32_t *jc, *joff;
         RETF(dbuf(c, "jc", f, &jc));
@@ -957,6 +1018,15 @@ int fem_mine_levelwise(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t n
     for (fem_level_stats &ls : c->stats) {
         ls.touched_relaxed = tv[2 * ls.level];
         ls.touched_exact = tv[2 * ls.level + 1];
+    }
+    for (uint32_t N = 2; N <= max_len; ++N) {
+        const uint32_t f = staged_f[N];
+        if (!f) continue;
+        const uint8_t *h = static_cast<const uint8_t *>(c->pin[N].p);
+        res->eps[N - 1].resize(f);
+        res->counts[N - 1].resize(f);
+        std::memcpy(res->eps[N - 1].data(), h, (size_t)f * sizeof(fem_episode));
+        std::memcpy(res->counts[N - 1].data(), h + (size_t)f * sizeof(fem_episode), (size_t)f * 4);
     }
     uint32_t e;
     RETF(read_err(c, st, &e));
