@@ -52,7 +52,9 @@ def build(force: bool = False) -> str:
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
+        # FEM_ORACLE_LIB names another build of fem_oracle.c: the mutation tests load
+        # copies with a planted mistake through it, to show the pins catch them
+        lib = ctypes.CDLL(os.environ.get("FEM_ORACLE_LIB") or build())
         u8p = ctypes.POINTER(ctypes.c_uint8)
         u32p = ctypes.POINTER(ctypes.c_uint32)
         i64p = ctypes.POINTER(ctypes.c_int64)
