@@ -360,7 +360,10 @@ def run_batched(args, rank, world, local):
                              exact_out=torch.zeros(len(sel), dtype=torch.int32, device="cuda"),
                              survived_out=torch.zeros(len(sel), dtype=torch.uint8, device="cuda")))
             units += float(len(sel)) * s.n
+    fem.fem_tune_enable(ctx, not args.no_tune)  # batch shapes measured at create time
+    t0 = time.perf_counter()
     b = fem.fem_batch_create(ctx, jobs, I)
+    create_s = time.perf_counter() - t0
     for _ in range(args.warmup):
         fem.fem_batch_run(b)
     torch.cuda.synchronize()
@@ -382,8 +385,12 @@ def run_batched(args, rank, world, local):
     launches = fem.fem_kernel_launches() - launches0
     ms_batched = ev0.elapsed_time(ev1) / args.steps
     ref = [(j["exact_out"].clone(), j["survived_out"].clone()) for j in jobs]
-    # plain form: one two-pass call per (recording, length), device buffers
+    # plain form: one two-pass call per (recording, length), device buffers; one untimed
+    # pass first (with tuning on it measures and caches the plain launch shapes too)
     plain_steps = max(1, min(3, args.steps))
+    for j in jobs:
+        fem.fem_count_two_pass(ctx, j["stream_id"], j["cands"], I, j["theta"],
+                               exact_out=j["exact_out"], survived_out=j["survived_out"])
     torch.cuda.synchronize()
     ev0.record()
     for _ in range(plain_steps):
@@ -412,7 +419,11 @@ def run_batched(args, rank, world, local):
                    "l2": "inputs larger than L2 (bucketed streams ~13 B/event)",
                    "step": "one fem_batch_run: relaxed pass, per-job elimination, exact pass, "
                            "scatter (graph replay)",
-                   "generate_s": round(gen_s, 1)},
+                   "generate_s": round(gen_s, 1),
+                   "mapping": ("rule (16 chunks per item)" if args.no_tune else
+                               "measured at create time (segment length and block sizes "
+                               "per length group)"),
+                   "create_s": round(create_s, 2)},
         "plain": {"value": units / (ms_plain / 1e3), "unit": UNIT, "ms_per_step": ms_plain,
                   "form": "one fem_count_two_pass call per (recording, episode length)",
                   "identical_results": bool(same)},

@@ -1068,7 +1068,9 @@ int fem_last_mine_stats(fem_ctx *c, fem_level_stats *out, uint32_t cap) {
 // ============================================================================ batches
 namespace {
 
-constexpr uint32_t kBatchChunksPerItem = 16;  // segment length of batched work items
+constexpr uint32_t kBatchChunksPerItem = 16;  // segment length of batched work items (rule)
+constexpr uint32_t kBatchMinChunksPerItem = 8;  // shortest segment length tried when tuning
+constexpr uint32_t kBatchMinThreads = 64;       // smallest block size tried when tuning
 
 struct BatchGroup {
     int N = 0;
@@ -1087,6 +1089,9 @@ struct BatchGroup {
     uint32_t *counters = nullptr;  // n_items_r, n_items_x, queue_r, queue_x, n_idx
     uint4 *tables = nullptr;
     uint32_t SB = 0, Tr = 128, Tx = 128, Rx = 16;
+    uint32_t cpi = kBatchChunksPerItem;  // chunks per work item (segment length)
+    std::vector<uint32_t> nch, mj;       // per group job: stream chunks, candidates
+    std::vector<CountParams> rj, xj;     // host templates of the per-job parameters
 };
 
 }  // namespace
@@ -1125,10 +1130,32 @@ void batch_free(fem_batch *b) {
     delete b;
 }
 
-// The whole two-pass count of the batch, enqueued on st without host round trips.
-int batch_enqueue(fem_batch *b, cudaStream_t st) {
-    fem_ctx *c = b->ctx;
-    for (BatchGroup &g : b->groups) {
+// Set a group's launch shape: segment length (chunks per item) and block sizes of
+// the two passes; rewrites the per-job segment counts and table slices.
+int batch_shape(BatchGroup &g, uint32_t cpi, uint32_t Tr, uint32_t Tx, cudaStream_t st) {
+    g.cpi = cpi, g.Tr = Tr, g.Tx = Tx;
+    uint64_t toff = 0;
+    for (uint32_t k = 0; k < g.n_jobs; ++k) {
+        uint32_t P = (g.nch[k] + cpi - 1) / cpi;
+        const uint32_t cps = (g.nch[k] + P - 1) / P;
+        P = (g.nch[k] + cps - 1) / cps;
+        for (CountParams *q : {&g.rj[k], &g.xj[k]}) {
+            q->cps = cps;
+            q->P = P;
+            q->tables = g.tables + toff;
+        }
+        toff += (uint64_t)g.mj[k] * P * S_MAX;
+    }
+    CK(cudaMemcpyAsync(g.rjobs, g.rj.data(), g.n_jobs * sizeof(CountParams),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(g.xjobs, g.xj.data(), g.n_jobs * sizeof(CountParams),
+                       cudaMemcpyHostToDevice, st));
+    return FEM_OK;
+}
+
+// The two-pass count of one length group, enqueued on st without host round trips.
+int batch_enqueue_group(fem_ctx *c, BatchGroup &g, cudaStream_t st) {
+    {
         CK(cudaMemsetAsync(g.counters, 0, 8 * sizeof(uint32_t), st));
         CK(cudaMemsetAsync(g.redo, 0, g.m, st));
         CK(cudaMemsetAsync(g.xredo, 0, g.m, st));
@@ -1149,6 +1176,47 @@ int batch_enqueue(fem_batch *b, cudaStream_t st) {
                               g.counters + 3, g.SB, c->sm_count, st));
         CK(launch_stitch_batch(g.xjobs, g.cand_off, g.n_jobs, g.m, c->d_err, st));
         CK(launch_batch_outputs(g.outs, g.cand_off, g.n_jobs, g.m, g.idx, g.counters + 4, g.ex, st));
+    }
+    return FEM_OK;
+}
+
+// The whole two-pass count of the batch, enqueued on st without host round trips.
+int batch_enqueue(fem_batch *b, cudaStream_t st) {
+    for (BatchGroup &g : b->groups) RET(batch_enqueue_group(b->ctx, g, st));
+    return FEM_OK;
+}
+
+// Batch launch shapes by measurement: for each length group, time every segment
+// length (8, 16, 32 chunks per item) and block size pair, each a complete two-pass
+// count, and keep the fastest.
+int batch_tune(fem_batch *b, cudaStream_t st) {
+    fem_ctx *c = b->ctx;
+    for (BatchGroup &g : b->groups) {
+        float best = -1;
+        uint32_t bc = g.cpi, br = g.Tr, bx = g.Tx;
+        for (uint32_t cpi : {8u, 16u, 32u}) {
+            for (uint32_t Tr : {128u, 256u}) {
+                if (Tr == 256 && g.N > 3) continue;
+                for (uint32_t Tx : {64u, 128u}) {
+                    RET(batch_shape(g, cpi, Tr, Tx, st));
+                    CK(cudaMemsetAsync(c->d_err, 0, 4, st));
+                    CK(cudaEventRecord(c->tev[0], st));
+                    RET(batch_enqueue_group(c, g, st));
+                    CK(cudaEventRecord(c->tev[1], st));
+                    uint32_t e;
+                    RET(read_err(c, st, &e));
+                    RET(err_status(e));
+                    float ms = 0;
+                    CK(cudaEventElapsedTime(&ms, c->tev[0], c->tev[1]));
+                    if (e & (ERR_RING | ERR_TABLE | ERR_CLASS)) ms *= 4;  // needs recounts
+                    if (best < 0 || ms < best) best = ms, bc = cpi, br = Tr, bx = Tx;
+                }
+            }
+        }
+        RET(batch_shape(g, bc, br, bx, st));
+        if (std::getenv("FEM_DEBUG"))
+            std::fprintf(stderr, "fem: batch N=%d jobs=%u m=%u: %u chunks per item, T %u/%u, %.3f ms\n",
+                         g.N, g.n_jobs, g.m, bc, br, bx, best);
     }
     return FEM_OK;
 }
@@ -1197,39 +1265,41 @@ int fem_batch_create(fem_ctx *c, const fem_job *jobs, uint32_t n_jobs, const fem
         BatchGroup g;
         g.N = N;
         struct Ent {
-            uint32_t j, P, cps;
+            uint32_t j, nch;
         };
         std::vector<Ent> ents;
         for (uint32_t j = 0; j < n_jobs; ++j) {
             if ((int)jobs[j].len != N || jobs[j].m == 0) continue;
             const StreamDev &s = *find_stream(c, jobs[j].stream_id);
-            const uint32_t nch = std::max<uint32_t>(s.n_chunks, 1);
-            uint32_t P = (nch + kBatchChunksPerItem - 1) / kBatchChunksPerItem;
-            const uint32_t cps = (nch + P - 1) / P;
-            P = (nch + cps - 1) / cps;
-            ents.push_back({j, P, cps});
+            ents.push_back({j, std::max<uint32_t>(s.n_chunks, 1)});
         }
         if (ents.empty()) continue;
-        // longest items first: the persistent blocks then finish together
+        // longest streams first: with equal segment lengths their items are the
+        // longest, and the persistent blocks then finish together
         std::stable_sort(ents.begin(), ents.end(),
-                         [](const Ent &a, const Ent &b2) { return a.cps > b2.cps; });
+                         [](const Ent &a, const Ent &b2) { return a.nch > b2.nch; });
         g.n_jobs = (uint32_t)ents.size();
         g.Tr = N <= 3 ? 256 : 128;
         g.Tx = 128;
         g.Rx = 16;
-        uint64_t m = 0, tab = 0, cap_r = 0, cap_x = 0;
+        // capacities for every shape batch_shape may set (shortest segments, smallest
+        // blocks)
+        uint64_t m = 0, tab = 0, cap = 0;
         uint32_t max_offs = 8;
         g.off.push_back(0);
         for (const Ent &e : ents) {
             const fem_job &jb = jobs[e.j];
             g.user_job.push_back(e.j);
+            g.nch.push_back(e.nch);
+            g.mj.push_back(jb.m);
             m += jb.m;
             g.off.push_back((uint32_t)m);
-            tab += (uint64_t)jb.m * e.P * S_MAX;
-            cap_r += (uint64_t)((jb.m + g.Tr - 1) / g.Tr) * e.P;
-            cap_x += (uint64_t)((jb.m + g.Tx - 1) / g.Tx) * e.P;
+            const uint64_t Pmax = (e.nch + kBatchMinChunksPerItem - 1) / kBatchMinChunksPerItem;
+            tab += (uint64_t)jb.m * Pmax * S_MAX;
+            cap += (uint64_t)((jb.m + kBatchMinThreads - 1) / kBatchMinThreads) * Pmax;
             max_offs = std::max(max_offs, find_stream(c, jb.stream_id)->offs);
         }
+        const uint64_t cap_r = cap, cap_x = cap;
         if (m > 0xFFFFFFF0ull || cap_r > 0xFFFFFFF0ull) return fail(FEM_ENOMEM);
         g.m = (uint32_t)m;
         g.cap_r = (uint32_t)cap_r;
@@ -1255,10 +1325,11 @@ int fem_batch_create(fem_ctx *c, const fem_job *jobs, uint32_t n_jobs, const fem
         BRET(balloc(b, cap_x, &g.items_x));
         BRET(balloc(b, 8, &g.counters));
         BRET(balloc(b, tab, &g.tables));
-        std::vector<CountParams> rj(n), xj(n);
+        std::vector<CountParams> &rj = g.rj, &xj = g.xj;
+        rj.resize(n);
+        xj.resize(n);
         std::vector<uint32_t> th(n);
         std::vector<BatchOut> bo(n);
-        uint64_t toff = 0;
         for (uint32_t k = 0; k < n; ++k) {
             const fem_job &jb = jobs[ents[k].j];
             const StreamDev &s = *find_stream(c, jb.stream_id);
@@ -1275,11 +1346,7 @@ int fem_batch_create(fem_ctx *c, const fem_job *jobs, uint32_t n_jobs, const fem
             p.K = s.K;
             p.ivl = b->ivl;
             p.n_ivl = nI;
-            p.cps = ents[k].cps;
-            p.P = ents[k].P;
-            p.tables = g.tables + toff;
-            p.err = c->d_err;
-            toff += (uint64_t)jb.m * ents[k].P * S_MAX;
+            p.err = c->d_err;  // segments and tables: batch_shape
             CountParams r = p, x = p;
             r.cands = g.cands + g.off[k];
             r.m = jb.m;
@@ -1293,15 +1360,16 @@ int fem_batch_create(fem_ctx *c, const fem_job *jobs, uint32_t n_jobs, const fem
             th[k] = jb.theta;
             bo[k] = BatchOut{jb.exact_out, jb.survived_out};
         }
-        BCK(cudaMemcpyAsync(g.rjobs, rj.data(), n * sizeof(CountParams), cudaMemcpyHostToDevice, st));
-        BCK(cudaMemcpyAsync(g.xjobs, xj.data(), n * sizeof(CountParams), cudaMemcpyHostToDevice, st));
+        BRET(batch_shape(g, kBatchChunksPerItem, g.Tr, g.Tx, st));
         BCK(cudaMemcpyAsync(g.cand_off, g.off.data(), (n + 1) * 4, cudaMemcpyHostToDevice, st));
         BCK(cudaMemcpyAsync(g.theta, th.data(), n * 4, cudaMemcpyHostToDevice, st));
         BCK(cudaMemcpyAsync(g.outs, bo.data(), n * sizeof(BatchOut), cudaMemcpyHostToDevice, st));
         BCK(cudaStreamSynchronize(st));  // host staging vectors go out of scope
         b->groups.push_back(std::move(g));
     }
-    // one eager run (sets kernel attributes, checks the inputs), then capture
+    // measured shapes when tuning is on; one eager run (sets kernel attributes, checks
+    // the inputs); then capture
+    if (c->tune_on) BRET(batch_tune(b, st));
     BRET(fem_batch_run(b, cuda_stream));
     BCK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
     BCK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));

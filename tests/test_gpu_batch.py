@@ -36,8 +36,12 @@ def make_jobs(ctx, batch, torch):
     return jobs, meta
 
 
-def test_batch_equals_single_recording_path_and_oracle(ctx):
+@pytest.mark.parametrize("tune", [False, True])
+def test_batch_equals_single_recording_path_and_oracle(ctx, tune):
+    """With tuning on, fem_batch_create first times every segment length / block size
+    pair per length group (each a complete count) and captures the fastest."""
     torch = pytest.importorskip("torch")
+    fem.fem_tune_enable(ctx, tune)
     batch = synth.batched_recordings(seed=0xB7, n_rec=10, t_range=(5.0, 150.0),
                                      m_range=(40, 1500))
     I = batch["intervals"]
@@ -75,3 +79,4 @@ def test_batch_equals_single_recording_path_and_oracle(ctx):
                                 f"job {k} oracle ex")
     finally:
         fem.fem_batch_destroy(b)
+        fem.fem_tune_enable(ctx, False)

@@ -113,6 +113,45 @@ def test_single_recording_mining_sampled(ctx, single_recording):
     assert np.all(want < theta)
 
 
+def test_single_recording_deep_sampled(ctx):
+    """The deep variant (theta = 300; about 12.5k frequent pairs, 2.4M level-3
+    candidates): at every level the candidate count equals the oracle's join of the
+    device's previous frequent set, sampled reported episodes have the oracle's exact
+    count, and sampled candidates not reported are below theta per the oracle."""
+    cfg = synth.single_recording(deep=True)
+    s = cfg["stream"]
+    I, theta = cfg["intervals"], cfg["theta"]
+    sid = fem.fem_load_stream(ctx, s.types, s.t, s.n_types)
+    got = fem.fem_mine_levelwise(ctx, sid, I, theta, cfg["max_len"])
+    stats = fem.fem_last_mine_stats(ctx)
+    fem.fem_free_stream(ctx, sid)
+    assert max(got) >= 3 and stats[1]["candidates"] > 1_000_000
+    rng = np.random.default_rng(7)
+    for st in stats:
+        N = st["level"]
+        rows = got.get(N, [])
+        assert st["frequent"] == len(rows)
+        if N == 2:
+            ft = [r[0][0] for r in got[1]]
+            L, E, iv = synth.level2_candidates(ft, len(I))
+            cands = [((int(E[i, 0]), int(E[i, 1])), (int(iv[i, 0]),)) for i in range(len(L))]
+        else:
+            cands = oracle.join([(r[0], r[1]) for r in got[N - 1]])
+        assert len(cands) == st["candidates"], f"level {N} candidates"
+        reported = {(r[0], r[1]): r[2] for r in rows}
+        if rows:
+            sel = [rows[i] for i in rng.choice(len(rows), min(48, len(rows)), replace=False)]
+            lens, E, iv = oracle._pack([(r[0], r[1]) for r in sel])
+            want = oracle.count_batch(s.types, s.t, lens, E, iv, I, oracle.EXACT)
+            assert_counts_equal([r[2] for r in sel], want, f"level {N} reported")
+        pool = [cands[i] for i in rng.choice(len(cands), min(400, len(cands)), replace=False)]
+        absent = [c for c in pool if c not in reported][:48]
+        if absent:
+            lens, E, iv = oracle._pack(absent)
+            want = oracle.count_batch(s.types, s.t, lens, E, iv, I, oracle.EXACT)
+            assert np.all(want < theta), f"level {N} missing a frequent episode"
+
+
 def test_large_stream_two_pass_sampled(ctx):
     """One hour at 50 Hz x 64 types (11.5M events), 100k candidates: Algorithm 4 on the
     device (autotuned mapping and one segment per chunk agree); 24 sampled candidates
