@@ -40,14 +40,16 @@ L2_FLUSH_BYTES = 256 << 20
 # deadline add, store/count; exact machine (Algorithm 1) pop test, window compare,
 # push (two more).
 OPS_PER_TOUCHED = {"relaxed": 4, "exact": 6}
-# DRAM bytes per launch of each counting launch of the mining step ("level/pass")
-# from one ncu capture, keyed by the SHA-256 of the kernel source it was taken on
-# (no entry: stale, reported as null).
+# DRAM bytes per launch of each counting launch of a workload's mining step
+# ("level/pass") from one ncu capture, keyed by the SHA-256 of the kernel source it was
+# taken on and the workload (no entry: stale or not captured, reported as null).
 NCU_TRAFFIC = {
     # counting kernels of commit 6fde740 (device code unchanged since), ncu --set full
     # of the first mining step: dram__bytes_read.sum + dram__bytes_write.sum per launch
-    "02eb35fb5593365f": {"2/relaxed": 4230400, "2/exact": 3986432, "3/relaxed": 3883008,
-                    "3/exact": 3727360},
+    "02eb35fb5593365f": {
+        "single_recording_64types_300s": {"2/relaxed": 4230400, "2/exact": 3986432,
+                                          "3/relaxed": 3883008, "3/exact": 3727360},
+    },
 }
 
 
@@ -263,7 +265,8 @@ def run_ours(args, rank, world, local):
     achieved = touched[dom] * ops / (avg_ms[dom] * 1e-3) / 1e12
     all_ops = sum(touched[k] * OPS_PER_TOUCHED[k[1]] for k in avg_ms)
     all_ach = all_ops / (sum(avg_ms.values()) * 1e-3) / 1e12
-    traffic = NCU_TRAFFIC.get(kernel_source_hash(), {}).get(f"{dom[0]}/{dom[1]}")
+    traffic = NCU_TRAFFIC.get(kernel_source_hash(), {}).get(cfg["name"], {}).get(
+        f"{dom[0]}/{dom[1]}")
     kname = f"k_count<{dom[0]}, {dom[1]}{', MapConcatenate' if dom_seg > 1 else ''}>"
 
     # end to end through the public API with host (pinned) buffers
@@ -436,8 +439,10 @@ def run_batched(args, rank, world, local):
 # --------------------------------------------------------------------------- large stream
 def run_large(args, rank, world, local):
     """One hour at 50 Hz x 64 types (~11.5M events), 100k random candidates of 3-5
-    nodes: the two-pass count with the autotuned mapping, and the same count forced
-    to one segment per chunk (thousands of MapConcatenate segments per episode)."""
+    nodes (or, for --workload bursty, a 300 s network-bursting recording with 36k
+    candidates): the two-pass count with the autotuned mapping, and the same count
+    forced to one segment per chunk (hundreds to thousands of MapConcatenate segments
+    per episode)."""
     import torch
 
     from paper_0905_2200_gb300 import build as fembuild
@@ -445,11 +450,15 @@ def run_large(args, rank, world, local):
 
     fembuild.build()
     torch.cuda.set_device(local)
-    cfg = synth.large_stream(seed=0xFE04 + rank)
+    bursty = args.workload == "bursty"
+    cfg = (synth.bursty_recording(seed=0xFE06 + rank) if bursty
+           else synth.large_stream(seed=0xFE04 + rank))
     s = cfg["stream"]
     I, theta = cfg["intervals"], cfg["theta"]
     L, E, iv = cfg["candidates"]
     ctx = fem.fem_create(local)
+    if not args.no_tune:
+        fem.fem_tune_enable(ctx, True)  # launch shapes measured during the warm-up steps
     sid = fem.fem_load_stream(ctx, torch.from_numpy(s.types).cuda(),
                               torch.from_numpy(s.t.view(np.int32)).cuda(), s.n_types)
     rec = torch.from_numpy(fem.pack_episodes(L, E, iv)).cuda()
@@ -458,18 +467,21 @@ def run_large(args, rank, world, local):
     sv = torch.zeros(m, dtype=torch.uint8, device="cuda")
     res = {}
     n_chunks = (s.n + 2047) // 2048
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     for name, seg in (("autotuned", 0), ("one_segment_per_chunk", n_chunks)):
         fem.fem_set_config(ctx, segments=seg)
         for _ in range(args.warmup):
             fem.fem_count_two_pass(ctx, sid, rec, I, theta, exact_out=ex, survived_out=sv)
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for i, (e0, e1) in enumerate(evs):
+            flush.fill_(i & 0xFF)  # L2 flush, outside the step's events
+            e0.record()
             fem.fem_count_two_pass(ctx, sid, rec, I, theta, exact_out=ex, survived_out=sv)
-        e1.record()
+            e1.record()
         torch.cuda.synchronize()
-        res[name] = (e0.elapsed_time(e1) / args.steps, ex.clone(), sv.clone())
+        res[name] = (sum(a.elapsed_time(b) for a, b in evs) / args.steps, ex.clone(), sv.clone())
     same = torch.equal(res["autotuned"][1], res["one_segment_per_chunk"][1])
     survivors = int(res["autotuned"][2].sum().item())
     frequent = int((res["autotuned"][1].view(torch.int32) >= theta).sum().item())
@@ -483,8 +495,9 @@ def run_large(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded Poisson spike trains with embedded cascades)",
         "config": {"workload": cfg["name"], "n_events": s.n, "n_types": s.n_types,
-                   "candidates": m, "lengths": [3, 5], "theta": theta,
-                   "l2": "inputs larger than L2 (150 MB bucketed stream)",
+                   "candidates": m, "lengths": [int(L.min()), int(L.max())], "theta": theta,
+                   "intervals_us": I.tolist(),
+                   "l2": "flushed between steps (256 MiB device write outside the step events)",
                    "step": "fem_count_two_pass over all candidates (Algorithm 4)"},
         "two_pass": {"survivors": survivors, "frequent": frequent,
                      "pruning_ratio": 1 - survivors / m},
@@ -689,7 +702,8 @@ def main(argv=None):
     ap.add_argument("--no-tune", action="store_true",
                     help="launch shapes from the fixed rule instead of measured ones")
     ap.add_argument("--workload",
-                    choices=["single_recording", "deep", "batched", "serving", "large"],
+                    choices=["single_recording", "deep", "batched", "serving", "large",
+                             "bursty"],
                     default="single_recording",
                     help="deep: the same recording mined at theta = 300 (levels 3-6 reached)")
     ap.add_argument("--session-s", type=float, default=20.0)
@@ -707,7 +721,7 @@ def main(argv=None):
             run_batched(args, rank, world, local)
         elif args.workload == "serving":
             run_serving(args, rank, world, local)
-        elif args.workload == "large":
+        elif args.workload in ("large", "bursty"):
             run_large(args, rank, world, local)
         else:
             run_ours(args, rank, world, local)

@@ -126,6 +126,53 @@ def single_recording(seed=0xFE02, deep=False):
                 stream=Stream(ty, t, 64, ch), intervals=I_MS4.copy(), theta=theta, max_len=6)
 
 
+# Interval set of the bursty workload: I_MS4's first three plus (15,20] ms, whose
+# hi < 2 lo lets more than two clusters of a list be live (the shared-memory rings).
+I_BURST = np.array([[0, 2000], [2000, 5000], [5000, 10000], [15000, 20000]], np.uint32)
+
+
+def bursty_recording(seed=0xFE06, n_types=64, duration_s=300.0, base_hz=5.0,
+                     burst_hz=0.5, burst_ms=(50.0, 200.0), burst_rate_hz=200.0):
+    """A network-bursting culture: every type fires at `base_hz`, and network bursts
+    (Poisson, `burst_hz`; duration uniform in `burst_ms`) make every type fire at
+    `burst_rate_hz` for the burst's length; 8 chains of 4-6 nodes at 1-3 Hz with
+    delays inside I_BURST.  Candidates: all 16,128 ordered pairs x I_BURST plus 20,000
+    random episodes of 3-4 nodes; threshold 5x the chance count of the narrowest
+    interval at the mean rate (903), which most pairs pass inside bursts, so the exact
+    pass (Algorithm 4's second pass) runs on most of them."""
+    rng = _rng(seed + 0x100)
+    ch = _chains(rng, 8, n_types, [4, 5, 6], len(I_BURST), 1.0, 3.0)
+    spec = [(tys, rate, [tuple(I_BURST[i]) for i in ivs]) for tys, ivs, rate in ch]
+    t, ty = poisson_stream(seed, n_types, base_hz, duration_s, chains=spec)
+    # bursts: per burst, every type a Poisson count over its span
+    T_us = int(round(duration_s * 1e6))
+    nb = rng.poisson(burst_hz * duration_s)
+    b0 = np.floor(rng.random(nb) * T_us).astype(np.int64)
+    blen = (rng.uniform(burst_ms[0], burst_ms[1], nb) * 1000).astype(np.int64)
+    bt, bty = [], []
+    for start, ln in zip(b0, blen):
+        k = rng.poisson(burst_rate_hz * ln * 1e-6, size=n_types)
+        tot = int(k.sum())
+        bt.append(start + np.floor(rng.random(tot) * ln).astype(np.int64))
+        bty.append(np.repeat(np.arange(n_types), k))
+    if nb:
+        t2 = np.concatenate([t.astype(np.int64)] + bt)
+        ty2 = np.concatenate([ty.astype(np.int64)] + bty)
+        emit = np.arange(t2.shape[0])
+        keep = t2 < T_us
+        t2, ty2, emit = t2[keep], ty2[keep], emit[keep]
+        order = np.lexsort((emit, ty2, t2))
+        t, ty = t2[order].astype(np.uint32), ty2[order].astype(np.uint8)
+    mean_hz = base_hz + burst_hz * np.mean(burst_ms) * 1e-3 * burst_rate_hz
+    theta = chance_theta(mean_hz, duration_s, 0.002)
+    L2, E2, iv2 = level2_candidates(range(n_types), len(I_BURST))
+    L3, E3, iv3 = random_candidates(seed + 0x200, 20_000, n_types, [3, 4], len(I_BURST))
+    cands = (np.concatenate([L2, L3]), np.concatenate([E2, E3]), np.concatenate([iv2, iv3]))
+    return dict(name=f"bursty_recording_{n_types}types_{int(duration_s)}s",
+                stream=Stream(ty, t, n_types, ch), intervals=I_BURST.copy(), theta=theta,
+                candidates=cands, bursts=(b0, blen))
+
+
 def large_stream(seed=0xFE04, n_candidates=100_000, duration_s=3600.0):
     """64 types at 50 Hz for 1 h plus 8 chains; 100k random candidates of lengths 3-5
     with distinct types and random intervals from I_MS4; threshold 5x the chance
