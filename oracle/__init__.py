@@ -71,6 +71,9 @@ def _load():
         lib.orc_two_pass.restype = ctypes.c_int
         lib.orc_two_pass.argtypes = [u8p, u32p, i64, i64, u8p, u8p, u32p, u32p,
                                      ctypes.c_uint32, u32p, u32p, u8p]
+        lib.orc_count_mapconcat_literal.restype = ctypes.c_uint32
+        lib.orc_count_mapconcat_literal.argtypes = [u8p, u32p, i64, ctypes.c_int, u8p, u32p,
+                                                    u32p, i64, i64p, i64p, i64p]
         lib.orc_count_mapconcat.restype = ctypes.c_uint32
         lib.orc_count_mapconcat.argtypes = [u8p, u32p, i64, ctypes.c_int, u8p, u32p, u32p,
                                             ctypes.c_int, i64, i64p, i64p]
@@ -144,6 +147,28 @@ def count_mapconcat(types, t, ep_types, lo, hi, bounds, pass_=EXACT, return_size
     if r == 0xFFFFFFFF:
         raise ValueError("bad segmentation or out of memory")
     return (int(r), sizes[:P]) if return_sizes else int(r)
+
+
+def count_mapconcat_literal(types, t, ep_types, lo, hi, tau):
+    """MapConcatenate as the paper prints it (Section 5.2.2; readings in fem_oracle.c):
+    time segments (tau[p], tau[p+1]], N machines per segment, tuples (a, count, b)
+    joined where b equals a.  Returns (count, tuples int64[P, N, 3], diag) where diag =
+    (boundaries where no tuple matched, boundaries where several did)."""
+    lib = _load()
+    types, t = _stream(types, t)
+    N = len(ep_types)
+    E, L, H = _edges(ep_types, lo, hi)
+    tau = np.ascontiguousarray(tau, dtype=np.int64)
+    P = len(tau) - 1
+    tup = np.zeros((max(P, 1), N, 3), np.int64)
+    diag = np.zeros(2, np.int64)
+    r = lib.orc_count_mapconcat_literal(_p(types, ctypes.c_uint8), _p(t, ctypes.c_uint32),
+                                        len(t), N, _p(E, ctypes.c_uint8), _p(L, ctypes.c_uint32),
+                                        _p(H, ctypes.c_uint32), P, _p(tau, ctypes.c_int64),
+                                        _p(tup, ctypes.c_int64), _p(diag, ctypes.c_int64))
+    if r == 0xFFFFFFFF:
+        raise ValueError("bad time segmentation or out of memory")
+    return int(r), tup[:P], (int(diag[0]), int(diag[1]))
 
 
 # --------------------------------------------------------------------------- candidate batches

@@ -378,3 +378,129 @@ uint32_t orc_count_mapconcat(const uint8_t *type, const uint32_t *t, int64_t n, 
     }
     return total;
 }
+
+/* ------------------------------------------------------------------------ */
+/*
+ * MapConcatenate as the paper prints it (Section 5.2.2), kept as a documented
+ * comparison with the exact reformulation above.  Readings (R13):
+ *   - segment p holds the events with tau[p] < t <= tau[p+1] (times, not indices);
+ *   - machine k (0 <= k < N) of segment p runs Algorithm 1 (pruned lists) on the
+ *     events with t > tau[p] - (hi[0] + ... + hi[k-1]);
+ *   - it counts the completions with tau[p] < t <= tau[p+1]; a is the end time of
+ *     its first completion with tau[p] < t < tau[p] + W (W = sum of hi), else
+ *     tau[p];
+ *   - past tau[p+1] it only advances the partial occurrences it holds (node 0
+ *     admits nothing), over the events with t < tau[p+1] + W; b is the end time
+ *     of the first completion there, else tau[p+1];
+ *   - Concatenate joins a tuple (a, c, b) of segment p to the tuple of segment
+ *     p+1 whose a equals b, starting from machine 0 of segment 0; when several
+ *     tuples match it takes the smallest k, when none matches it takes k = 0 and
+ *     counts the boundary in diag[0] (diag[1] counts boundaries with several).
+ * The paper composes the tuples pairwise in a tree; with a single choice per
+ * boundary that composition equals this left-to-right one.
+ */
+
+/* Algorithm 1 step with pruned lists; with allow_start == 0 node 0 admits
+ * nothing.  Returns 1 on a completion (the lists are then empty). */
+static int literal_step(tlist *s, int N, const uint8_t *E, const uint32_t *lo,
+                        const uint32_t *hi, uint8_t ty, uint32_t tt, int allow_start,
+                        int *oom)
+{
+    for (int i = N - 1; i >= 0; i--) {
+        if (ty != E[i]) continue;
+        if (i == 0) {
+            if (!allow_start) continue;
+            if (N == 1) return 1;
+            tlist *L0 = &s[0];
+            while (L0->head < L0->len && tt - L0->v[L0->head] > hi[0]) L0->head++;
+            if (tl_push(L0, tt)) { *oom = 1; return 0; }
+            continue;
+        }
+        tlist *Q = &s[i - 1];
+        while (Q->head < Q->len && tt - Q->v[Q->head] > hi[i - 1]) Q->head++;
+        if (!(Q->head < Q->len && tt - Q->v[Q->head] > lo[i - 1])) continue;
+        if (i == N - 1) {
+            for (int k = 0; k < N; k++) tl_clear(&s[k]);
+            return 1;
+        }
+        tlist *L = &s[i];
+        while (L->head < L->len && tt - L->v[L->head] > hi[i]) L->head++;
+        if (tl_push(L, tt)) { *oom = 1; return 0; }
+    }
+    return 0;
+}
+
+/* First index j with t[j] > x (n if none). */
+static int64_t first_after(const uint32_t *t, int64_t n, int64_t x)
+{
+    int64_t a = 0, b = n;
+    while (a < b) {
+        int64_t mid = a + (b - a) / 2;
+        if ((int64_t)t[mid] > x) b = mid; else a = mid + 1;
+    }
+    return a;
+}
+
+/*
+ * tau: int64[P+1], strictly increasing, tau[0] < t[0], tau[P] >= t[n-1].
+ * tuples_out (optional): int64[P*N*3] = (a, count, b) of machine k of segment p
+ * at [(p*N + k)*3].  Returns the concatenated count (UINT32_MAX on error).
+ */
+uint32_t orc_count_mapconcat_literal(const uint8_t *type, const uint32_t *t, int64_t n,
+                                     int N, const uint8_t *E, const uint32_t *lo,
+                                     const uint32_t *hi, int64_t P, const int64_t *tau,
+                                     int64_t *tuples_out, int64_t *diag)
+{
+    if (P < 1 || N < 1 || N > ORC_LMAX) return UINT32_MAX;
+    for (int64_t p = 0; p < P; p++)
+        if (tau[p + 1] <= tau[p]) return UINT32_MAX;
+    if (n && (tau[0] >= (int64_t)t[0] || tau[P] < (int64_t)t[n - 1])) return UINT32_MAX;
+    int64_t W = 0;
+    for (int k = 0; k + 1 < N; k++) W += hi[k];
+    int64_t *tup = (int64_t *)malloc((size_t)(P * N * 3) * sizeof(int64_t));
+    if (!tup) return UINT32_MAX;
+    int oom = 0;
+    for (int64_t p = 0; p < P && !oom; p++) {
+        int64_t back = 0;
+        for (int k = 0; k < N && !oom; k++) {
+            if (k > 0) back += hi[k - 1];
+            tlist s[ORC_LMAX];
+            memset(s, 0, sizeof(s));
+            int64_t cnt = 0, a = tau[p], b = tau[p + 1];
+            int have_a = 0;
+            for (int64_t j = first_after(t, n, tau[p] - back); j < n; j++) {
+                int64_t tj = t[j];
+                int phase2 = tj > tau[p + 1];
+                if (phase2 && tj >= tau[p + 1] + W) break;
+                int done = literal_step(s, N, E, lo, hi, type[j], t[j], !phase2, &oom);
+                if (oom) break;
+                if (!done) continue;
+                if (phase2) { b = tj; break; }
+                if (tj > tau[p]) {
+                    cnt++;
+                    if (!have_a && tj < tau[p] + W) { a = tj; have_a = 1; }
+                }
+            }
+            for (int q = 0; q < ORC_LMAX; q++) tl_free(&s[q]);
+            int64_t *o = tup + (p * N + k) * 3;
+            o[0] = a; o[1] = cnt; o[2] = b;
+        }
+    }
+    if (oom) { free(tup); return UINT32_MAX; }
+    if (tuples_out) memcpy(tuples_out, tup, (size_t)(P * N * 3) * sizeof(int64_t));
+    int64_t none = 0, several = 0;
+    int64_t total = tup[1];
+    int64_t cur_b = tup[2];
+    for (int64_t p = 1; p < P; p++) {
+        int pick = -1, hits = 0;
+        for (int k = 0; k < N; k++)
+            if (tup[(p * N + k) * 3] == cur_b) { hits++; if (pick < 0) pick = k; }
+        if (hits == 0) { none++; pick = 0; }
+        if (hits > 1) several++;
+        total += tup[(p * N + pick) * 3 + 1];
+        cur_b = tup[(p * N + pick) * 3 + 2];
+    }
+    free(tup);
+    if (diag) { diag[0] = none; diag[1] = several; }
+    return (uint32_t)total;
+}

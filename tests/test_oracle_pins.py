@@ -33,7 +33,8 @@ def load_golden(name):
                 section = "stream"
                 continue
             if parts[0] in ("episode", "interval", "occurrences", "non_overlapped", "cut",
-                            "serial_count", "naive_segment_sum"):
+                            "serial_count", "naive_segment_sum", "tau", "exact_count",
+                            "literal_count", "no_match", "several"):
                 section = None
                 vals = [int(x) for x in parts[1:]]
                 if parts[0] == "interval":
@@ -369,3 +370,47 @@ def test_join_output_is_canonical_and_distinct_typed():
                    ((1, 2, 3), (0, 0)), ((1, 2, 3), (1, 0))]
     keys = [oracle.canonical_key(*c) for c in out]
     assert keys == sorted(keys)
+
+
+# --------------------------------------------------------------------------- MapConcatenate as printed
+@pytest.mark.parametrize("seed", range(30))
+def test_literal_mapconcat_single_segment_is_algorithm_1(seed):
+    """With one time segment the printed scheme is one machine over the whole stream."""
+    rng = np.random.default_rng(9000 + seed)
+    ty, t = synth.tiny_stream(9000 + seed, int(rng.integers(1, 40)), 3, 5, tie_prob=0.25)
+    E, lo, hi = random_episode(rng, 3, int(rng.integers(1, 4)), 8)
+    got = oracle.count_mapconcat_literal(ty, t, E, lo, hi, [int(t[0]) - 1, int(t[-1])])[0]
+    assert got == bf.count(ty, t, E, lo, hi)
+
+
+def test_literal_mapconcat_fig3_recovers_the_serial_count():
+    """Fig. 3's stream: a fresh machine on the second segment finds g and misses h3;
+    the printed scheme's machine started W earlier does not, so the count is the
+    serial one (3), where summing fresh per-segment machines gives 2."""
+    d, ty, t, E, lo, hi = load_golden("fig3_map_split.txt")
+    cut = d["cut"][0]
+    tau = [int(t[0]) - 1, int(t[cut - 1]), int(t[-1])]
+    got, tup, diag = oracle.count_mapconcat_literal(ty, t, E, lo, hi, tau)
+    assert got == d["serial_count"][0] == 3
+    assert tup[1, 0, 1] + tup[0, 0, 1] == d["naive_segment_sum"][0]   # machine 0 alone
+    assert tup[0, 0, 2] == tup[1, 1, 0]                              # b of seg 0 = a of machine 1
+
+
+@pytest.mark.parametrize("name", ["literal_mc_d1_short_segments.txt",
+                                  "literal_mc_d2_window_edge.txt",
+                                  "literal_mc_d3_machine_out_of_step.txt"])
+def test_literal_mapconcat_catalogued_divergences(name):
+    """Three hand-traced streams on which the printed scheme undercounts (the exact
+    reformulation does not): D1 occurrences spanning more than two segments, D2 an
+    occurrence ending exactly at tau + W, D3 machines out of step with the serial
+    machine's last completion."""
+    d, ty, t, E, lo, hi = load_golden(name)
+    got, tup, diag = oracle.count_mapconcat_literal(ty, t, E, lo, hi, d["tau"])
+    assert oracle.count_one(ty, t, E, lo, hi, oracle.EXACT) == bf.count(ty, t, E, lo, hi) \
+        == d["exact_count"][0]
+    assert got == d["literal_count"][0]
+    assert diag == (d["no_match"][0], d["several"][0])
+    # the exact reformulation over the same cut points (index ranges) is exact
+    idx = [0] + [int(np.searchsorted(t, x, side="right")) for x in d["tau"][1:-1]] + [len(t)]
+    idx = sorted(set(idx))
+    assert oracle.count_mapconcat(ty, t, E, lo, hi, idx) == d["exact_count"][0]
