@@ -455,8 +455,8 @@ uint32_t orc_count_mapconcat_literal(const uint8_t *type, const uint32_t *t, int
     for (int64_t p = 0; p < P; p++)
         if (tau[p + 1] <= tau[p]) return UINT32_MAX;
     if (n && (tau[0] >= (int64_t)t[0] || tau[P] < (int64_t)t[n - 1])) return UINT32_MAX;
-    int64_t W = 0;
-    for (int k = 0; k + 1 < N; k++) W += hi[k];
+    int64_t W = 0;   /* sum over the N - 1 edges of hi */
+    for (int k = 0; k < N - 1; k++) W += hi[k];
     int64_t *tup = (int64_t *)malloc((size_t)(P * N * 3) * sizeof(int64_t));
     if (!tup) return UINT32_MAX;
     int oom = 0;

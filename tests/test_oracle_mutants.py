@@ -44,6 +44,10 @@ MUTANTS = [
      "if (!(set[i - 1] && tt - s[i - 1] <= hi[i - 1] && tt != s[i - 1])) continue;"),
     ("mapconcat: window without the first edge",
      "for (int k = 0; k + 1 < N; k++) W += hi[k];", "for (int k = 1; k + 1 < N; k++) W += hi[k];"),
+    ("printed mapconcat: machines do not start back by the summed hi",
+     "            if (k > 0) back += hi[k - 1];\n", ""),
+    ("printed mapconcat: cross-over window closed",
+     "if (phase2 && tj >= tau[p + 1] + W) break;", "if (phase2 && tj > tau[p + 1] + W) break;"),
     ("mapconcat: class restarts at its own event",
      "int64_t from = c == ORC_NONE ? w : c + 1;", "int64_t from = c == ORC_NONE ? w : c;"),
 ]
