@@ -74,7 +74,7 @@ EXPORTS = ["fem_create", "fem_destroy", "fem_set_config", "fem_load_stream", "fe
            "fem_server_create", "fem_server_destroy", "fem_server_open_stream",
            "fem_server_append", "fem_server_submit", "fem_server_poll", "fem_server_result",
            "fem_server_release", "fem_server_drain", "fem_tune_enable", "fem_tune_size",
-           "fem_tune_save", "fem_tune_load"]
+           "fem_tune_save", "fem_tune_load", "fem_count_mapconcat_literal"]
 
 _lib = None
 
@@ -109,6 +109,8 @@ def load(path: str | None = None):
         "fem_result_free": (None, [vp]),
         "fem_last_mine_stats": (I, [vp, ctypes.POINTER(fem_level_stats), u32]),
         "fem_strerror": (ctypes.c_char_p, [I]),
+        "fem_count_mapconcat_literal": (I, [vp, i32, vp, u32, I, ctypes.POINTER(fem_interval),
+                                            u32, u32, vp, I, ctypes.POINTER(u32), vp]),
         "fem_tune_enable": (I, [vp, I]),
         "fem_tune_size": (I, [vp, ctypes.POINTER(u32)]),
         "fem_tune_save": (I, [vp, ctypes.c_char_p]),
@@ -217,6 +219,23 @@ def fem_set_config(ctx, segments=0, threads_per_block=0, ring_capacity=0, reset=
         return
     cfg = fem_config(int(segments), int(threads_per_block), int(ring_capacity))
     _check(lib.fem_set_config(ctx, ctypes.byref(cfg)), "fem_set_config")
+
+
+def fem_count_mapconcat_literal(ctx, sid, cands, intervals, segments, out=None, stream=None):
+    """MapConcatenate as Section 5.2.2 prints it (comparison with the exact counts);
+    returns (counts uint32[m] or `out`, (boundaries with no match, with several))."""
+    lib = load()
+    m = int(cands.shape[0])
+    pc, dc = _ptr(cands)
+    if out is None:
+        out = np.zeros(m, np.uint32)
+    po, do = _ptr(out)
+    iv, nI = _intervals(intervals)
+    diag = (ctypes.c_uint32 * 2)()
+    _check(lib.fem_count_mapconcat_literal(ctx, int(sid), pc, m, dc, iv, nI, int(segments), po, do,
+                                           diag, _stream_handle(stream)),
+           "fem_count_mapconcat_literal")
+    return out, (int(diag[0]), int(diag[1]))
 
 
 def fem_tune_enable(ctx, on=True):
