@@ -63,6 +63,8 @@ struct fem_ctx {
         float ms;
     };
     std::map<std::string, Shape> tune;
+    // MapConcatenate segment starts per (stream id, segment count), when not uniform
+    std::map<std::pair<int32_t, uint32_t>, uint32_t *> seg_starts;
     bool tune_on = false, tuning = false;
     cudaEvent_t tev[2] = {nullptr, nullptr};
 };
@@ -213,6 +215,67 @@ struct PassInfo {
     float ms_kernel = 0, ms_stitch = 0;
 };
 
+void drop_segment_starts(fem_ctx *c, int32_t id) {
+    for (auto it = c->seg_starts.begin(); it != c->seg_starts.end();) {
+        if (it->first.first == id) {
+            cudaFree(it->second);
+            it = c->seg_starts.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+// First chunk of each of P MapConcatenate segments (P + 1 entries): equal shares of
+// the chunks, except that a cut falling inside a burst -- the chunk before it lasts
+// less than half the median chunk -- moves, by at most an eighth of a segment, to
+// the chunk boundary after the longest-lasting chunk nearby.  The window before a
+// segment then holds few events, so its entry classes stay few.  Returns NULL when
+// no cut moves (the counters then use p * cps).
+int segment_starts(fem_ctx *c, const StreamDev &s, uint32_t P, uint32_t cps, cudaStream_t st,
+                   const uint32_t **out) {
+    *out = nullptr;
+    if (P < 2 || s.h_cfirst.size() != (size_t)s.n_chunks + 1 || !s.median_span) return FEM_OK;
+    const auto key = std::make_pair(s.id, P);
+    auto it = c->seg_starts.find(key);
+    if (it != c->seg_starts.end()) {
+        *out = it->second;
+        return FEM_OK;
+    }
+    std::vector<uint32_t> b(P + 1);
+    bool moved = false;
+    const uint32_t r = cps / 8;
+    auto span_before = [&](uint32_t q) { return s.h_cfirst[q] - s.h_cfirst[q - 1]; };
+    for (uint32_t p = 0; p <= P; ++p) {
+        uint32_t q = std::min(p * cps, s.n_chunks);
+        if (p > 0 && p < P && r > 0 && span_before(q) < s.median_span / 2) {
+            uint32_t best = q;
+            for (uint32_t d = 1; d <= r; ++d) {
+                if (q + d < s.n_chunks && span_before(q + d) > span_before(best)) best = q + d;
+                if (q > d && q - d > b[p - 1] && span_before(q - d) > span_before(best)) best = q - d;
+            }
+            moved |= best != q;
+            q = best;
+        }
+        b[p] = q;
+    }
+    b[P] = s.n_chunks;
+    if (!moved) {
+        c->seg_starts[key] = nullptr;
+        return FEM_OK;
+    }
+    uint32_t *d = nullptr;
+    if (cudaMalloc(&d, (P + 1) * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return FEM_ENOMEM;
+    }
+    CK(cudaMemcpyAsync(d, b.data(), (P + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    c->seg_starts[key] = d;
+    *out = d;
+    return FEM_OK;
+}
+
 uint32_t ceil_log2(uint64_t v) {
     uint32_t r = 0;
     while ((1ull << r) < v) ++r;
@@ -343,6 +406,7 @@ int count_launch(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const
     p.P = P;
     if (P > 1) {
         RET(dbuf(c, "tables", (size_t)P * m * S_MAX, &p.tables));
+        RET(segment_starts(c, s, P, cps, st, &p.seg_c0));
     }
     uint32_t T = choose_threads(c, N, pass, P > 1, R, s.offs, m);
     if (T_t && count_smem_bytes(N, pass, P > 1, R, T_t, s.offs) <= 100 * 1024) T = T_t;
@@ -411,6 +475,7 @@ int count_finish(fem_ctx *c, const StreamDev &s, const PassLaunch &pl, uint32_t 
         RET(dbuf(c, "redo2", r, &q.redo));
         CK(cudaMemsetAsync(q.redo, 0, r, st));
         const uint32_t Rq = pass == FEM_PASS_EXACT ? tr.R : 1;
+        q.seg_c0 = nullptr;
         if (tr.mc && s.n_chunks > 1) {
             q.P = s.n_chunks;
             q.cps = 1;
@@ -585,6 +650,7 @@ int fem_destroy(fem_ctx *c) {
         if (e) cudaEventDestroy(e);
     for (auto &e : c->tev)
         if (e) cudaEventDestroy(e);
+    for (auto &kv : c->seg_starts) cudaFree(kv.second);
     for (StreamDev &s : c->pool) free_stream_buffers(s);
     for (auto &b : c->pin)
         if (b.p) cudaFreeHost(b.p);
@@ -716,13 +782,28 @@ int fem_load_stream(fem_ctx *c, const uint8_t *types, const uint32_t *t_us, uint
                 break;
             }
         }
-        uint32_t e = 0;
-        if ((rc = read_err(c, st, &e)) != FEM_OK) break;
-        if ((rc = err_status(e)) != FEM_OK) break;
-        if (n) {
-            uint32_t tm;
-            if ((rc = read_words(c, s.t + (n - 1), 1, &tm, st)) != FEM_OK) break;
-            s.t_max = tm;
+        // error word, last time and the chunk start times in one round trip
+        void *h;
+        if ((rc = pinbuf(c, 0, (size_t)(nc + 3) * 4, st, &h)) != FEM_OK) break;
+        uint32_t *hw = static_cast<uint32_t *>(h);
+        if (cudaMemcpyAsync(hw, c->d_err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            (n && cudaMemcpyAsync(hw + 1, s.t + (n - 1), 4, cudaMemcpyDeviceToHost, st) !=
+                      cudaSuccess) ||
+            cudaMemcpyAsync(hw + 2, s.cfirst, (size_t)(nc + 1) * 4, cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = FEM_ECUDA;
+            break;
+        }
+        if ((rc = err_status(hw[0])) != FEM_OK) break;
+        if (n) s.t_max = hw[1];
+        s.h_cfirst.assign(hw + 2, hw + 2 + nc + 1);
+        std::vector<uint32_t> spans;
+        for (uint32_t q = 1; q < nc; ++q) spans.push_back(s.h_cfirst[q] - s.h_cfirst[q - 1]);
+        s.median_span = 0;
+        if (!spans.empty()) {
+            std::nth_element(spans.begin(), spans.begin() + spans.size() / 2, spans.end());
+            s.median_span = spans[spans.size() / 2];
         }
     } while (0);
     if (rc != FEM_OK) {
@@ -732,6 +813,7 @@ int fem_load_stream(fem_ctx *c, const uint8_t *types, const uint32_t *t_us, uint
         return rc;
     }
     const int32_t id = c->next_id++;
+    s.id = id;
     c->streams[id] = s;
     *id_out = id;
     return FEM_OK;
@@ -742,6 +824,7 @@ int fem_free_stream(fem_ctx *c, int32_t id) {
     auto it = c->streams.find(id);
     if (it == c->streams.end()) return FEM_ENOSTREAM;
     cudaSetDevice(c->device);
+    drop_segment_starts(c, id);
     // Keep the buffers for the next load (work already queued that reads them runs
     // first: every stream of this context is synchronised before reuse).
     cudaDeviceSynchronize();
@@ -788,6 +871,90 @@ int fem_count_candidates(fem_ctx *c, int32_t id, const fem_episode *cands, uint3
     uint32_t *dout = counts_out;
     if (!counts_on_device) RET(dbuf(c, "counts_out", m, &dout));
     RET(count_any(c, *s, dc, nullptr, m, d_ivl, nI, pass, dout, st));
+    if (!counts_on_device) {
+        CK(cudaMemcpyAsync(counts_out, dout, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return FEM_OK;
+}
+
+int fem_count_mapconcat_literal(fem_ctx *c, int32_t id, const fem_episode *cands, uint32_t m,
+                                int cands_on_device, const fem_interval *I, uint32_t nI,
+                                uint32_t segments, uint32_t *counts_out, int counts_on_device,
+                                uint32_t *diag_out, void *cuda_stream) {
+    if (!c || (m && (!cands || !counts_out))) return FEM_EINVAL;
+    const StreamDev *s = find_stream(c, id);
+    if (!s) return FEM_ENOSTREAM;
+    RET(check_intervals(*s, I, nI));
+    if (diag_out) diag_out[0] = diag_out[1] = 0;
+    if (m == 0) return FEM_OK;
+    cudaSetDevice(c->device);
+    cudaStream_t st = pick(c, cuda_stream);
+    CK(cudaMemsetAsync(c->d_err, 0, 4, st));
+    uint2 *d_ivl;
+    RET(upload_intervals(c, I, nI, st, &d_ivl));
+    const fem_episode *dc = cands;
+    if (!cands_on_device) {
+        fem_episode *tmp;
+        RET(dbuf(c, "cands_in", m, &tmp));
+        CK(cudaMemcpyAsync(tmp, cands, (size_t)m * sizeof(fem_episode), cudaMemcpyHostToDevice, st));
+        dc = tmp;
+    }
+    uint32_t *dout = counts_out;
+    if (!counts_on_device) RET(dbuf(c, "counts_out", m, &dout));
+    // the printed scheme needs distinct types (as the exact MapConcatenate does)
+    CK(cudaMemsetAsync(c->d_small + W_INFO, 0, 2 * sizeof(uint32_t), st));
+    CK(launch_validate_cands(dc, nullptr, m, s->K, nI, c->d_small + W_INFO, c->d_err, st));
+    uint32_t info[2], e;
+    RET(read_words(c, c->d_small + W_INFO, 2, info, st));
+    RET(read_err(c, st, &e));
+    RET(err_status(e));
+    if (info[1]) return FEM_EINVAL;
+    if (s->n == 0) {
+        CK(cudaMemsetAsync(dout, 0, (size_t)m * 4, st));
+    } else {
+        // time cuts at the first event of every cps-th chunk (dropped where equal
+        // times would make them non-increasing)
+        std::vector<uint32_t> cf(s->n_chunks + 1);
+        CK(cudaMemcpyAsync(cf.data(), s->cfirst, cf.size() * 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const uint32_t P0 = std::max<uint32_t>(1, std::min<uint32_t>(segments ? segments : 1,
+                                                                     s->n_chunks));
+        const uint32_t cps = (s->n_chunks + P0 - 1) / P0;
+        std::vector<int64_t> tau{(int64_t)cf[0] - 1};
+        for (uint32_t c0 = cps; c0 < s->n_chunks; c0 += cps)
+            if ((int64_t)cf[c0] - 1 > tau.back() && (int64_t)cf[c0] - 1 < (int64_t)s->t_max)
+                tau.push_back((int64_t)cf[c0] - 1);
+        tau.push_back((int64_t)s->t_max);
+        const uint32_t P = (uint32_t)tau.size() - 1;
+        int64_t *d_tau;
+        uint4 *tuples;
+        RET(dbuf(c, "lit_tau", tau.size(), &d_tau));
+        RET(dbuf(c, "lit_tuples", (size_t)m * P * FEM_MAX_LEN, &tuples));
+        CK(cudaMemcpyAsync(d_tau, tau.data(), tau.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                           st));
+        CK(cudaMemsetAsync(c->d_small + W_INFO, 0, 2 * sizeof(uint32_t), st));
+        LiteralParams p{};
+        p.bev = s->bev;
+        p.boff = s->boff;
+        p.t = s->t;
+        p.offs = s->offs;
+        p.n = s->n;
+        p.cands = dc;
+        p.m = m;
+        p.ivl = d_ivl;
+        p.tau = d_tau;
+        p.P = P;
+        p.tuples = tuples;
+        p.err = c->d_err;
+        CK(launch_literal(p, info[0], dout, c->d_small + W_INFO, st));
+        uint32_t dg[2];
+        RET(read_words(c, c->d_small + W_INFO, 2, dg, st));
+        RET(read_err(c, st, &e));
+        if (e & ERR_RING) return FEM_EOVERFLOW;
+        RET(err_status(e));
+        if (diag_out) diag_out[0] = dg[0], diag_out[1] = dg[1];
+    }
     if (!counts_on_device) {
         CK(cudaMemcpyAsync(counts_out, dout, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/fem.h"
 
 namespace fem {
@@ -54,6 +56,10 @@ struct StreamDev {
     uint16_t *boff = nullptr;
     uint32_t *cfirst = nullptr;
     uint32_t *hist = nullptr;
+    // host side: the stream's id, a copy of cfirst and the median chunk duration (us)
+    int32_t id = 0;
+    std::vector<uint32_t> h_cfirst;
+    uint32_t median_span = 0;
 };
 
 // Arguments of the counting kernels (one pass over one candidate set).
@@ -73,6 +79,8 @@ struct CountParams {
     uint32_t *out;              // counts [m] (single segment)
     uint32_t cps;               // chunks per segment
     uint32_t P;                 // segments
+    const uint32_t *seg_c0;     // optional: first chunk of segment p (P + 1 entries);
+                                // NULL: p * cps
     uint4 *tables;              // [P][m][S_MAX] (key, count, exit, 0) when P > 1
     uint8_t *redo;              // [m] set to 1 when a candidate must be recounted
     uint32_t *err;
@@ -82,6 +90,22 @@ struct CountParams {
     uint64_t ev_begin, ev_end;
     uint32_t *state;            // per-candidate carried state (count, machine), in and out
     uint32_t state_stride;      // words per candidate: 1 + (N-1) relaxed, 1 + (N-1)(1 + 2R) exact
+};
+
+// MapConcatenate as printed (fem_literal.cu): time segments (tau[p], tau[p+1]]
+struct LiteralParams {
+    const uint2 *bev;
+    const uint16_t *boff;
+    const uint32_t *t;
+    uint32_t offs;
+    uint64_t n;
+    const fem_episode *cands;   // m records, distinct types
+    uint32_t m;
+    const uint2 *ivl;
+    const int64_t *tau;         // P + 1 increasing times, tau[0] < t[0], tau[P] >= t[n-1]
+    uint32_t P;
+    uint4 *tuples;              // [m][P][FEM_MAX_LEN]
+    uint32_t *err;
 };
 
 // Per-job output arrays of a batch (device pointers owned by the caller).
@@ -175,6 +199,11 @@ cudaError_t launch_count_batch(int N, int pass, uint32_t ring_cap, uint32_t thre
                                const uint32_t *n_items, uint32_t *queue, uint32_t SB,
                                int sm_count, cudaStream_t st);
 cudaError_t count_set_smem_limits();
+// fem_literal.cu: map (one thread per episode, segment and machine) and join;
+// len_mask has bit N set for every episode length N present; diag[2] accumulates the
+// boundaries where no tuple / several tuples matched
+cudaError_t launch_literal(const LiteralParams &p, uint32_t len_mask, uint32_t *out, uint32_t *diag,
+                           cudaStream_t st);
 // fem_mine.cu
 // stitch of a batch: job_base[j] = first global episode slot of job j (n_jobs + 1
 // entries); slots >= a job's current m are skipped
