@@ -63,8 +63,6 @@ struct fem_ctx {
         float ms;
     };
     std::map<std::string, Shape> tune;
-    // MapConcatenate segment starts per (stream id, segment count), when not uniform
-    std::map<std::pair<int32_t, uint32_t>, uint32_t *> seg_starts;
     bool tune_on = false, tuning = false;
     cudaEvent_t tev[2] = {nullptr, nullptr};
 };
@@ -215,67 +213,6 @@ struct PassInfo {
     float ms_kernel = 0, ms_stitch = 0;
 };
 
-void drop_segment_starts(fem_ctx *c, int32_t id) {
-    for (auto it = c->seg_starts.begin(); it != c->seg_starts.end();) {
-        if (it->first.first == id) {
-            cudaFree(it->second);
-            it = c->seg_starts.erase(it);
-        } else {
-            ++it;
-        }
-    }
-}
-
-// First chunk of each of P MapConcatenate segments (P + 1 entries): equal shares of
-// the chunks, except that a cut falling inside a burst -- the chunk before it lasts
-// less than half the median chunk -- moves, by at most an eighth of a segment, to
-// the chunk boundary after the longest-lasting chunk nearby.  The window before a
-// segment then holds few events, so its entry classes stay few.  Returns NULL when
-// no cut moves (the counters then use p * cps).
-int segment_starts(fem_ctx *c, const StreamDev &s, uint32_t P, uint32_t cps, cudaStream_t st,
-                   const uint32_t **out) {
-    *out = nullptr;
-    if (P < 2 || s.h_cfirst.size() != (size_t)s.n_chunks + 1 || !s.median_span) return FEM_OK;
-    const auto key = std::make_pair(s.id, P);
-    auto it = c->seg_starts.find(key);
-    if (it != c->seg_starts.end()) {
-        *out = it->second;
-        return FEM_OK;
-    }
-    std::vector<uint32_t> b(P + 1);
-    bool moved = false;
-    const uint32_t r = cps / 8;
-    auto span_before = [&](uint32_t q) { return s.h_cfirst[q] - s.h_cfirst[q - 1]; };
-    for (uint32_t p = 0; p <= P; ++p) {
-        uint32_t q = std::min(p * cps, s.n_chunks);
-        if (p > 0 && p < P && r > 0 && span_before(q) < s.median_span / 2) {
-            uint32_t best = q;
-            for (uint32_t d = 1; d <= r; ++d) {
-                if (q + d < s.n_chunks && span_before(q + d) > span_before(best)) best = q + d;
-                if (q > d && q - d > b[p - 1] && span_before(q - d) > span_before(best)) best = q - d;
-            }
-            moved |= best != q;
-            q = best;
-        }
-        b[p] = q;
-    }
-    b[P] = s.n_chunks;
-    if (!moved) {
-        c->seg_starts[key] = nullptr;
-        return FEM_OK;
-    }
-    uint32_t *d = nullptr;
-    if (cudaMalloc(&d, (P + 1) * sizeof(uint32_t)) != cudaSuccess) {
-        cudaGetLastError();
-        return FEM_ENOMEM;
-    }
-    CK(cudaMemcpyAsync(d, b.data(), (P + 1) * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));
-    c->seg_starts[key] = d;
-    *out = d;
-    return FEM_OK;
-}
-
 uint32_t ceil_log2(uint64_t v) {
     uint32_t r = 0;
     while ((1ull << r) < v) ++r;
@@ -406,7 +343,6 @@ int count_launch(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const
     p.P = P;
     if (P > 1) {
         RET(dbuf(c, "tables", (size_t)P * m * S_MAX, &p.tables));
-        RET(segment_starts(c, s, P, cps, st, &p.seg_c0));
     }
     uint32_t T = choose_threads(c, N, pass, P > 1, R, s.offs, m);
     if (T_t && count_smem_bytes(N, pass, P > 1, R, T_t, s.offs) <= 100 * 1024) T = T_t;
@@ -475,7 +411,6 @@ int count_finish(fem_ctx *c, const StreamDev &s, const PassLaunch &pl, uint32_t 
         RET(dbuf(c, "redo2", r, &q.redo));
         CK(cudaMemsetAsync(q.redo, 0, r, st));
         const uint32_t Rq = pass == FEM_PASS_EXACT ? tr.R : 1;
-        q.seg_c0 = nullptr;
         if (tr.mc && s.n_chunks > 1) {
             q.P = s.n_chunks;
             q.cps = 1;
@@ -650,7 +585,6 @@ int fem_destroy(fem_ctx *c) {
         if (e) cudaEventDestroy(e);
     for (auto &e : c->tev)
         if (e) cudaEventDestroy(e);
-    for (auto &kv : c->seg_starts) cudaFree(kv.second);
     for (StreamDev &s : c->pool) free_stream_buffers(s);
     for (auto &b : c->pin)
         if (b.p) cudaFreeHost(b.p);
@@ -782,29 +716,17 @@ int fem_load_stream(fem_ctx *c, const uint8_t *types, const uint32_t *t_us, uint
                 break;
             }
         }
-        // error word, last time and the chunk start times in one round trip
-        void *h;
-        if ((rc = pinbuf(c, 0, (size_t)(nc + 3) * 4, st, &h)) != FEM_OK) break;
-        uint32_t *hw = static_cast<uint32_t *>(h);
+        // error word and last time in one round trip
+        uint32_t *hw = c->h_small;
         if (cudaMemcpyAsync(hw, c->d_err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             (n && cudaMemcpyAsync(hw + 1, s.t + (n - 1), 4, cudaMemcpyDeviceToHost, st) !=
                       cudaSuccess) ||
-            cudaMemcpyAsync(hw + 2, s.cfirst, (size_t)(nc + 1) * 4, cudaMemcpyDeviceToHost, st) !=
-                cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             rc = FEM_ECUDA;
             break;
         }
         if ((rc = err_status(hw[0])) != FEM_OK) break;
         if (n) s.t_max = hw[1];
-        s.h_cfirst.assign(hw + 2, hw + 2 + nc + 1);
-        std::vector<uint32_t> spans;
-        for (uint32_t q = 1; q < nc; ++q) spans.push_back(s.h_cfirst[q] - s.h_cfirst[q - 1]);
-        s.median_span = 0;
-        if (!spans.empty()) {
-            std::nth_element(spans.begin(), spans.begin() + spans.size() / 2, spans.end());
-            s.median_span = spans[spans.size() / 2];
-        }
     } while (0);
     if (rc != FEM_OK) {
         cudaGetLastError();
@@ -813,7 +735,6 @@ int fem_load_stream(fem_ctx *c, const uint8_t *types, const uint32_t *t_us, uint
         return rc;
     }
     const int32_t id = c->next_id++;
-    s.id = id;
     c->streams[id] = s;
     *id_out = id;
     return FEM_OK;
@@ -824,7 +745,6 @@ int fem_free_stream(fem_ctx *c, int32_t id) {
     auto it = c->streams.find(id);
     if (it == c->streams.end()) return FEM_ENOSTREAM;
     cudaSetDevice(c->device);
-    drop_segment_starts(c, id);
     // Keep the buffers for the next load (work already queued that reads them runs
     // first: every stream of this context is synchronised before reuse).
     cudaDeviceSynchronize();

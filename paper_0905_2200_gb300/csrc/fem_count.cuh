@@ -121,12 +121,9 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
 
     // ---------------------------------------------------------------- segment and window
     // A ranged count (single segment) covers events [ev_begin, ev_end) only.
-    const uint32_t c_seg0 = p.ranged   ? (uint32_t)(p.ev_begin / CHUNK)
-                            : p.seg_c0 ? p.seg_c0[seg]
-                                       : seg * p.cps;
+    const uint32_t c_seg0 = p.ranged ? (uint32_t)(p.ev_begin / CHUNK) : seg * p.cps;
     const uint32_t c_end = p.ranged ? (uint32_t)((p.ev_end + CHUNK - 1) / CHUNK)
-                           : p.seg_c0 ? p.seg_c0[seg + 1]
-                                      : min(c_seg0 + p.cps, p.n_chunks);
+                                    : min(c_seg0 + p.cps, p.n_chunks);
     const uint32_t lo_local = p.ranged ? (uint32_t)(p.ev_begin - (uint64_t)c_seg0 * CHUNK) : 0u;
     const uint32_t hi_local = p.ranged && c_end > 0
                                   ? (uint32_t)(p.ev_end - (uint64_t)(c_end - 1) * CHUNK)

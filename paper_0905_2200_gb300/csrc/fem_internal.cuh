@@ -16,8 +16,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <vector>
-
 #include "../../include/fem.h"
 
 namespace fem {
@@ -56,10 +54,6 @@ struct StreamDev {
     uint16_t *boff = nullptr;
     uint32_t *cfirst = nullptr;
     uint32_t *hist = nullptr;
-    // host side: the stream's id, a copy of cfirst and the median chunk duration (us)
-    int32_t id = 0;
-    std::vector<uint32_t> h_cfirst;
-    uint32_t median_span = 0;
 };
 
 // Arguments of the counting kernels (one pass over one candidate set).
@@ -79,8 +73,6 @@ struct CountParams {
     uint32_t *out;              // counts [m] (single segment)
     uint32_t cps;               // chunks per segment
     uint32_t P;                 // segments
-    const uint32_t *seg_c0;     // optional: first chunk of segment p (P + 1 entries);
-                                // NULL: p * cps
     uint4 *tables;              // [P][m][S_MAX] (key, count, exit, 0) when P > 1
     uint8_t *redo;              // [m] set to 1 when a candidate must be recounted
     uint32_t *err;
