@@ -54,10 +54,15 @@ NCU_TRAFFIC = {
 
 
 def kernel_source_hash() -> str:
+    """SHA-256 (16 hex digits) of what the counting kernels are compiled from: their two
+    files and the device part of the internal header (up to its host launcher list)."""
     h = hashlib.sha256()
-    for f in ("fem_count.cuh", "fem_count.cu", "fem_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_0905_2200_gb300", "csrc", f), "rb") as fh:
+    csrc = os.path.join(ROOT, "paper_0905_2200_gb300", "csrc")
+    for f in ("fem_count.cuh", "fem_count.cu"):
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(csrc, "fem_internal.cuh"), "rb") as fh:
+        h.update(fh.read().split(b"// ---------------------------------------------------------------- launchers (host side)")[0])
     return h.hexdigest()[:16]
 
 

@@ -248,14 +248,16 @@ def _pack(cands):
     return lens, E, iv
 
 
-def join(frequent):
+def join(frequent, repeated_types=False):
     """Next-level candidates from the frequent N-node episodes.
 
     alpha and beta join when alpha without its first node equals beta without
     its last node (types and intervals); the candidate is alpha followed by
     beta's last edge and node, kept only if that node's type is new to alpha
-    (episodes are tuples of distinct types, Def. 2.2).  Returned in canonical
-    order.
+    (episodes are tuples of distinct types, Def. 2.2) unless ``repeated_types``
+    (then every such candidate is kept: dropping the first or last node of an
+    episode with repeated types cannot lower its count either).  Returned in
+    canonical order.
     """
     by_prefix = {}
     for ty, ix in frequent:
@@ -263,14 +265,15 @@ def join(frequent):
     out = []
     for ty, ix in frequent:
         for bty, bix in by_prefix.get((ty[1:], ix[1:]), []):
-            if bty[-1] in ty:
+            if bty[-1] in ty and not repeated_types:
                 continue
             out.append((ty + (bty[-1],), ix + (bix[-1],)))
     out.sort(key=lambda c: canonical_key(*c))
     return out
 
 
-def mine(types, t, n_types, intervals, theta, max_len, two_pass_counting=True):
+def mine(types, t, n_types, intervals, theta, max_len, two_pass_counting=True,
+         repeated_types=False):
     """Problem 1 (Section 2), level by level.
 
     Level 1: the count of a one-node episode is the number of events of its
@@ -278,7 +281,8 @@ def mine(types, t, n_types, intervals, theta, max_len, two_pass_counting=True):
     interval.  Level N+1: :func:`join` of level N's frequent set.  Each level is
     counted with Algorithm 4 (relaxed pass, drop below theta, exact pass) or,
     if ``two_pass_counting`` is False, with the exact pass alone.  An episode is
-    frequent iff its exact count is >= theta.
+    frequent iff its exact count is >= theta.  With ``repeated_types`` a type may
+    appear at several nodes (level 2 includes (a, a); the join keeps repeats).
 
     Returns {level: [(types tuple, interval-index tuple, count), ...]} with
     each level in canonical order; level 1 lists (type,), (), count.
@@ -288,7 +292,8 @@ def mine(types, t, n_types, intervals, theta, max_len, two_pass_counting=True):
     hist = np.bincount(types, minlength=n_types)
     res = {1: [((a,), (), int(hist[a])) for a in range(n_types) if hist[a] >= theta]}
     f1 = [a for a in range(n_types) if hist[a] >= theta]
-    cands = [((a, b), (iv,)) for a in f1 for iv in range(len(intervals)) for b in f1 if a != b]
+    cands = [((a, b), (iv,)) for a in f1 for iv in range(len(intervals)) for b in f1
+             if a != b or repeated_types]
     level = 2
     while cands and level <= max_len:
         lens, E, iv = _pack(cands)
@@ -304,6 +309,6 @@ def mine(types, t, n_types, intervals, theta, max_len, two_pass_counting=True):
         res[level] = freq
         if level == max_len:
             break
-        cands = join([(ty, ix) for ty, ix, _ in freq])
+        cands = join([(ty, ix) for ty, ix, _ in freq], repeated_types)
         level += 1
     return res

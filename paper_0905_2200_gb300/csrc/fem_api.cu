@@ -462,8 +462,30 @@ int count_any(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const ui
     RET(read_words(c, c->d_small + W_INFO, 2, info, st));
     RET(read_err(c, st, &e));
     RET(err_status(e));
-    const bool distinct = info[1] == 0;
     const uint32_t lens = info[0];
+    if (info[1] && info[1] < m) {
+        // distinct-type and repeated-type episodes mixed: count each part on its own
+        // (repeated types run with one segment), then put the counts back in place
+        uint8_t *rf;
+        uint32_t *ridx, *rg, *rout, *scratch;
+        RET(dbuf(c, "rep_flags", m, &rf));
+        RET(dbuf(c, "rep_idx", m, &ridx));
+        RET(dbuf(c, "rep_gather", m, &rg));
+        RET(dbuf(c, "rep_out", m, &rout));
+        RET(dbuf(c, "rep_scratch", compact_scratch_words(m), &scratch));
+        for (bool rep : {false, true}) {
+            CK(launch_repeat_flags(cands, gather, m, !rep, rf, st));
+            CK(launch_compact(nullptr, rf, 0, m, ridx, c->d_small + W_COUNT2, scratch, st));
+            uint32_t k;
+            RET(read_words(c, c->d_small + W_COUNT2, 1, &k, st));
+            if (!k) continue;
+            CK(launch_compose_idx(gather, ridx, k, rg, st));
+            RET(count_any(c, s, cands, rg, k, d_ivl, nI, pass, rout, st));
+            CK(launch_scatter_u32(rout, ridx, k, out, st));
+        }
+        return FEM_OK;
+    }
+    const bool distinct = info[1] == 0;
     if (__builtin_popcount(lens) == 1) {
         const int N = __builtin_ctz(lens);
         return count_pass(c, s, cands, gather, m, N, d_ivl, nI, pass, out, distinct, st, nullptr);
@@ -934,7 +956,15 @@ int fem_count_two_pass(fem_ctx *c, int32_t id, const fem_episode *cands, uint32_
 
 int fem_mine_levelwise(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t nI,
                        uint32_t theta, uint32_t max_len, void *cuda_stream, fem_result **out) {
+    return fem_mine_levelwise_ex(c, id, I, nI, theta, max_len, 0u, cuda_stream, out);
+}
+
+int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t nI,
+                          uint32_t theta, uint32_t max_len, uint32_t flags, void *cuda_stream,
+                          fem_result **out) {
     if (!c || !out || max_len < 1 || max_len > FEM_MAX_LEN) return FEM_EINVAL;
+    if (flags & ~FEM_MINE_REPEATED_TYPES) return FEM_EINVAL;
+    const bool repeats = (flags & FEM_MINE_REPEATED_TYPES) != 0;
     *out = nullptr;
     const StreamDev *sp = find_stream(c, id);
     if (!sp) return FEM_ENOSTREAM;
@@ -989,12 +1019,12 @@ int fem_mine_levelwise(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t n
         res->eps[0].push_back(e);
         res->counts[0].push_back(hist[ft[i]]);
     }
-    if (max_len < 2 || f1 < 2 || nI == 0) {
+    if (max_len < 2 || f1 < (repeats ? 1u : 2u) || nI == 0) {
         *out = res;
         return FEM_OK;
     }
     // level 2: ordered pairs of distinct frequent types x intervals
-    uint64_t m64 = (uint64_t)f1 * nI * (f1 - 1);
+    uint64_t m64 = (uint64_t)f1 * nI * (repeats ? f1 : f1 - 1);
     if (m64 > 0xFFFFFFF0ull) return fail(FEM_ENOMEM);
     uint32_t m = (uint32_t)m64;
     const char *cname[2] = {"candsA", "candsB"};
@@ -1002,7 +1032,7 @@ int fem_mine_levelwise(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t n
     fem_episode *cands;
     RETF(dbuf(c, cname[cur], m, &cands));
     cudaEventRecord(c->ev[0], st);
-    CKF(launch_level2(ftypes, f1, nI, cands, st));
+    CKF(launch_level2(ftypes, f1, nI, repeats, cands, st));
     cudaEventRecord(c->ev[1], st);
     // Per level the host waits three times: for the survivor count, the frequent
     // count and the next level's candidate count (each read together with the error
@@ -1036,8 +1066,11 @@ int fem_mine_levelwise(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t n
         // first pass (Algorithm 3) on every candidate, then eliminate relaxed < theta
         PassLaunch plr;
         cudaEventRecord(c->ev[2], st);
-        RETF(count_launch(c, s, cands, nullptr, m, (int)N, d_ivl, nI, FEM_PASS_RELAXED, rel, true,
-                          st, &plr));
+        if (repeats)  // repeated types among the candidates: split and count (count_any)
+            RETF(count_any(c, s, cands, nullptr, m, d_ivl, nI, FEM_PASS_RELAXED, rel, st));
+        else
+            RETF(count_launch(c, s, cands, nullptr, m, (int)N, d_ivl, nI, FEM_PASS_RELAXED, rel,
+                              true, st, &plr));
         cudaEventRecord(c->ev[3], st);
         CKF(launch_touched(cands, nullptr, m, s.hist, touched + 2 * N, st));
         cudaEventRecord(c->ev[4], st);
@@ -1056,8 +1089,11 @@ int fem_mine_levelwise(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t n
         RETF(dbuf(c, "idx_f", ms, &idx_f));
         PassLaunch plx;
         cudaEventRecord(c->ev[6], st);
-        RETF(count_launch(c, s, cands, idx_s, ms, (int)N, d_ivl, nI, FEM_PASS_EXACT, ex, true, st,
-                          &plx));
+        if (repeats)
+            RETF(count_any(c, s, cands, idx_s, ms, d_ivl, nI, FEM_PASS_EXACT, ex, st));
+        else
+            RETF(count_launch(c, s, cands, idx_s, ms, (int)N, d_ivl, nI, FEM_PASS_EXACT, ex, true,
+                              st, &plx));
         cudaEventRecord(c->ev[7], st);
         CKF(launch_touched(cands, idx_s, ms, s.hist, touched + 2 * N + 1, st));
         uint32_t f = 0;
@@ -1089,13 +1125,13 @@ int fem_mine_levelwise(fem_ctx *c, int32_t id, const fem_interval *I, uint32_t n
         RETF(dbuf(c, "jc", f, &jc));
         RETF(dbuf(c, "joff", f, &joff));
         cudaEventRecord(c->ev[0], st);
-        CKF(launch_join_count(F, f, N, jc, st));
+        CKF(launch_join_count(F, f, N, repeats, jc, st));
         CKF(launch_exclusive_scan(jc, f, joff, c->d_small + W_COUNT2, scratch, st));
         uint32_t mn;
         RETF(read_words(c, c->d_small + W_COUNT2, 1, &mn, st));
         cur ^= 1;
         RETF(dbuf(c, cname[cur], std::max<uint32_t>(mn, 1), &cands));
-        CKF(launch_join_emit(F, f, N, joff, cands, st));
+        CKF(launch_join_emit(F, f, N, repeats, joff, cands, st));
         cudaEventRecord(c->ev[1], st);
         m = mn;
     }

@@ -225,14 +225,16 @@ cudaError_t launch_gather_episodes(const fem_episode *src, const uint32_t *idx, 
 cudaError_t launch_scatter_u32(const uint32_t *src, const uint32_t *idx, uint32_t m,
                                uint32_t *dst, cudaStream_t st);
 cudaError_t launch_fill_flags(const uint32_t *idx, uint32_t m, uint8_t *flags, cudaStream_t st);
-cudaError_t launch_level2(const uint32_t *ftypes, uint32_t f, uint32_t n_ivl, fem_episode *out,
-                          cudaStream_t st);
-cudaError_t launch_join_count(const fem_episode *F, uint32_t f, uint32_t N, uint32_t *cnt,
-                              cudaStream_t st);
+cudaError_t launch_level2(const uint32_t *ftypes, uint32_t f, uint32_t n_ivl, bool repeats,
+                          fem_episode *out, cudaStream_t st);
+cudaError_t launch_join_count(const fem_episode *F, uint32_t f, uint32_t N, bool repeats,
+                              uint32_t *cnt, cudaStream_t st);
 cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t m, uint32_t *out,
                                   uint32_t *total, uint32_t *scratch, cudaStream_t st);
-cudaError_t launch_join_emit(const fem_episode *F, uint32_t f, uint32_t N, const uint32_t *off,
-                             fem_episode *out, cudaStream_t st);
+cudaError_t launch_join_emit(const fem_episode *F, uint32_t f, uint32_t N, bool repeats,
+                             const uint32_t *off, fem_episode *out, cudaStream_t st);
+cudaError_t launch_repeat_flags(const fem_episode *c, const uint32_t *gather, uint32_t m, bool invert,
+                                uint8_t *flags, cudaStream_t st);
 // fem_batch.cu
 cudaError_t launch_batch_items(const CountParams *jobs, uint32_t n_jobs, uint32_t T,
                                uint32_t *item_off, uint32_t *n_items, uint32_t cap, uint4 *items,

@@ -251,6 +251,26 @@ __global__ void k_len_flags(const fem_episode *__restrict__ c, const uint32_t *g
     if (i < m) flags[i] = ld_ep(c, gather ? gather[i] : i).len == N;
 }
 
+// flags[i] = 1 if candidate i (gathered) has a repeated type, xor `invert`
+__global__ void k_repeat_flags(const fem_episode *__restrict__ c, const uint32_t *__restrict__ gather,
+                               uint32_t m, uint32_t invert, uint8_t *__restrict__ flags) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const fem_episode e = c[gather ? gather[i] : i];
+    uint32_t rep = 0;
+    for (uint32_t a = 0; a < e.len && a < FEM_MAX_LEN; ++a)
+        for (uint32_t b = a + 1; b < e.len && b < FEM_MAX_LEN; ++b) rep |= e.types[a] == e.types[b];
+    flags[i] = (uint8_t)(rep ^ invert);
+}
+
+cudaError_t launch_repeat_flags(const fem_episode *c, const uint32_t *gather, uint32_t m, bool invert,
+                                uint8_t *flags, cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    k_repeat_flags<<<(m + 255) / 256, 256, 0, st>>>(c, gather, m, invert ? 1u : 0u, flags);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_len_flags(const fem_episode *c, const uint32_t *gather, uint32_t m, uint32_t N,
                              uint8_t *flags, cudaStream_t st) {
     if (m == 0) return cudaSuccess;
@@ -492,17 +512,20 @@ cudaError_t launch_type_filter(const uint32_t *hist, uint32_t K, uint32_t theta,
 
 // Level 2: every ordered pair (a, b) of distinct frequent types, once per interval,
 // in canonical order (a, interval, b).
+// Level 2: ordered pairs (a, b) of frequent types, a != b unless `repeats`, once per
+// interval, in canonical order (a, interval, b).
 __global__ void k_level2(const uint32_t *__restrict__ ftypes, uint32_t f, uint32_t n_ivl,
-                         fem_episode *__restrict__ out) {
-    const uint64_t m = (uint64_t)f * n_ivl * (f - 1);
+                         uint32_t repeats, fem_episode *__restrict__ out) {
+    const uint32_t nb = repeats ? f : f - 1;  // second types per first type
+    const uint64_t m = (uint64_t)f * n_ivl * nb;
     const uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (c >= m) return;
-    const uint64_t per_a = (uint64_t)n_ivl * (f - 1);
+    const uint64_t per_a = (uint64_t)n_ivl * nb;
     const uint32_t ai = (uint32_t)(c / per_a);
     const uint32_t r = (uint32_t)(c % per_a);
-    const uint32_t iv = r / (f - 1);
-    const uint32_t bj = r % (f - 1);
-    const uint32_t bi = bj < ai ? bj : bj + 1;
+    const uint32_t iv = r / nb;
+    const uint32_t bj = r % nb;
+    const uint32_t bi = (repeats || bj < ai) ? bj : bj + 1;
     fem_episode e;
     memset(&e, 0, sizeof(e));
     e.types[0] = (uint8_t)ftypes[ai];
@@ -512,11 +535,12 @@ __global__ void k_level2(const uint32_t *__restrict__ ftypes, uint32_t f, uint32
     st_ep(out, c, e);
 }
 
-cudaError_t launch_level2(const uint32_t *ftypes, uint32_t f, uint32_t n_ivl, fem_episode *out,
-                          cudaStream_t st) {
-    if (f < 2 || n_ivl == 0) return cudaSuccess;
-    const uint64_t m = (uint64_t)f * n_ivl * (f - 1);
-    k_level2<<<(uint32_t)((m + 255) / 256), 256, 0, st>>>(ftypes, f, n_ivl, out);
+cudaError_t launch_level2(const uint32_t *ftypes, uint32_t f, uint32_t n_ivl, bool repeats,
+                          fem_episode *out, cudaStream_t st) {
+    if (f < (repeats ? 1u : 2u) || n_ivl == 0) return cudaSuccess;
+    const uint64_t m = (uint64_t)f * n_ivl * (repeats ? f : f - 1);
+    k_level2<<<(uint32_t)((m + 255) / 256), 256, 0, st>>>(ftypes, f, n_ivl, repeats ? 1u : 0u,
+                                                          out);
     note_launch();
     return cudaGetLastError();
 }
@@ -565,20 +589,23 @@ __device__ __forceinline__ bool has_type(const fem_episode &a, uint32_t N, uint3
 // beta minus its last node; the child appends beta's last edge and node, whose
 // type must be new to alpha.  F is in canonical order, so the betas of one
 // alpha are contiguous and the children come out in canonical order.
+// The child alpha + beta's last node is kept if that type is new to alpha, or
+// always when `repeats`.
 __global__ void k_join_count(const fem_episode *__restrict__ F, uint32_t f, uint32_t N,
-                             uint32_t *__restrict__ cnt) {
+                             uint32_t repeats, uint32_t *__restrict__ cnt) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= f) return;
     const fem_episode a = ld_ep(F, i);
     uint32_t lo, hi;
     join_range(F, f, N, a, &lo, &hi);
     uint32_t c = 0;
-    for (uint32_t j = lo; j < hi; ++j) c += !has_type(a, N, ld_ep(F, j).types[N - 1]);
+    for (uint32_t j = lo; j < hi; ++j) c += repeats || !has_type(a, N, ld_ep(F, j).types[N - 1]);
     cnt[i] = c;
 }
 
 __global__ void k_join_emit(const fem_episode *__restrict__ F, uint32_t f, uint32_t N,
-                            const uint32_t *__restrict__ off, fem_episode *__restrict__ out) {
+                            uint32_t repeats, const uint32_t *__restrict__ off,
+                            fem_episode *__restrict__ out) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= f) return;
     const fem_episode a = ld_ep(F, i);
@@ -588,7 +615,7 @@ __global__ void k_join_emit(const fem_episode *__restrict__ F, uint32_t f, uint3
     for (uint32_t j = lo; j < hi; ++j) {
         const fem_episode b = ld_ep(F, j);
         const uint32_t x = b.types[N - 1];
-        if (has_type(a, N, x)) continue;
+        if (!repeats && has_type(a, N, x)) continue;
         fem_episode c = a;
         c.types[N] = (uint8_t)x;
         c.ivl[N - 1] = b.ivl[N - 2];
@@ -597,18 +624,18 @@ __global__ void k_join_emit(const fem_episode *__restrict__ F, uint32_t f, uint3
     }
 }
 
-cudaError_t launch_join_count(const fem_episode *F, uint32_t f, uint32_t N, uint32_t *cnt,
-                              cudaStream_t st) {
+cudaError_t launch_join_count(const fem_episode *F, uint32_t f, uint32_t N, bool repeats,
+                              uint32_t *cnt, cudaStream_t st) {
     if (f == 0) return cudaSuccess;
-    k_join_count<<<(f + 127) / 128, 128, 0, st>>>(F, f, N, cnt);
+    k_join_count<<<(f + 127) / 128, 128, 0, st>>>(F, f, N, repeats ? 1u : 0u, cnt);
     note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_join_emit(const fem_episode *F, uint32_t f, uint32_t N, const uint32_t *off,
-                             fem_episode *out, cudaStream_t st) {
+cudaError_t launch_join_emit(const fem_episode *F, uint32_t f, uint32_t N, bool repeats,
+                             const uint32_t *off, fem_episode *out, cudaStream_t st) {
     if (f == 0) return cudaSuccess;
-    k_join_emit<<<(f + 127) / 128, 128, 0, st>>>(F, f, N, off, out);
+    k_join_emit<<<(f + 127) / 128, 128, 0, st>>>(F, f, N, repeats ? 1u : 0u, off, out);
     note_launch();
     return cudaGetLastError();
 }

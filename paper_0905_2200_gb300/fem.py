@@ -74,7 +74,8 @@ EXPORTS = ["fem_create", "fem_destroy", "fem_set_config", "fem_load_stream", "fe
            "fem_server_create", "fem_server_destroy", "fem_server_open_stream",
            "fem_server_append", "fem_server_submit", "fem_server_poll", "fem_server_result",
            "fem_server_release", "fem_server_drain", "fem_tune_enable", "fem_tune_size",
-           "fem_tune_save", "fem_tune_load", "fem_count_mapconcat_literal"]
+           "fem_tune_save", "fem_tune_load", "fem_count_mapconcat_literal",
+           "fem_mine_levelwise_ex"]
 
 _lib = None
 
@@ -103,6 +104,8 @@ def load(path: str | None = None):
                                    vp, vp, I, vp]),
         "fem_mine_levelwise": (I, [vp, i32, ctypes.POINTER(fem_interval), u32, u32, u32, vp,
                                    ctypes.POINTER(vp)]),
+        "fem_mine_levelwise_ex": (I, [vp, i32, ctypes.POINTER(fem_interval), u32, u32, u32, u32,
+                                      vp, ctypes.POINTER(vp)]),
         "fem_result_level": (I, [vp, u32, ctypes.POINTER(u32), ctypes.POINTER(vp),
                                  ctypes.POINTER(vp)]),
         "fem_result_max_level": (u32, [vp]),
@@ -320,16 +323,26 @@ def fem_count_two_pass(ctx, sid, cands, intervals, theta, exact_out=None, surviv
     return exact_out, survived_out
 
 
-def fem_mine_levelwise(ctx, sid, intervals, theta, max_len, stream=None, raw=False):
+MINE_REPEATED_TYPES = 1
+
+
+def fem_mine_levelwise(ctx, sid, intervals, theta, max_len, stream=None, raw=False,
+                       repeated_types=False):
     """Problem 1: {level: [(types tuple, interval tuple, count), ...]} in canonical order.
 
-    raw=True returns {level: (records uint8[f,16], counts uint32[f])} instead."""
+    raw=True returns {level: (records uint8[f,16], counts uint32[f])} instead;
+    repeated_types=True mines episodes whose types may repeat (fem_mine_levelwise_ex)."""
     lib = load()
     iv, nI = _intervals(intervals)
     res = ctypes.c_void_p()
-    _check(lib.fem_mine_levelwise(ctx, int(sid), iv, nI, int(theta), int(max_len),
-                                  _stream_handle(stream), ctypes.byref(res)),
-           "fem_mine_levelwise")
+    if repeated_types:
+        _check(lib.fem_mine_levelwise_ex(ctx, int(sid), iv, nI, int(theta), int(max_len),
+                                         MINE_REPEATED_TYPES, _stream_handle(stream),
+                                         ctypes.byref(res)), "fem_mine_levelwise_ex")
+    else:
+        _check(lib.fem_mine_levelwise(ctx, int(sid), iv, nI, int(theta), int(max_len),
+                                      _stream_handle(stream), ctypes.byref(res)),
+               "fem_mine_levelwise")
     try:
         out = {}
         for level in range(1, int(max_len) + 1):

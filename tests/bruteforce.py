@@ -78,9 +78,12 @@ def count(types, t, E, lo, hi, relaxed=False):
     return max_disjoint_greedy(spans(occurrences(types, t, E, lo, hi, relaxed)))
 
 
-def all_episodes(n_types, n_intervals, max_len):
-    """Every distinct-type episode of 2..max_len nodes: (types tuple, interval-index tuple)."""
+def all_episodes(n_types, n_intervals, max_len, repeated_types=False):
+    """Every episode of 2..max_len nodes, distinct-type unless repeated_types:
+    (types tuple, interval-index tuple)."""
     for N in range(2, max_len + 1):
-        for tys in itertools.permutations(range(n_types), N):
+        tuples = (itertools.product(range(n_types), repeat=N) if repeated_types
+                  else itertools.permutations(range(n_types), N))
+        for tys in tuples:
             for ivs in itertools.product(range(n_intervals), repeat=N - 1):
                 yield tys, ivs

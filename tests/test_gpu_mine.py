@@ -61,6 +61,27 @@ def test_mine_edge_cases(ctx):
         fem.fem_free_stream(ctx, sid)
 
 
+@pytest.mark.parametrize("segments", [0, 3])
+def test_mine_repeated_types_equals_oracle(ctx, segments):
+    """Mining with repeated types allowed, on a stream with the chains A -> B -> A and
+    C -> D -> C -> E: the repeat-keeping miner equals the oracle's (candidate sets with
+    both distinct and repeated types are split, the repeated ones counted with one
+    segment)."""
+    t, ty = synth.poisson_stream(0xAB, 10, 8.0, 30.0,
+                                 chains=[((0, 1, 0), 3.0, [(2000, 5000), (5000, 10000)]),
+                                         ((2, 3, 2, 4), 2.0, [(0, 2000), (2000, 5000),
+                                                              (10000, 20000)])])
+    sid = fem.fem_load_stream(ctx, ty, t, 10)
+    if segments:
+        fem.fem_set_config(ctx, segments=segments)
+    got = fem.fem_mine_levelwise(ctx, sid, I_MS4, 40, 5, repeated_types=True)
+    want = oracle.mine(ty, t, 10, I_MS4, 40, 5, repeated_types=True)
+    assert got == want
+    assert any(len(set(r[0])) < len(r[0]) for lv in got.values() for r in lv)
+    assert max(got) >= 3
+    fem.fem_free_stream(ctx, sid)
+
+
 @pytest.fixture(scope="module")
 def single_recording(ctx):
     cfg = synth.single_recording()

@@ -322,13 +322,18 @@ def test_mapconcat_cuts_at_timestamp_ties():
 
 
 # --------------------------------------------------------------------------- miner
-def _bf_mine(ty, t, K, I, theta, max_len):
-    """Every distinct-type episode up to max_len, counted, kept if >= theta."""
+def _bf_mine(ty, t, K, I, theta, max_len, repeated_types=False):
+    """Every episode up to max_len (distinct-type unless repeated_types), counted by
+    brute force (maximum non-overlapped set of enumerated occurrences), kept if >= theta."""
     hist = np.bincount(ty, minlength=K)
     res = {1: [((a,), (), int(hist[a])) for a in range(K) if hist[a] >= theta]}
-    eps = list(bf.all_episodes(K, len(I), max_len))
-    lens, E, iv = oracle._pack(eps)
-    cnt = oracle.count_batch(ty, t, lens, E, iv, I, oracle.EXACT)
+    eps = list(bf.all_episodes(K, len(I), max_len, repeated_types))
+    if repeated_types:
+        cnt = [bf.count(ty, t, list(tys), [int(I[i][0]) for i in ivs], [int(I[i][1]) for i in ivs])
+               for tys, ivs in eps]
+    else:
+        lens, E, iv = oracle._pack(eps)
+        cnt = oracle.count_batch(ty, t, lens, E, iv, I, oracle.EXACT)
     for (tys, ivs), c in zip(eps, cnt):
         if c >= theta:
             res.setdefault(len(tys), []).append((tys, ivs, int(c)))
@@ -351,6 +356,23 @@ def test_levelwise_miner_equals_brute_force_miner(seed):
     want = _bf_mine(ty, t, K, I, theta, 4)
     assert got == {k: v for k, v in want.items() if v}
     assert len(got) >= 2
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_repeated_type_miner_equals_brute_force_miner(seed):
+    """Mining with repeated types allowed (A -> B -> A): every episode over 2-3 types
+    up to length 3 counted by brute force (occurrence enumeration + maximum
+    non-overlapped set), against the level-wise miner with the repeat-keeping join."""
+    rng = np.random.default_rng(40 + seed)
+    K = int(rng.integers(2, 4))
+    t, ty = synth.poisson_stream(800 + seed, K, 4.0, 6.0,
+                                 chains=[((0, 1, 0), 3.0, [(2000, 6000)] * 2)])
+    I = np.array([[2000, 6000], [0, 3000]], np.uint32)
+    theta = int(rng.integers(6, 10))
+    got = oracle.mine(ty, t, K, I, theta, 3, repeated_types=True)
+    want = _bf_mine(ty, t, K, I, theta, 3, repeated_types=True)
+    assert got == {k: v for k, v in want.items() if v}
+    assert any(len(set(r[0])) < len(r[0]) for lv in got.values() for r in lv)
 
 
 def test_two_pass_miner_equals_exact_only_miner():
