@@ -44,11 +44,13 @@ OPS_PER_TOUCHED = {"relaxed": 4, "exact": 6}
 # ("level/pass") from one ncu capture, keyed by the SHA-256 of the kernel source it was
 # taken on and the workload (no entry: stale or not captured, reported as null).
 NCU_TRAFFIC = {
-    # counting kernels of commit 6fde740 (device code unchanged since), ncu --set full
-    # of the first mining step: dram__bytes_read.sum + dram__bytes_write.sum per launch
-    "02eb35fb5593365f": {
-        "single_recording_64types_300s": {"2/relaxed": 4230400, "2/exact": 3986432,
-                                          "3/relaxed": 3883008, "3/exact": 3727360},
+    # counting kernels as of commit 6fde740 (device code unchanged since), ncu --set full
+    # of the first mining step with the rule's launch shapes (--no-tune; the same shape
+    # the tuned step uses for its dominant launch, level 3 relaxed):
+    # dram__bytes_read.sum + dram__bytes_write.sum per launch
+    "3764f997b6e8e60e": {
+        "single_recording_64types_300s": {"2/relaxed": 4208384, "2/exact": 3983616,
+                                          "3/relaxed": 3886336, "3/exact": 3726080},
     },
 }
 
@@ -587,6 +589,59 @@ def run_literal(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_windows(args, rank, world, local):
+    """Window-based frequency (Section 2's alternative measure) of the 64-type
+    recording's 16,128 level-2 candidates, 40 ms windows, one thread per episode."""
+    import torch
+
+    from paper_0905_2200_gb300 import build as fembuild
+    from paper_0905_2200_gb300 import fem, synth
+
+    fembuild.build()
+    torch.cuda.set_device(local)
+    cfg = workload(rank)
+    s = cfg["stream"]
+    I = cfg["intervals"]
+    L, E, iv = synth.level2_candidates(range(s.n_types), len(I))
+    ctx = fem.fem_create(local)
+    sid = fem.fem_load_stream(ctx, torch.from_numpy(s.types).cuda(),
+                              torch.from_numpy(s.t.view(np.int32)).cuda(), s.n_types)
+    rec = torch.from_numpy(fem.pack_episodes(L, E, iv)).cuda()
+    m = rec.shape[0]
+    out = torch.zeros(m, dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        fem.fem_count_windows(ctx, sid, rec, I, args.window_us, out=out)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for i, (e0, e1) in enumerate(evs):
+        flush.fill_(i & 0xFF)
+        e0.record()
+        fem.fem_count_windows(ctx, sid, rec, I, args.window_us, out=out)
+        e1.record()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    cnt = out.cpu().numpy()
+    fem.fem_destroy(ctx)
+    if rank != 0:
+        return
+    span = int(s.t[-1]) - int(s.t[0]) + args.window_us
+    line = {
+        "metric": METRIC, "value": m * s.n / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded Poisson spike trains with embedded cascades)",
+        "config": {"workload": cfg["name"] + "_level2_window_frequency", "n_events": s.n,
+                   "candidates": m, "window_us": args.window_us,
+                   "l2": "flushed between steps (256 MiB device write outside the step events)",
+                   "step": "fem_count_windows over all level-2 candidates"},
+        "window_fraction": {"min": float(cnt.min() / span), "median": float(np.median(cnt) / span),
+                            "max": float(cnt.max() / span)},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # --------------------------------------------------------------------------- serving form
 def run_serving(args, rank, world, local):
     """32 live streams appended in 100 ms chunks at real-time pace after a 60 s
@@ -782,13 +837,15 @@ def main(argv=None):
                     help="launch shapes from the fixed rule instead of measured ones")
     ap.add_argument("--workload",
                     choices=["single_recording", "deep", "batched", "serving", "large",
-                             "bursty", "literal"],
+                             "bursty", "literal", "windows"],
                     default="single_recording",
                     help="deep: the same recording mined at theta = 300 (levels 3-6 reached)")
     ap.add_argument("--session-s", type=float, default=20.0)
     ap.add_argument("--req-rate", type=float, default=10.0)
     ap.add_argument("--serve-budget-gb", type=int, default=16)
     ap.add_argument("--recordings", type=int, default=256)
+    ap.add_argument("--window-us", type=int, default=40_000,
+                    help="--workload windows: window width in microseconds")
     ap.add_argument("--segments", type=int, default=20,
                     help="--workload literal: segments per episode for both schemes")
     args = ap.parse_args(argv)
@@ -806,6 +863,8 @@ def main(argv=None):
             run_large(args, rank, world, local)
         elif args.workload == "literal":
             run_literal(args, rank, world, local)
+        elif args.workload == "windows":
+            run_windows(args, rank, world, local)
         else:
             run_ours(args, rank, world, local)
     finally:

@@ -71,6 +71,9 @@ def _load():
         lib.orc_two_pass.restype = ctypes.c_int
         lib.orc_two_pass.argtypes = [u8p, u32p, i64, i64, u8p, u8p, u32p, u32p,
                                      ctypes.c_uint32, u32p, u32p, u8p]
+        lib.orc_count_windows.restype = ctypes.c_uint64
+        lib.orc_count_windows.argtypes = [u8p, u32p, i64, ctypes.c_int, u8p, u32p, u32p,
+                                          ctypes.c_uint32]
         lib.orc_count_mapconcat_literal.restype = ctypes.c_uint32
         lib.orc_count_mapconcat_literal.argtypes = [u8p, u32p, i64, ctypes.c_int, u8p, u32p,
                                                     u32p, i64, i64p, i64p, i64p]
@@ -147,6 +150,31 @@ def count_mapconcat(types, t, ep_types, lo, hi, bounds, pass_=EXACT, return_size
     if r == 0xFFFFFFFF:
         raise ValueError("bad segmentation or out of memory")
     return (int(r), sizes[:P]) if return_sizes else int(r)
+
+
+def count_windows(types, t, ep_types, lo, hi, w):
+    """Window-based frequency (Section 2's alternative measure, with the episode's
+    interval constraints): how many integer starts s have an occurrence inside the
+    window [s, s + w)."""
+    lib = _load()
+    types, t = _stream(types, t)
+    N = len(ep_types)
+    E, L, H = _edges(ep_types, lo, hi)
+    r = lib.orc_count_windows(_p(types, ctypes.c_uint8), _p(t, ctypes.c_uint32), len(t), N,
+                              _p(E, ctypes.c_uint8), _p(L, ctypes.c_uint32),
+                              _p(H, ctypes.c_uint32), int(w))
+    if r == 0xFFFFFFFFFFFFFFFF:
+        raise ValueError("bad episode or window, or out of memory")
+    return int(r)
+
+
+def count_windows_batch(types, t, lens, ep_types, ivl, intervals, w):
+    """count_windows for m candidates given as (len, types, interval indices)."""
+    lo, hi = resolve(lens, ep_types, ivl, intervals)
+    E = np.asarray(ep_types, dtype=np.uint8).reshape(-1, LMAX)
+    return np.array([count_windows(types, t, E[i, :int(lens[i])], lo[i, :int(lens[i]) - 1],
+                                   hi[i, :int(lens[i]) - 1], w) for i in range(len(lens))],
+                    np.uint64)
 
 
 def count_mapconcat_literal(types, t, ep_types, lo, hi, tau):

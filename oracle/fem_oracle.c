@@ -504,3 +504,59 @@ uint32_t orc_count_mapconcat_literal(const uint8_t *type, const uint32_t *t, int
     if (diag) { diag[0] = none; diag[1] = several; }
     return (uint32_t)total;
 }
+
+/* ------------------------------------------------------------------------ */
+/*
+ * Window-based frequency, the alternative the paper's Section 2 names (windows of
+ * Mannila et al.), with the episode's interval constraints (reading R14): the
+ * number of integer window starts s such that the window [s, s + w) holds every
+ * event of some occurrence (t[i_1] >= s and t[i_N] < s + w).
+ *
+ * For each event j that can be the last node, L(j) = the latest first-node time
+ * over the occurrences ending at j, by the recurrence over nodes
+ *   L_0(j) = t[j];  L_k(j) = max { L_{k-1}(i) : i < j, type[i] = E[k-1],
+ *                                  lo[k-1] < t[j] - t[i] <= hi[k-1] }
+ * (undefined if the set is empty).  The occurrences ending at j then cover exactly
+ * the starts s in (t[j] - w, L(j)], and the count is the size of the union of
+ * those ranges over j.
+ */
+uint64_t orc_count_windows(const uint8_t *type, const uint32_t *t, int64_t n, int N,
+                           const uint8_t *E, const uint32_t *lo, const uint32_t *hi,
+                           uint32_t w)
+{
+    if (N < 1 || N > ORC_LMAX || w == 0) return UINT64_MAX;
+    int64_t *L = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * (size_t)N * sizeof(int64_t));
+    if (!L) return UINT64_MAX;
+    for (int64_t q = 0; q < n * N; q++) L[q] = -1;          /* -1: undefined */
+    for (int k = 0; k < N; k++) {
+        for (int64_t j = 0; j < n; j++) {
+            if (type[j] != E[k]) continue;
+            if (k == 0) { L[j * N] = t[j]; continue; }
+            int64_t best = -1;
+            for (int64_t i = j - 1; i >= 0 && t[j] - t[i] <= hi[k - 1]; i--) {
+                if (type[i] != E[k - 1] || L[i * N + k - 1] < 0) continue;
+                if (t[j] - t[i] <= lo[k - 1]) continue;
+                if (L[i * N + k - 1] > best) best = L[i * N + k - 1];
+            }
+            L[j * N + k] = best;
+        }
+    }
+    uint64_t total = 0;
+    int64_t cur_a = 0, cur_b = -1;                          /* merged [cur_a, cur_b] */
+    int have = 0;
+    for (int64_t j = 0; j < n; j++) {
+        int64_t b = L[j * N + N - 1];
+        if (type[j] != E[N - 1] || b < 0) continue;
+        int64_t a = (int64_t)t[j] - (int64_t)w + 1;
+        if (a > b) continue;                                /* occurrence longer than w */
+        if (have && a <= cur_b + 1) {
+            if (b > cur_b) cur_b = b;
+        } else {
+            if (have) total += (uint64_t)(cur_b - cur_a + 1);
+            cur_a = a; cur_b = b; have = 1;
+        }
+    }
+    if (have) total += (uint64_t)(cur_b - cur_a + 1);
+    free(L);
+    return total;
+}

@@ -904,6 +904,57 @@ int fem_count_mapconcat_literal(fem_ctx *c, int32_t id, const fem_episode *cands
     return FEM_OK;
 }
 
+int fem_count_windows(fem_ctx *c, int32_t id, const fem_episode *cands, uint32_t m,
+                      int cands_on_device, const fem_interval *I, uint32_t nI, uint32_t window_us,
+                      uint64_t *counts_out, int counts_on_device, void *cuda_stream) {
+    if (!c || (m && (!cands || !counts_out)) || window_us == 0) return FEM_EINVAL;
+    const StreamDev *s = find_stream(c, id);
+    if (!s) return FEM_ENOSTREAM;
+    RET(check_intervals(*s, I, nI));
+    if (m == 0) return FEM_OK;
+    cudaSetDevice(c->device);
+    cudaStream_t st = pick(c, cuda_stream);
+    CK(cudaMemsetAsync(c->d_err, 0, 4, st));
+    uint2 *d_ivl;
+    RET(upload_intervals(c, I, nI, st, &d_ivl));
+    const fem_episode *dc = cands;
+    if (!cands_on_device) {
+        fem_episode *tmp;
+        RET(dbuf(c, "cands_in", m, &tmp));
+        CK(cudaMemcpyAsync(tmp, cands, (size_t)m * sizeof(fem_episode), cudaMemcpyHostToDevice, st));
+        dc = tmp;
+    }
+    uint64_t *dout = counts_out;
+    if (!counts_on_device) RET(dbuf(c, "win_out", m, &dout));
+    CK(cudaMemsetAsync(c->d_small + W_INFO, 0, 2 * sizeof(uint32_t), st));
+    CK(launch_validate_cands(dc, nullptr, m, s->K, nI, c->d_small + W_INFO, c->d_err, st));
+    uint32_t info[2], e;
+    RET(read_words(c, c->d_small + W_INFO, 2, info, st));
+    RET(read_err(c, st, &e));
+    RET(err_status(e));
+    if (info[1]) return FEM_EINVAL;  // distinct types only
+    WindowParams p{};
+    p.bev = s->bev;
+    p.boff = s->boff;
+    p.offs = s->offs;
+    p.n = s->n;
+    p.cands = dc;
+    p.m = m;
+    p.ivl = d_ivl;
+    p.w = window_us;
+    p.out = dout;
+    p.err = c->d_err;
+    CK(launch_count_windows(p, info[0], st));
+    RET(read_err(c, st, &e));
+    if (e & ERR_RING) return FEM_EOVERFLOW;
+    RET(err_status(e));
+    if (!counts_on_device) {
+        CK(cudaMemcpyAsync(counts_out, dout, (size_t)m * 8, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return FEM_OK;
+}
+
 int fem_count_two_pass(fem_ctx *c, int32_t id, const fem_episode *cands, uint32_t m,
                        int cands_on_device, const fem_interval *I, uint32_t nI, uint32_t theta,
                        uint32_t *exact_out, uint8_t *survived_out, int outs_on_device,

@@ -191,6 +191,20 @@ cudaError_t launch_count_batch(int N, int pass, uint32_t ring_cap, uint32_t thre
                                const uint32_t *n_items, uint32_t *queue, uint32_t SB,
                                int sm_count, cudaStream_t st);
 cudaError_t count_set_smem_limits();
+// fem_windows.cu: window-based frequency, one thread per episode (distinct types)
+struct WindowParams {
+    const uint2 *bev;
+    const uint16_t *boff;
+    uint32_t offs;
+    uint64_t n;
+    const fem_episode *cands;
+    uint32_t m;
+    const uint2 *ivl;
+    uint32_t w;          // window width (us), > 0
+    uint64_t *out;       // [m]
+    uint32_t *err;
+};
+cudaError_t launch_count_windows(const WindowParams &p, uint32_t len_mask, cudaStream_t st);
 // fem_literal.cu: map (one thread per episode, segment and machine) and join;
 // len_mask has bit N set for every episode length N present; diag[2] accumulates the
 // boundaries where no tuple / several tuples matched

@@ -75,7 +75,7 @@ EXPORTS = ["fem_create", "fem_destroy", "fem_set_config", "fem_load_stream", "fe
            "fem_server_append", "fem_server_submit", "fem_server_poll", "fem_server_result",
            "fem_server_release", "fem_server_drain", "fem_tune_enable", "fem_tune_size",
            "fem_tune_save", "fem_tune_load", "fem_count_mapconcat_literal",
-           "fem_mine_levelwise_ex"]
+           "fem_mine_levelwise_ex", "fem_count_windows"]
 
 _lib = None
 
@@ -114,6 +114,8 @@ def load(path: str | None = None):
         "fem_strerror": (ctypes.c_char_p, [I]),
         "fem_count_mapconcat_literal": (I, [vp, i32, vp, u32, I, ctypes.POINTER(fem_interval),
                                             u32, u32, vp, I, ctypes.POINTER(u32), vp]),
+        "fem_count_windows": (I, [vp, i32, vp, u32, I, ctypes.POINTER(fem_interval), u32, u32,
+                                  vp, I, vp]),
         "fem_tune_enable": (I, [vp, I]),
         "fem_tune_size": (I, [vp, ctypes.POINTER(u32)]),
         "fem_tune_save": (I, [vp, ctypes.c_char_p]),
@@ -239,6 +241,20 @@ def fem_count_mapconcat_literal(ctx, sid, cands, intervals, segments, out=None, 
                                            diag, _stream_handle(stream)),
            "fem_count_mapconcat_literal")
     return out, (int(diag[0]), int(diag[1]))
+
+
+def fem_count_windows(ctx, sid, cands, intervals, window_us, out=None, stream=None):
+    """Window-based frequency of each candidate: uint64[m] window starts (or `out`)."""
+    lib = load()
+    m = int(cands.shape[0])
+    pc, dc = _ptr(cands)
+    if out is None:
+        out = np.zeros(m, np.uint64)
+    po, do = _ptr(out)
+    iv, nI = _intervals(intervals)
+    _check(lib.fem_count_windows(ctx, int(sid), pc, m, dc, iv, nI, int(window_us), po, do,
+                                 _stream_handle(stream)), "fem_count_windows")
+    return out
 
 
 def fem_tune_enable(ctx, on=True):

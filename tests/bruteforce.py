@@ -87,3 +87,13 @@ def all_episodes(n_types, n_intervals, max_len, repeated_types=False):
         for tys in tuples:
             for ivs in itertools.product(range(n_intervals), repeat=N - 1):
                 yield tys, ivs
+
+
+def window_count(types, t, E, lo, hi, w):
+    """Number of integer window starts s such that some occurrence lies inside
+    [s, s + w): the union over occurrences of the starts in (t_last - w, t_first]."""
+    starts = set()
+    for o in occurrences(types, t, E, lo, hi):
+        a, b = int(t[o[-1]]) - w + 1, int(t[o[0]])
+        starts.update(range(a, b + 1))
+    return len(starts)

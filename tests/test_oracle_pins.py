@@ -436,3 +436,25 @@ def test_literal_mapconcat_catalogued_divergences(name):
     idx = [0] + [int(np.searchsorted(t, x, side="right")) for x in d["tau"][1:-1]] + [len(t)]
     idx = sorted(set(idx))
     assert oracle.count_mapconcat(ty, t, E, lo, hi, idx) == d["exact_count"][0]
+
+
+# --------------------------------------------------------------------------- window-based frequency
+@pytest.mark.parametrize("seed", range(40))
+def test_window_count_equals_brute_force(seed):
+    """The window-based frequency (Section 2's alternative measure) by the oracle's
+    recurrence over nodes equals the union of every occurrence's window starts."""
+    rng = np.random.default_rng(6000 + seed)
+    ty, t = synth.tiny_stream(6000 + seed, int(rng.integers(1, 30)), 3, 4, tie_prob=0.2)
+    E, lo, hi = random_episode(rng, 3, int(rng.integers(1, 4)), 8)
+    for w in (1, 3, 9, 30):
+        assert oracle.count_windows(ty, t, E, lo, hi, w) == bf.window_count(ty, t, E, lo, hi, w)
+
+
+def test_window_count_single_node_and_empty():
+    """One node: each event covers w starts, merged where they overlap; an episode
+    that never occurs covers none."""
+    ty = np.array([0, 0, 1, 0], np.uint8)
+    t = np.array([10, 12, 13, 40], np.uint32)
+    assert oracle.count_windows(ty, t, [0], [], [], 5) == len(set(range(6, 11)) | set(range(8, 13))
+                                                              | set(range(36, 41)))
+    assert oracle.count_windows(ty, t, [1, 1], [0], [5], 5) == 0
