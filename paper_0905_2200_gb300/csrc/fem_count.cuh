@@ -576,135 +576,158 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                 }
             }
             const uint32_t lim = c + 1 == c_end ? hi_local : KEY_END;
-            const bool lean =
+            bool lean =
                 distinct && (!MC || (c >= c_seg0 && umask == 0 && c_start[0] != 0xFFFFFFFFu));
-            if (lean && !purged) {
-                purge_invisible();
-                purged = true;
-            }
-            if (EXN && lean && ring2) {
-                if (!in_regs2) to_regs2();
-                for (;;) {
-                    uint32_t mk = key[0];
-#pragma unroll
-                    for (int k = 1; k < N; ++k) mk = min(mk, key[k]);
-                    if (mk >= lim) break;
-                    for_nodes_desc<N - 1>([&](auto kc) {
-                        constexpr int k = decltype(kc)::value;
-                        if (key[k] == mk) {
-                            const uint32_t tt = tv[k];
-                            // drop list q's clusters that ended more than hi before tt
-                            auto pop2 = [&](int q) {
-                                if (tail[q] > 0 && tt - fy[q] > ep.hi[q])
-                                    fx[q] = bx[q], fy[q] = by[q], --tail[q];
-                                if (tail[q] > 0 && tt - fy[q] > ep.hi[q]) tail[q] = 0;
-                            };
-                            // append tt to list q (tail = number of live clusters)
-                            auto push2 = [&](int q) {
-                                pop2(q);
-                                const uint32_t n = tail[q];
-                                if (n > 0 && tt - by[q] <= ep.hi[q] - ep.lo[q]) {
-                                    by[q] = tt;
-                                    if (n == 1) fy[q] = tt;
-                                } else if (n == 0) {
-                                    fx[q] = fy[q] = bx[q] = by[q] = tt, tail[q] = 1;
-                                } else if (n == 1) {
-                                    bx[q] = by[q] = tt, tail[q] = 2;
-                                } else {  // cannot happen when hi >= 2 lo; reported
-                                    overflow = true;
-                                    fx[q] = bx[q], fy[q] = by[q], bx[q] = by[q] = tt;
-                                }
-                            };
-                            if constexpr (k == 0) {
-                                push2(0);
-                            } else {
-                                constexpr int q = k - 1;
-                                pop2(q);
-                                if (tail[q] > 0 && tt - fx[q] > ep.lo[q]) {
-                                    if constexpr (k == N - 1) {
-                                        if constexpr (MC) {
-                                            c_start[0] = (uint32_t)(cbase + mk) + 1, ++c_cnt[0],
-                                            c0_done = true;
-                                        } else {
-                                            ++cnt;
-                                        }
-#pragma unroll
-                                        for (int r = 0; r < NE; ++r) tail[r] = 0;
-                                    } else {
-                                        push2(k);
-                                    }
-                                }
-                            }
-                            ++ptr[k];
-                            const uint2 e = ev[ptr[k]];
-                            tv[k] = e.x;
-                            key[k] = ptr[k] < end[k] ? e.y : KEY_END;
-                        }
-                    });
-                }
-            } else if (lean) {
+            if (!lean) {
+                if (in_regs2) from_regs2();
+                uint32_t since = 0;
                 for (;;) {
                     uint32_t mk = key[0];
 #pragma unroll
                     for (int k = 1; k < N; ++k) mk = min(mk, key[k]);
                     if (mk >= lim) break;
                     const uint32_t gidx = (uint32_t)(cbase + mk);
+                    const bool last_hit = key[N - 1] == mk;
+                    capable = false;
+                    bool done = false;
                     for_nodes_desc<N - 1>([&](auto kc) {
                         constexpr int k = decltype(kc)::value;
                         if (key[k] == mk) {
-                            step_lean(kc, tv[k], gidx);
+                            if (!done) done = step(kc, tv[k], gidx);
+                            // next entry of this group; reading one past the group's end stays
+                            // inside the stage buffer and the value is then discarded
                             ++ptr[k];
                             const uint2 e = ev[ptr[k]];
                             tv[k] = e.x;
                             key[k] = ptr[k] < end[k] ? e.y : KEY_END;
                         }
                     });
-                }
-            } else {
-            if (in_regs2) from_regs2();
-            for (;;) {
-                uint32_t mk = key[0];
+                    if (MC && last_hit && capable && (uint64_t)gidx < L &&
+                        c_start[0] != gidx + 1) {
+                        // entry class r = gidx (the serial machine's last completion was r);
+                        // when class "none" completed at r too, it is that class: no slot
+                        const uint32_t free_slots = ~used & (((1u << SC) - 1u) & ~1u);
+                        if (free_slots) {
+                            const int q0 = __ffs(free_slots) - 1;
 #pragma unroll
-                for (int k = 1; k < N; ++k) mk = min(mk, key[k]);
-                if (mk >= lim) break;
-                const uint32_t gidx = (uint32_t)(cbase + mk);
-                const bool last_hit = key[N - 1] == mk;
-                capable = false;
-                bool done = false;
-                for_nodes_desc<N - 1>([&](auto kc) {
-                    constexpr int k = decltype(kc)::value;
-                    if (key[k] == mk) {
-                        if (!done) done = step(kc, tv[k], gidx);
-                        // next entry of this group; reading one past the group's end stays
-                        // inside the stage buffer and the value is then discarded
-                        ++ptr[k];
-                        const uint2 e = ev[ptr[k]];
-                        tv[k] = e.x;
-                        key[k] = ptr[k] < end[k] ? e.y : KEY_END;
-                    }
-                });
-                if (MC && last_hit && capable && (uint64_t)gidx < L &&
-                    c_start[0] != gidx + 1) {
-                    // entry class r = gidx (the serial machine's last completion was r);
-                    // when class "none" completed at r too, it is that class: no slot
-                    const uint32_t free_slots = ~used & (((1u << SC) - 1u) & ~1u);
-                    if (free_slots) {
-                        const int q0 = __ffs(free_slots) - 1;
-#pragma unroll
-                        for (int q = 1; q < SC; ++q) {
-                            if (q == q0) {
-                                c_key[q] = gidx;
-                                c_start[q] = gidx + 1;
-                                c_cnt[q] = 0;
+                            for (int q = 1; q < SC; ++q) {
+                                if (q == q0) {
+                                    c_key[q] = gidx;
+                                    c_start[q] = gidx + 1;
+                                    c_cnt[q] = 0;
+                                }
                             }
+                            used |= 1u << q0;
+                            umask |= 1u << q0;
+                        } else {
+                            class_overflow = true;
                         }
-                        used |= 1u << q0;
-                        umask |= 1u << q0;
-                    } else {
-                        class_overflow = true;
+                    }
+                    // Exact MapConcatenate: classes also merge every 64 events (not only at
+                    // chunk ends), and once class "none" is the only one left inside the
+                    // segment the rest of the chunk takes the lean step.  (The relaxed
+                    // pass keeps chunk-end merges: its general step is cheap, and the extra
+                    // registers would cost it occupancy.)
+                    if constexpr (MC && PASS == FEM_PASS_EXACT) {
+                        if (umask && ++since == 64) {
+                            since = 0;
+                            uint32_t nk = key[0], nt = tv[0];
+#pragma unroll
+                            for (int k = 1; k < N; ++k)
+                                if (key[k] < nk) nk = key[k], nt = tv[k];
+                            if (nk < lim) try_merge(nt, c < c_seg0);
+                        }
+                        if (distinct && c >= c_seg0 && umask == 0 && c_start[0] != 0xFFFFFFFFu) {
+                            lean = true;
+                            break;
+                        }
                     }
                 }
             }
+            if (lean) {
+                if (!purged) {
+                    purge_invisible();
+                    purged = true;
+                }
+                if (EXN && ring2) {
+                    if (!in_regs2) to_regs2();
+                    for (;;) {
+                        uint32_t mk = key[0];
+#pragma unroll
+                        for (int k = 1; k < N; ++k) mk = min(mk, key[k]);
+                        if (mk >= lim) break;
+                        for_nodes_desc<N - 1>([&](auto kc) {
+                            constexpr int k = decltype(kc)::value;
+                            if (key[k] == mk) {
+                                const uint32_t tt = tv[k];
+                                // drop list q's clusters that ended more than hi before tt
+                                auto pop2 = [&](int q) {
+                                    if (tail[q] > 0 && tt - fy[q] > ep.hi[q])
+                                        fx[q] = bx[q], fy[q] = by[q], --tail[q];
+                                    if (tail[q] > 0 && tt - fy[q] > ep.hi[q]) tail[q] = 0;
+                                };
+                                // append tt to list q (tail = number of live clusters)
+                                auto push2 = [&](int q) {
+                                    pop2(q);
+                                    const uint32_t n = tail[q];
+                                    if (n > 0 && tt - by[q] <= ep.hi[q] - ep.lo[q]) {
+                                        by[q] = tt;
+                                        if (n == 1) fy[q] = tt;
+                                    } else if (n == 0) {
+                                        fx[q] = fy[q] = bx[q] = by[q] = tt, tail[q] = 1;
+                                    } else if (n == 1) {
+                                        bx[q] = by[q] = tt, tail[q] = 2;
+                                    } else {  // cannot happen when hi >= 2 lo; reported
+                                        overflow = true;
+                                        fx[q] = bx[q], fy[q] = by[q], bx[q] = by[q] = tt;
+                                    }
+                                };
+                                if constexpr (k == 0) {
+                                    push2(0);
+                                } else {
+                                    constexpr int q = k - 1;
+                                    pop2(q);
+                                    if (tail[q] > 0 && tt - fx[q] > ep.lo[q]) {
+                                        if constexpr (k == N - 1) {
+                                            if constexpr (MC) {
+                                                c_start[0] = (uint32_t)(cbase + mk) + 1, ++c_cnt[0],
+                                                c0_done = true;
+                                            } else {
+                                                ++cnt;
+                                            }
+#pragma unroll
+                                            for (int r = 0; r < NE; ++r) tail[r] = 0;
+                                        } else {
+                                            push2(k);
+                                        }
+                                    }
+                                }
+                                ++ptr[k];
+                                const uint2 e = ev[ptr[k]];
+                                tv[k] = e.x;
+                                key[k] = ptr[k] < end[k] ? e.y : KEY_END;
+                            }
+                        });
+                    }
+                } else {
+                    for (;;) {
+                        uint32_t mk = key[0];
+#pragma unroll
+                        for (int k = 1; k < N; ++k) mk = min(mk, key[k]);
+                        if (mk >= lim) break;
+                        const uint32_t gidx = (uint32_t)(cbase + mk);
+                        for_nodes_desc<N - 1>([&](auto kc) {
+                            constexpr int k = decltype(kc)::value;
+                            if (key[k] == mk) {
+                                step_lean(kc, tv[k], gidx);
+                                ++ptr[k];
+                                const uint2 e = ev[ptr[k]];
+                                tv[k] = e.x;
+                                key[k] = ptr[k] < end[k] ? e.y : KEY_END;
+                            }
+                        });
+                    }
+                }
             }
             if (MC && umask) try_merge(p.cfirst[c + 1], c < c_seg0);
         }
