@@ -274,7 +274,10 @@ def run_ours(args, rank, world, local):
     all_ach = all_ops / (sum(avg_ms.values()) * 1e-3) / 1e12
     traffic = NCU_TRAFFIC.get(kernel_source_hash(), {}).get(cfg["name"], {}).get(
         f"{dom[0]}/{dom[1]}")
-    kname = f"k_count<{dom[0]}, {dom[1]}{', MapConcatenate' if dom_seg > 1 else ''}>"
+    # the library's kernel for that (length, pass): three register budgets
+    kfn = ("k_count_exact" if dom[1] == "exact" and dom[0] <= 2 else
+           "k_count_wide" if dom[1] == "exact" or dom[0] >= 4 else "k_count")
+    kname = f"{kfn}<{dom[0]}, {dom[1]}{', MapConcatenate' if dom_seg > 1 else ''}>"
 
     # end to end through the public API with host (pinned) buffers
     h_types = torch.from_numpy(s.types.copy()).pin_memory()

@@ -38,7 +38,7 @@ cudaError_t run_batch(const BatchArgs &a, uint32_t threads, int sm_count, cudaSt
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(k_count_batch<N, PASS, MC, R>,
+        attr_err = cudaFuncSetAttribute(count_batch_kernel<N, PASS, MC, R>(),
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     });
     if (attr_err != cudaSuccess) return attr_err;
@@ -49,11 +49,11 @@ cudaError_t run_batch(const BatchArgs &a, uint32_t threads, int sm_count, cudaSt
     if (!blocks) {
         int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, k_count_batch<N, PASS, MC, R>, (int)threads, sm);
+            &per_sm, count_batch_kernel<N, PASS, MC, R>(), (int)threads, sm);
         if (e != cudaSuccess) return e;
         blocks = (uint32_t)std::max(1, per_sm) * (uint32_t)sm_count;
     }
-    k_count_batch<N, PASS, MC, R><<<blocks, threads, sm, st>>>(a.jobs, a.items, a.n_items,
+    count_batch_kernel<N, PASS, MC, R>()<<<blocks, threads, sm, st>>>(a.jobs, a.items, a.n_items,
                                                                a.queue, a.SB);
     note_launch();
     return cudaGetLastError();
@@ -79,14 +79,14 @@ cudaError_t run(const CountParams &p, uint32_t threads, cudaStream_t st) {
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [] {
-        attr_err = cudaFuncSetAttribute(k_count<N, PASS, MC, R>,
+        attr_err = cudaFuncSetAttribute(count_kernel<N, PASS, MC, R>(),
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     });
     if (attr_err != cudaSuccess) return attr_err;
     const size_t sm = count_smem_bytes(N, PASS, MC, R, threads, p.offs);
     if (sm > 227 * 1024) return cudaErrorInvalidConfiguration;
     dim3 grid((p.m + threads - 1) / threads, p.P);
-    k_count<N, PASS, MC, R><<<grid, threads, sm, st>>>(p);
+    count_kernel<N, PASS, MC, R>()<<<grid, threads, sm, st>>>(p);
     note_launch();
     return cudaGetLastError();
 }

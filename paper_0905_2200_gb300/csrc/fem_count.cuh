@@ -808,9 +808,14 @@ __device__ __forceinline__ void init_stage_bars(uint8_t *smem, uint32_t SB) {
     __syncthreads();
 }
 
-// One block per (episode tile, segment) of one candidate set.
+// One block per (episode tile, segment) of one candidate set.  Three register
+// budgets, each the fastest measured for its kernels: the compiler's default for the
+// relaxed pass up to three nodes (64 registers keep four 256-thread blocks per SM);
+// three blocks per SM for the exact pass with two nodes; and one block's worth for
+// longer episodes, whose class tables and lists otherwise land in local memory
+// (level-5 relaxed on the 11.8M-event stream: 170 -> 71 ms).
 template <int N, int PASS, bool MC, int R>
-__global__ void __launch_bounds__(256) k_count(const CountParams p) {
+__device__ __forceinline__ void count_block(const CountParams &p) {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t SB = stage_bytes(p.offs);
     init_stage_bars(smem, SB);
@@ -818,15 +823,30 @@ __global__ void __launch_bounds__(256) k_count(const CountParams p) {
     count_item<N, PASS, MC, R>(p, blockIdx.x, blockIdx.y, smem, SB, q);
 }
 
+template <int N, int PASS, bool MC, int R>
+__global__ void __launch_bounds__(256) k_count(const CountParams p) {
+    count_block<N, PASS, MC, R>(p);
+}
+
+template <int N, int PASS, bool MC, int R>
+__global__ void __launch_bounds__(256, 3) k_count_exact(const CountParams p) {
+    count_block<N, PASS, MC, R>(p);
+}
+
+template <int N, int PASS, bool MC, int R>
+__global__ void __launch_bounds__(256, 1) k_count_wide(const CountParams p) {
+    count_block<N, PASS, MC, R>(p);
+}
+
 // Persistent form for a batch of candidate sets over several streams: each block
 // takes (job, tile, segment) items from a device queue until the list is
 // exhausted.  Items come longest first; `jobs` and the item list are device
 // resident, so a captured graph can replay the launch with new sizes.
 template <int N, int PASS, bool MC, int R>
-__global__ void __launch_bounds__(256) k_count_batch(const CountParams *__restrict__ jobs,
-                                                     const uint4 *__restrict__ items,
-                                                     const uint32_t *n_items, uint32_t *queue,
-                                                     uint32_t SB) {
+__device__ __forceinline__ void count_batch_loop(const CountParams *__restrict__ jobs,
+                                                 const uint4 *__restrict__ items,
+                                                 const uint32_t *n_items, uint32_t *queue,
+                                                 uint32_t SB) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ CountParams s_job;
     __shared__ uint32_t s_item;
@@ -843,6 +863,46 @@ __global__ void __launch_bounds__(256) k_count_batch(const CountParams *__restri
         if (!count_item<N, PASS, MC, R>(s_job, d.y, d.z, smem, SB, q)) break;
         __syncthreads();
     }
+}
+
+template <int N, int PASS, bool MC, int R>
+__global__ void __launch_bounds__(256) k_count_batch(const CountParams *__restrict__ jobs,
+                                                     const uint4 *__restrict__ items,
+                                                     const uint32_t *n_items, uint32_t *queue,
+                                                     uint32_t SB) {
+    count_batch_loop<N, PASS, MC, R>(jobs, items, n_items, queue, SB);
+}
+
+template <int N, int PASS, bool MC, int R>
+__global__ void __launch_bounds__(256, 3)
+    k_count_batch_exact(const CountParams *__restrict__ jobs, const uint4 *__restrict__ items,
+                        const uint32_t *n_items, uint32_t *queue, uint32_t SB) {
+    count_batch_loop<N, PASS, MC, R>(jobs, items, n_items, queue, SB);
+}
+
+template <int N, int PASS, bool MC, int R>
+__global__ void __launch_bounds__(256, 1)
+    k_count_batch_wide(const CountParams *__restrict__ jobs, const uint4 *__restrict__ items,
+                       const uint32_t *n_items, uint32_t *queue, uint32_t SB) {
+    count_batch_loop<N, PASS, MC, R>(jobs, items, n_items, queue, SB);
+}
+
+// The kernel (register budget) of a (N, pass, MC, R) instantiation.
+template <int N, int PASS>
+constexpr int count_budget() {  // 0: compiler default, 3: three blocks per SM, 1: one
+    return PASS == FEM_PASS_EXACT ? (N <= 2 ? 3 : 1) : (N <= 3 ? 0 : 1);
+}
+template <int N, int PASS, bool MC, int R>
+constexpr auto count_kernel() {
+    if constexpr (count_budget<N, PASS>() == 3) return k_count_exact<N, PASS, MC, R>;
+    else if constexpr (count_budget<N, PASS>() == 1) return k_count_wide<N, PASS, MC, R>;
+    else return k_count<N, PASS, MC, R>;
+}
+template <int N, int PASS, bool MC, int R>
+constexpr auto count_batch_kernel() {
+    if constexpr (count_budget<N, PASS>() == 3) return k_count_batch_exact<N, PASS, MC, R>;
+    else if constexpr (count_budget<N, PASS>() == 1) return k_count_batch_wide<N, PASS, MC, R>;
+    else return k_count_batch<N, PASS, MC, R>;
 }
 
 }  // namespace fem
