@@ -261,16 +261,23 @@ int tune_pass(fem_ctx *c, const std::string &key, const StreamDev &s, const fem_
         for (uint32_t T : Ts) {
             c->cfg.segments = P;
             c->cfg.threads_per_block = T;
-            cudaEventRecord(c->tev[0], st);
-            rc = count_pass(c, s, cands, gather, m, N, d_ivl, nI, pass, out, distinct, st, nullptr);
-            cudaEventRecord(c->tev[1], st);
-            if (rc != FEM_OK) break;
-            float ms = 0;
-            if (cudaEventSynchronize(c->tev[1]) != cudaSuccess ||
-                cudaEventElapsedTime(&ms, c->tev[0], c->tev[1]) != cudaSuccess) {
-                rc = FEM_ECUDA;
-                break;
+            // twice, keeping the faster: the first launch of a kernel also loads it
+            float ms = -1;
+            for (int rep = 0; rep < 2 && rc == FEM_OK; ++rep) {
+                cudaEventRecord(c->tev[0], st);
+                rc = count_pass(c, s, cands, gather, m, N, d_ivl, nI, pass, out, distinct, st,
+                                nullptr);
+                cudaEventRecord(c->tev[1], st);
+                if (rc != FEM_OK) break;
+                float t = 0;
+                if (cudaEventSynchronize(c->tev[1]) != cudaSuccess ||
+                    cudaEventElapsedTime(&t, c->tev[0], c->tev[1]) != cudaSuccess) {
+                    rc = FEM_ECUDA;
+                    break;
+                }
+                if (ms < 0 || t < ms) ms = t;
             }
+            if (rc != FEM_OK) break;
             if (!best.P || ms < best.ms) best = fem_ctx::Shape{P, T, ms};
         }
         if (rc != FEM_OK) break;
@@ -1373,16 +1380,20 @@ int batch_tune(fem_batch *b, cudaStream_t st) {
                 if (Tr == 256 && g.N > 3) continue;
                 for (uint32_t Tx : {64u, 128u}) {
                     RET(batch_shape(g, cpi, Tr, Tx, st));
-                    CK(cudaMemsetAsync(c->d_err, 0, 4, st));
-                    CK(cudaEventRecord(c->tev[0], st));
-                    RET(batch_enqueue_group(c, g, st));
-                    CK(cudaEventRecord(c->tev[1], st));
-                    uint32_t e;
-                    RET(read_err(c, st, &e));
-                    RET(err_status(e));
-                    float ms = 0;
-                    CK(cudaEventElapsedTime(&ms, c->tev[0], c->tev[1]));
-                    if (e & (ERR_RING | ERR_TABLE | ERR_CLASS)) ms *= 4;  // needs recounts
+                    float ms = -1;
+                    for (int rep = 0; rep < 2; ++rep) {  // the faster of two (kernel loading)
+                        CK(cudaMemsetAsync(c->d_err, 0, 4, st));
+                        CK(cudaEventRecord(c->tev[0], st));
+                        RET(batch_enqueue_group(c, g, st));
+                        CK(cudaEventRecord(c->tev[1], st));
+                        uint32_t e;
+                        RET(read_err(c, st, &e));
+                        RET(err_status(e));
+                        float t = 0;
+                        CK(cudaEventElapsedTime(&t, c->tev[0], c->tev[1]));
+                        if (e & (ERR_RING | ERR_TABLE | ERR_CLASS)) t *= 4;  // needs recounts
+                        if (ms < 0 || t < ms) ms = t;
+                    }
                     if (best < 0 || ms < best) best = ms, bc = cpi, br = Tr, bx = Tx;
                 }
             }
