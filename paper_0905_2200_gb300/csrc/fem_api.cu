@@ -69,10 +69,18 @@ struct fem_ctx {
 
 namespace {
 
-#define CK(x)                                   \
-    do {                                        \
-        cudaError_t e_ = (x);                   \
-        if (e_ != cudaSuccess) return FEM_ECUDA; \
+// FEM_DEBUG set: a failing CUDA call is reported on stderr with its line
+void report_cuda(cudaError_t e, int line) {
+    if (std::getenv("FEM_DEBUG"))
+        std::fprintf(stderr, "fem: CUDA error %s at fem_api.cu:%d\n", cudaGetErrorString(e), line);
+}
+#define CK(x)                          \
+    do {                               \
+        cudaError_t e_ = (x);          \
+        if (e_ != cudaSuccess) {       \
+            report_cuda(e_, __LINE__); \
+            return FEM_ECUDA;          \
+        }                              \
     } while (0)
 #define RET(x)                  \
     do {                        \
@@ -194,9 +202,9 @@ uint32_t choose_segments(fem_ctx *c, const StreamDev &s, uint32_t m, bool distin
     return (uint32_t)std::min<uint64_t>(P, maxP);
 }
 
-uint32_t choose_threads(fem_ctx *c, int N, int pass, bool mc, uint32_t R, uint32_t offs,
-                        uint32_t m) {
-    if (c->cfg.threads_per_block) return c->cfg.threads_per_block;
+// Block size by shared memory (and, for few episodes, smaller blocks), ignoring any
+// configured size.
+uint32_t auto_threads(int N, int pass, bool mc, uint32_t R, uint32_t offs, uint32_t m) {
     for (uint32_t T : {256u, 128u, 64u, 32u}) {
         if (T > 32 && m <= T / 2) continue;  // few episodes: small blocks, more of them
         if (T == 256 && N > 3) continue;  // register budget
@@ -206,6 +214,12 @@ uint32_t choose_threads(fem_ctx *c, int N, int pass, bool mc, uint32_t R, uint32
         if (count_smem_bytes(N, pass, mc, R, T, offs) <= 220 * 1024) return T;
     }
     return 8;
+}
+
+uint32_t choose_threads(fem_ctx *c, int N, int pass, bool mc, uint32_t R, uint32_t offs,
+                        uint32_t m) {
+    if (c->cfg.threads_per_block) return c->cfg.threads_per_block;
+    return auto_threads(N, pass, mc, R, offs, m);
 }
 
 struct PassInfo {
@@ -353,6 +367,9 @@ int count_launch(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const
     }
     uint32_t T = choose_threads(c, N, pass, P > 1, R, s.offs, m);
     if (T_t && count_smem_bytes(N, pass, P > 1, R, T_t, s.offs) <= 100 * 1024) T = T_t;
+    // a configured block size whose rings would not fit in shared memory is replaced
+    if (count_smem_bytes(N, pass, P > 1, R, T, s.offs) > 200 * 1024)
+        T = auto_threads(N, pass, P > 1, R, s.offs, m);
     CK(cudaEventRecord(c->kev[0], st));
     CK(launch_count(N, pass, P > 1, R, T, p, st));
     CK(cudaEventRecord(c->kev[1], st));
@@ -428,7 +445,9 @@ int count_finish(fem_ctx *c, const StreamDev &s, const PassLaunch &pl, uint32_t 
             q.tables = nullptr;
         }
         const bool mc2 = q.P > 1;
-        const uint32_t T2 = choose_threads(c, N, pass, mc2, Rq, s.offs, r);
+        // the recount's rings are larger: its block size is chosen for them, whatever
+        // size is configured (or being tried) for the first count
+        const uint32_t T2 = auto_threads(N, pass, mc2, Rq, s.offs, r);
         CK(launch_count(N, pass, mc2, Rq, T2, q, st));
         if (mc2) CK(launch_stitch(q.tables, r, q.P, rout, q.redo, c->d_err, st));
         RET(read_err(c, st, &e));

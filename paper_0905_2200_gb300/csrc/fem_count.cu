@@ -12,6 +12,7 @@ size_t count_smem_bytes(int N, int pass, bool mc, uint32_t ring_cap, uint32_t th
     size_t b = 2 * (size_t)stage_bytes(offs) + 128;
     if (pass == FEM_PASS_EXACT && N > 1)
         b += (size_t)(N - 1) * ring_cap * threads * 8u;
+    if (mc && N >= 3) b += (size_t)S_MAX * threads * 4u;  // class keys
     return b;
 }
 
@@ -42,7 +43,7 @@ cudaError_t run_batch(const BatchArgs &a, uint32_t threads, int sm_count, cudaSt
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     });
     if (attr_err != cudaSuccess) return attr_err;
-    size_t sm = 2 * (size_t)a.SB + 128;
+    size_t sm = 2 * (size_t)a.SB + 128 + (N >= 3 ? (size_t)S_MAX * threads * 4u : 0);  // keys
     if (PASS == FEM_PASS_EXACT && N > 1) sm += (size_t)(N - 1) * R * threads * 8u;
     if (sm > 200 * 1024) return cudaErrorInvalidConfiguration;
     uint32_t blocks = a.blocks;

@@ -173,7 +173,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
 #pragma unroll
     for (int k = 0; k < NE; ++k) dl[k] = ms[k] = head[k] = tail[k] = fx[k] = fy[k] = bx[k] = by[k] = 0;
     // MapConcatenate entry classes: class 0 is "none"; class j >= 1 restarts after the
-    // last-node event c_key[j] of the window.  A class that completes at the same
+    // last-node event c_key_s[j] of the window.  A class that completes at the same
     // event as class 0 is identical to it from then on: it is merged (its bit in
     // umask cleared, c_cnt[j] holding its count minus class 0's) and no longer updated.
     constexpr int SC = MC ? S_MAX : 1;
@@ -181,9 +181,32 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
     // before the segment starts has the same count and exit as class "none", so its
     // slot is freed: the stitch reads class "none" for any class key not listed.
     uint32_t used = 0, umask = 0;
-    uint32_t c_key[SC], c_start[SC], c_cnt[SC];
+    // Class keys are written when a class is registered and read for the tables only.
+    // From three nodes on they live in shared memory ([slot][thread], after the rings):
+    // that frees eight registers where the machine state needs them (level-3 relaxed
+    // 0.51 -> 0.47 ms); for two nodes registers are faster.
+    constexpr bool KEYS_SMEM = MC && N >= 3;
+    uint32_t c_start[SC], c_cnt[SC], c_key[KEYS_SMEM ? 1 : SC];
 #pragma unroll
-    for (int j = 0; j < SC; ++j) c_key[j] = CLS_NONE, c_start[j] = 0, c_cnt[j] = 0;
+    for (int j = 0; j < SC; ++j) c_start[j] = 0, c_cnt[j] = 0;
+#pragma unroll
+    for (int j = 0; j < (KEYS_SMEM ? 1 : SC); ++j) c_key[j] = CLS_NONE;
+    uint32_t *c_key_s = reinterpret_cast<uint32_t *>(
+                            ring_raw + (PASS == FEM_PASS_EXACT && N > 1 ? (size_t)NE * R * T * 8u : 0)) +
+                        tid;
+    auto set_key = [&](int q0, uint32_t v) {
+        if constexpr (KEYS_SMEM) {
+            c_key_s[(uint32_t)q0 * T] = v;
+        } else {
+#pragma unroll
+            for (int q = 1; q < SC; ++q)
+                if (q == q0) c_key[q] = v;
+        }
+    };
+    auto get_key = [&](int q) -> uint32_t {
+        if constexpr (KEYS_SMEM) return q == 0 ? CLS_NONE : c_key_s[(uint32_t)q * T];
+        else return c_key[q];
+    };
     // Class "none" is a fresh machine at the window start w: it sees chains whose
     // first event is at index >= w, i.e. whose first node's time is >= X.  Until the
     // first node-0 event at or after X its start is unknown and nothing is visible.
@@ -207,9 +230,9 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                         if (c_start[j] <= msv) {
                             if (!inc) {
                                 // class j says "the serial machine's last completion before
-                                // the segment was c_key[j]"; a completion before the segment
+                                // the segment was c_key_s[j]"; a completion before the segment
                                 // refutes it, so it is never handed in: drop it
-                                used &= ~(1u << j), umask &= ~(1u << j), c_key[j] = CLS_NONE;
+                                used &= ~(1u << j), umask &= ~(1u << j);
                                 continue;
                             }
                             c_start[j] = gidx + 1, c_cnt[j] += inc;
@@ -465,7 +488,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                 if (!differ) {
                     c_cnt[j] -= c_cnt[0];
                     umask &= ~(1u << j);
-                    if (window) used &= ~(1u << j), c_key[j] = CLS_NONE;
+                    if (window) used &= ~(1u << j);
                 }
             }
         }
@@ -609,10 +632,10 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                         const uint32_t free_slots = ~used & (((1u << SC) - 1u) & ~1u);
                         if (free_slots) {
                             const int q0 = __ffs(free_slots) - 1;
+                            set_key(q0, gidx);
 #pragma unroll
                             for (int q = 1; q < SC; ++q) {
                                 if (q == q0) {
-                                    c_key[q] = gidx;
                                     c_start[q] = gidx + 1;
                                     c_cnt[q] = 0;
                                 }
@@ -790,7 +813,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                 // handed on only if it lies in the next segment's window
                 uint32_t ex = (q == 0 && !c0_done) ? CLS_NONE : st - 1u;
                 if (ex != CLS_NONE && !last_seg && p.t[ex] < Xn) ex = CLS_NONE;
-                e = make_uint4(c_key[q], cntq, ex, 0);
+                e = make_uint4(get_key(q), cntq, ex, 0);
             }
             tab[q] = e;
         }

@@ -135,6 +135,32 @@ def test_exact_ring_overflow_is_recounted(ctx):
     fem.fem_free_stream(ctx, sid)
 
 
+@pytest.mark.parametrize("threads", [256, 32])
+def test_recount_block_size_fits_its_rings(ctx, threads):
+    """Overflowing episodes are recounted with larger rings; the recount picks a block
+    size its shared memory can hold, whatever size is configured for the first count
+    (here with three segments, so the segmented recount runs)."""
+    ty, t = [], []
+    cur = 0
+    for b in range(12):              # 12 bursts of 600 events: four chunks, cut in bursts
+        cur += 1_000_000
+        for j in range(600):
+            ty.append(j % 3)
+            t.append(cur + j * 10)
+        ty.append(3)
+        t.append(cur + 5_000)
+    order = np.argsort(np.array(t), kind="stable")
+    ty, t = np.array(ty, np.uint8)[order], np.array(t, np.uint32)[order]
+    sid = fem.fem_load_stream(ctx, ty, t, 4)
+    I = np.array([[4_000, 6_000], [0, 10_000], [1_000, 9_000]], np.uint32)
+    L, E, iv = synth.random_candidates(71, 60, 4, [2, 3, 4], 3)
+    fem.fem_set_config(ctx, segments=3, threads_per_block=threads)
+    got = fem.fem_count_candidates(ctx, sid, fem.pack_episodes(L, E, iv), I, fem.PASS_EXACT)
+    fem.fem_set_config(ctx, reset=True)
+    assert_counts_equal(got, oracle_counts(ty, t, L, E, iv, I, fem.PASS_EXACT), f"T={threads}")
+    fem.fem_free_stream(ctx, sid)
+
+
 @pytest.mark.parametrize("pass_", PASSES)
 def test_repeated_types_use_single_segment_path(ctx, mid, pass_):
     ty, t, K, chains, sid = mid
