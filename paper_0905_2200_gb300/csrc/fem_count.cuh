@@ -801,10 +801,14 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
     if (!MC) {
         p.out[ci] = ok ? cnt : 0u;
     } else {
+        // slots 0 .. n-1 are written (n = 1 + the highest used slot, in slot 0's w);
+        // the stitch reads no further
         uint4 *tab = p.tables + ((uint64_t)seg * p.m + ci) * S_MAX;
+        const uint32_t n_slots = used ? 32u - __clz(used) : 1u;
 #pragma unroll
         for (int q = 0; q < S_MAX; ++q) {
-            uint4 e = make_uint4(CLS_EMPTY, 0, CLS_NONE, 0);
+            if ((uint32_t)q >= n_slots) break;
+            uint4 e = make_uint4(CLS_EMPTY, 0, CLS_NONE, q == 0 ? n_slots : 0u);
             if (ok && (q == 0 || ((used >> q) & 1u))) {
                 const bool merged = q > 0 && !((umask >> q) & 1u);
                 const uint32_t cntq = merged ? c_cnt[0] + c_cnt[q] : c_cnt[q];
@@ -813,7 +817,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                 // handed on only if it lies in the next segment's window
                 uint32_t ex = (q == 0 && !c0_done) ? CLS_NONE : st - 1u;
                 if (ex != CLS_NONE && !last_seg && p.t[ex] < Xn) ex = CLS_NONE;
-                e = make_uint4(get_key(q), cntq, ex, 0);
+                e = make_uint4(get_key(q), cntq, ex, q == 0 ? n_slots : 0u);
             }
             tab[q] = e;
         }

@@ -79,21 +79,25 @@ __device__ void stitch_one(const uint4 *__restrict__ tables, uint32_t m, uint32_
     bool ident = a == b, bad = false;
 #pragma unroll
     for (int j = 0; j < S_MAX; ++j) fk[j] = CLS_EMPTY, fc[j] = 0, fe[j] = CLS_NONE;
-    if (!ident) {
-        const uint4 *ta = tables + ((uint64_t)a * m + ci) * S_MAX;
+    // a table's slot 0 holds, in w, how many slots the counter wrote; the rest are empty
+    auto load_table = [&](const uint4 *t, uint32_t *k, uint32_t *cnt, uint32_t *ex) {
+        const uint4 e0 = t[0];
+        const uint32_t n = e0.w;
+        k[0] = e0.x, cnt[0] = e0.y, ex[0] = e0.z;
 #pragma unroll
-        for (int j = 0; j < S_MAX; ++j) {
-            const uint4 e = ta[j];
-            fk[j] = e.x, fc[j] = e.y, fe[j] = e.z;
-        }
-        for (uint32_t q = a + 1; q < b; ++q) {
-            const uint4 *tq = tables + ((uint64_t)q * m + ci) * S_MAX;
-            uint32_t gk[S_MAX], gc[S_MAX], ge[S_MAX];
-#pragma unroll
-            for (int i = 0; i < S_MAX; ++i) {
-                const uint4 e = tq[i];
-                gk[i] = e.x, gc[i] = e.y, ge[i] = e.z;
+        for (int j = 1; j < S_MAX; ++j) {
+            k[j] = CLS_EMPTY, cnt[j] = 0, ex[j] = CLS_NONE;
+            if ((uint32_t)j < n) {
+                const uint4 e = t[j];
+                k[j] = e.x, cnt[j] = e.y, ex[j] = e.z;
             }
+        }
+    };
+    if (!ident) {
+        load_table(tables + ((uint64_t)a * m + ci) * S_MAX, fk, fc, fe);
+        for (uint32_t q = a + 1; q < b; ++q) {
+            uint32_t gk[S_MAX], gc[S_MAX], ge[S_MAX];
+            load_table(tables + ((uint64_t)q * m + ci) * S_MAX, gk, gc, ge);
 #pragma unroll
             for (int j = 0; j < S_MAX; ++j) {
                 if (fk[j] == CLS_EMPTY) continue;
