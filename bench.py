@@ -44,13 +44,12 @@ OPS_PER_TOUCHED = {"relaxed": 4, "exact": 6}
 # ("level/pass") from one ncu capture, keyed by the SHA-256 of the kernel source it was
 # taken on and the workload (no entry: stale or not captured, reported as null).
 NCU_TRAFFIC = {
-    # counting kernels as of commit 6fde740 (device code unchanged since), ncu --set full
-    # of the first mining step with the rule's launch shapes (--no-tune; the same shape
-    # the tuned step uses for its dominant launch, level 3 relaxed):
-    # dram__bytes_read.sum + dram__bytes_write.sum per launch
-    "3764f997b6e8e60e": {
-        "single_recording_64types_300s": {"2/relaxed": 4208384, "2/exact": 3983616,
-                                          "3/relaxed": 3886336, "3/exact": 3726080},
+    # current counting kernels, ncu --set full of the first mining step with the rule's
+    # launch shapes (--no-tune; the tuned step uses the same shape for its dominant launch,
+    # level 3 relaxed): dram__bytes_read.sum + dram__bytes_write.sum per launch
+    "0691ce70eeae5822": {
+        "single_recording_64types_300s": {"2/relaxed": 13621760, "2/exact": 8650496,
+                                          "3/relaxed": 12829952, "3/exact": 3723008},
     },
 }
 

@@ -1306,6 +1306,7 @@ struct fem_batch {
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    uint32_t graph_kernels = 0;  // kernel nodes of the captured graph (launch accounting)
 };
 
 namespace {
@@ -1584,6 +1585,15 @@ int fem_batch_create(fem_ctx *c, const fem_job *jobs, uint32_t n_jobs, const fem
     if (ce != cudaSuccess) return fail(FEM_ECUDA);
     b->graph = graph;
     BCK(cudaGraphInstantiate(&b->exec, graph, 0));
+    size_t n_nodes = 0;
+    BCK(cudaGraphGetNodes(graph, nullptr, &n_nodes));
+    std::vector<cudaGraphNode_t> nodes(n_nodes);
+    if (n_nodes) BCK(cudaGraphGetNodes(graph, nodes.data(), &n_nodes));
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType ty;
+        BCK(cudaGraphNodeGetType(nd, &ty));
+        b->graph_kernels += ty == cudaGraphNodeTypeKernel;
+    }
     *out = b;
     return FEM_OK;
 #undef BRET
@@ -1598,6 +1608,7 @@ int fem_batch_run(fem_batch *b, void *cuda_stream) {
     CK(cudaMemsetAsync(c->d_err, 0, 4, st));
     if (b->exec) {
         CK(cudaGraphLaunch(b->exec, st));
+        note_launch(b->graph_kernels);
     } else {
         RET(batch_enqueue(b, st));
     }

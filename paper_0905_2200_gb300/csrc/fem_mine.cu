@@ -593,10 +593,24 @@ __device__ __forceinline__ bool has_type(const fem_episode &a, uint32_t N, uint3
 // beta minus its last node; the child appends beta's last edge and node, whose
 // type must be new to alpha.  F is in canonical order, so the betas of one
 // alpha are contiguous and the children come out in canonical order.
+// Up to this many frequent episodes (48 KB) are staged in each block's shared memory,
+// so the binary searches and the scans of matching ranges read no global memory.
+constexpr uint32_t JOIN_SMEM_MAX = 3072;
+
+__device__ __forceinline__ const fem_episode *stage_frequent(const fem_episode *F, uint32_t f) {
+    extern __shared__ uint4 s_freq[];
+    if (f > JOIN_SMEM_MAX) return F;  // uniform over the launch
+    for (uint32_t j = threadIdx.x; j < f; j += blockDim.x)
+        s_freq[j] = reinterpret_cast<const uint4 *>(F)[j];
+    __syncthreads();
+    return reinterpret_cast<const fem_episode *>(s_freq);
+}
+
 // The child alpha + beta's last node is kept if that type is new to alpha, or
 // always when `repeats`.
-__global__ void k_join_count(const fem_episode *__restrict__ F, uint32_t f, uint32_t N,
+__global__ void k_join_count(const fem_episode *__restrict__ Fg, uint32_t f, uint32_t N,
                              uint32_t repeats, uint32_t *__restrict__ cnt) {
+    const fem_episode *F = stage_frequent(Fg, f);
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= f) return;
     const fem_episode a = ld_ep(F, i);
@@ -607,9 +621,10 @@ __global__ void k_join_count(const fem_episode *__restrict__ F, uint32_t f, uint
     cnt[i] = c;
 }
 
-__global__ void k_join_emit(const fem_episode *__restrict__ F, uint32_t f, uint32_t N,
+__global__ void k_join_emit(const fem_episode *__restrict__ Fg, uint32_t f, uint32_t N,
                             uint32_t repeats, const uint32_t *__restrict__ off,
                             fem_episode *__restrict__ out) {
+    const fem_episode *F = stage_frequent(Fg, f);
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= f) return;
     const fem_episode a = ld_ep(F, i);
@@ -631,7 +646,8 @@ __global__ void k_join_emit(const fem_episode *__restrict__ F, uint32_t f, uint3
 cudaError_t launch_join_count(const fem_episode *F, uint32_t f, uint32_t N, bool repeats,
                               uint32_t *cnt, cudaStream_t st) {
     if (f == 0) return cudaSuccess;
-    k_join_count<<<(f + 127) / 128, 128, 0, st>>>(F, f, N, repeats ? 1u : 0u, cnt);
+    const size_t sm = f <= JOIN_SMEM_MAX ? (size_t)f * sizeof(fem_episode) : 0;
+    k_join_count<<<(f + 127) / 128, 128, sm, st>>>(F, f, N, repeats ? 1u : 0u, cnt);
     note_launch();
     return cudaGetLastError();
 }
@@ -639,7 +655,8 @@ cudaError_t launch_join_count(const fem_episode *F, uint32_t f, uint32_t N, bool
 cudaError_t launch_join_emit(const fem_episode *F, uint32_t f, uint32_t N, bool repeats,
                              const uint32_t *off, fem_episode *out, cudaStream_t st) {
     if (f == 0) return cudaSuccess;
-    k_join_emit<<<(f + 127) / 128, 128, 0, st>>>(F, f, N, repeats ? 1u : 0u, off, out);
+    const size_t sm = f <= JOIN_SMEM_MAX ? (size_t)f * sizeof(fem_episode) : 0;
+    k_join_emit<<<(f + 127) / 128, 128, sm, st>>>(F, f, N, repeats ? 1u : 0u, off, out);
     note_launch();
     return cudaGetLastError();
 }
