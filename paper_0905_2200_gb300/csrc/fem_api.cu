@@ -1212,9 +1212,15 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
         cudaEventRecord(c->ev[1], st);
         m = mn;
     }
-    unsigned long long tv[2 * (FEM_MAX_LEN + 1)];
-    CKF(cudaMemcpyAsync(tv, touched, sizeof(tv), cudaMemcpyDeviceToHost, st));
+    // statistics and the error word in the last round trip (pinned words)
+    constexpr size_t TB = 2 * (FEM_MAX_LEN + 1) * sizeof(unsigned long long);
+    static_assert(TB + 4 <= 64 * sizeof(uint32_t), "pinned word buffer too small");
+    CKF(cudaMemcpyAsync(c->h_small, touched, TB, cudaMemcpyDeviceToHost, st));
+    CKF(cudaMemcpyAsync(c->h_small + TB / 4, c->d_err, 4, cudaMemcpyDeviceToHost, st));
     CKF(cudaStreamSynchronize(st));
+    unsigned long long tv[2 * (FEM_MAX_LEN + 1)];
+    std::memcpy(tv, c->h_small, TB);
+    const uint32_t e = c->h_small[TB / 4];
     for (fem_level_stats &ls : c->stats) {
         ls.touched_relaxed = tv[2 * ls.level];
         ls.touched_exact = tv[2 * ls.level + 1];
@@ -1228,8 +1234,6 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
         std::memcpy(res->eps[N - 1].data(), h, (size_t)f * sizeof(fem_episode));
         std::memcpy(res->counts[N - 1].data(), h + (size_t)f * sizeof(fem_episode), (size_t)f * 4);
     }
-    uint32_t e;
-    RETF(read_err(c, st, &e));
     RETF(err_status(e));
     *out = res;
     return FEM_OK;
