@@ -55,11 +55,14 @@ NCU_TRAFFIC = {
 
 
 def kernel_source_hash() -> str:
-    """SHA-256 (16 hex digits) of what the counting kernels are compiled from: their two
-    files and the device part of the internal header (up to its host launcher list)."""
+    """SHA-256 (16 hex digits) of what the counting kernels are compiled and launched
+    from: their files and the device part of the internal header (up to its host
+    launcher list)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0905_2200_gb300", "csrc")
-    for f in ("fem_count.cuh", "fem_count.cu"):
+    for f in ("fem_count.cuh", "fem_count_launch.cuh", "fem_count.cu", "fem_count_relaxed.cu",
+              "fem_count_exact.cu", "fem_count_exact_n12.cu", "fem_count_exact_n34.cu",
+              "fem_count_exact_n56.cu", "fem_count_exact_n78.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     with open(os.path.join(csrc, "fem_internal.cuh"), "rb") as fh:

@@ -204,14 +204,15 @@ uint32_t choose_segments(fem_ctx *c, const StreamDev &s, uint32_t m, bool distin
 
 // Block size by shared memory (and, for few episodes, smaller blocks), ignoring any
 // configured size.
-uint32_t auto_threads(int N, int pass, bool mc, uint32_t R, uint32_t offs, uint32_t m) {
+uint32_t auto_threads(int N, int pass, bool mc, uint32_t R, uint32_t offs, uint32_t m,
+                      uint32_t classes = S_MAX) {
     for (uint32_t T : {256u, 128u, 64u, 32u}) {
         if (T > 32 && m <= T / 2) continue;  // few episodes: small blocks, more of them
         if (T == 256 && N > 3) continue;  // register budget
-        if (count_smem_bytes(N, pass, mc, R, T, offs) <= 80 * 1024) return T;
+        if (count_smem_bytes(N, pass, mc, R, T, offs, classes) <= 80 * 1024) return T;
     }
     for (uint32_t T : {32u, 16u, 8u}) {
-        if (count_smem_bytes(N, pass, mc, R, T, offs) <= 220 * 1024) return T;
+        if (count_smem_bytes(N, pass, mc, R, T, offs, classes) <= 220 * 1024) return T;
     }
     return 8;
 }
@@ -435,10 +436,13 @@ int count_finish(fem_ctx *c, const StreamDev &s, const PassLaunch &pl, uint32_t 
         RET(dbuf(c, "redo2", r, &q.redo));
         CK(cudaMemsetAsync(q.redo, 0, r, st));
         const uint32_t Rq = pass == FEM_PASS_EXACT ? tr.R : 1;
+        // the segmented recount has twice the entry-class slots (episodes come here
+        // when a window held more classes than a table could)
+        const uint32_t cls = tr.mc && s.n_chunks > 1 ? 2 * S_MAX : S_MAX;
         if (tr.mc && s.n_chunks > 1) {
             q.P = s.n_chunks;
             q.cps = 1;
-            RET(dbuf(c, "redo_tables", (size_t)q.P * r * S_MAX, &q.tables));
+            RET(dbuf(c, "redo_tables", (size_t)q.P * r * cls, &q.tables));
         } else {
             q.P = 1;
             q.cps = std::max<uint32_t>(s.n_chunks, 1);
@@ -447,9 +451,9 @@ int count_finish(fem_ctx *c, const StreamDev &s, const PassLaunch &pl, uint32_t 
         const bool mc2 = q.P > 1;
         // the recount's rings are larger: its block size is chosen for them, whatever
         // size is configured (or being tried) for the first count
-        const uint32_t T2 = auto_threads(N, pass, mc2, Rq, s.offs, r);
-        CK(launch_count(N, pass, mc2, Rq, T2, q, st));
-        if (mc2) CK(launch_stitch(q.tables, r, q.P, rout, q.redo, c->d_err, st));
+        const uint32_t T2 = auto_threads(N, pass, mc2, Rq, s.offs, r, cls);
+        CK(launch_count(N, pass, mc2, Rq, T2, q, st, cls));
+        if (mc2) CK(launch_stitch(q.tables, r, q.P, rout, q.redo, c->d_err, st, cls));
         RET(read_err(c, st, &e));
         RET(err_status(e));
         if (std::getenv("FEM_DEBUG"))

@@ -73,7 +73,7 @@ __device__ __forceinline__ uint64_t *stage_bars(uint8_t *smem, uint32_t SB) {
 // consumed chunk stages (it selects the stage and mbarrier phase of each chunk and
 // carries over to the block's next item).  Returns false if a bounded wait gave up;
 // the caller must then stop using the block's shared memory.
-template <int N, int PASS, bool MC, int R>
+template <int N, int PASS, bool MC, int R, int SMX = S_MAX>
 __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, uint32_t seg,
                                            uint8_t *smem, uint32_t SB, uint32_t &q) {
     constexpr int NE = EpRegs<N>::NE;
@@ -176,7 +176,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
     // last-node event c_key_s[j] of the window.  A class that completes at the same
     // event as class 0 is identical to it from then on: it is merged (its bit in
     // umask cleared, c_cnt[j] holding its count minus class 0's) and no longer updated.
-    constexpr int SC = MC ? S_MAX : 1;
+    constexpr int SC = MC ? SMX : 1;  // entry classes per table (SMX slots)
     // used: slots (>= 1) holding a class.  A class that merges into class "none"
     // before the segment starts has the same count and exit as class "none", so its
     // slot is freed: the stitch reads class "none" for any class key not listed.
@@ -379,7 +379,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
         }
     };
     auto step_lean = [&](auto kc, uint32_t tt, uint32_t gidx) {
-        constexpr int k = decltype(kc)::value;
+        [[maybe_unused]] constexpr int k = decltype(kc)::value;
         auto done_lean = [&]() {
             if constexpr (MC) {
                 c_start[0] = gidx + 1, ++c_cnt[0], c0_done = true;
@@ -803,10 +803,10 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
     } else {
         // slots 0 .. n-1 are written (n = 1 + the highest used slot, in slot 0's w);
         // the stitch reads no further
-        uint4 *tab = p.tables + ((uint64_t)seg * p.m + ci) * S_MAX;
+        uint4 *tab = p.tables + ((uint64_t)seg * p.m + ci) * SMX;
         const uint32_t n_slots = used ? 32u - __clz(used) : 1u;
 #pragma unroll
-        for (int q = 0; q < S_MAX; ++q) {
+        for (int q = 0; q < SMX; ++q) {
             if ((uint32_t)q >= n_slots) break;
             uint4 e = make_uint4(CLS_EMPTY, 0, CLS_NONE, q == 0 ? n_slots : 0u);
             if (ok && (q == 0 || ((used >> q) & 1u))) {
@@ -841,28 +841,30 @@ __device__ __forceinline__ void init_stage_bars(uint8_t *smem, uint32_t SB) {
 // three blocks per SM for the exact pass with two nodes; and one block's worth for
 // longer episodes, whose class tables and lists otherwise land in local memory
 // (level-5 relaxed on the 11.8M-event stream: 170 -> 71 ms).
-template <int N, int PASS, bool MC, int R>
+template <int N, int PASS, bool MC, int R, int SMX>
 __device__ __forceinline__ void count_block(const CountParams &p) {
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t SB = stage_bytes(p.offs);
     init_stage_bars(smem, SB);
     uint32_t q = 0;
-    count_item<N, PASS, MC, R>(p, blockIdx.x, blockIdx.y, smem, SB, q);
+    count_item<N, PASS, MC, R, SMX>(p, blockIdx.x, blockIdx.y, smem, SB, q);
 }
 
-template <int N, int PASS, bool MC, int R>
+// SMX: entry-class slots per transfer table (more for the recount of episodes whose
+// first count ran out of slots)
+template <int N, int PASS, bool MC, int R, int SMX>
 __global__ void __launch_bounds__(256) k_count(const CountParams p) {
-    count_block<N, PASS, MC, R>(p);
+    count_block<N, PASS, MC, R, SMX>(p);
 }
 
-template <int N, int PASS, bool MC, int R>
+template <int N, int PASS, bool MC, int R, int SMX>
 __global__ void __launch_bounds__(256, 3) k_count_exact(const CountParams p) {
-    count_block<N, PASS, MC, R>(p);
+    count_block<N, PASS, MC, R, SMX>(p);
 }
 
-template <int N, int PASS, bool MC, int R>
+template <int N, int PASS, bool MC, int R, int SMX>
 __global__ void __launch_bounds__(256, 1) k_count_wide(const CountParams p) {
-    count_block<N, PASS, MC, R>(p);
+    count_block<N, PASS, MC, R, SMX>(p);
 }
 
 // Persistent form for a batch of candidate sets over several streams: each block
@@ -919,11 +921,11 @@ template <int N, int PASS>
 constexpr int count_budget() {  // 0: compiler default, 3: three blocks per SM, 1: one
     return PASS == FEM_PASS_EXACT ? (N <= 2 ? 3 : 1) : (N <= 3 ? 0 : 1);
 }
-template <int N, int PASS, bool MC, int R>
+template <int N, int PASS, bool MC, int R, int SMX = S_MAX>
 constexpr auto count_kernel() {
-    if constexpr (count_budget<N, PASS>() == 3) return k_count_exact<N, PASS, MC, R>;
-    else if constexpr (count_budget<N, PASS>() == 1) return k_count_wide<N, PASS, MC, R>;
-    else return k_count<N, PASS, MC, R>;
+    if constexpr (count_budget<N, PASS>() == 3) return k_count_exact<N, PASS, MC, R, SMX>;
+    else if constexpr (count_budget<N, PASS>() == 1) return k_count_wide<N, PASS, MC, R, SMX>;
+    else return k_count<N, PASS, MC, R, SMX>;
 }
 template <int N, int PASS, bool MC, int R>
 constexpr auto count_batch_kernel() {

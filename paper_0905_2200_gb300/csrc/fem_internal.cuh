@@ -180,10 +180,12 @@ cudaError_t launch_scatter_dev(const uint32_t *src, const uint32_t *idx, const u
 int fem_ctx_device(const fem_ctx *c);
 int fem_ctx_sms(const fem_ctx *c);
 // fem_count.cu
+// classes: entry-class slots per transfer table (S_MAX; 2 S_MAX for the segmented recount,
+// relaxed or exact with ring_cap 32)
 cudaError_t launch_count(int N, int pass, bool mc, uint32_t ring_cap, uint32_t threads,
-                         const CountParams &p, cudaStream_t st);
+                         const CountParams &p, cudaStream_t st, uint32_t classes = S_MAX);
 size_t count_smem_bytes(int N, int pass, bool mc, uint32_t ring_cap, uint32_t threads,
-                        uint32_t offs);
+                        uint32_t offs, uint32_t classes = S_MAX);
 bool count_config_supported(int N, int pass, bool mc, uint32_t ring_cap);
 // persistent batched counting (segmented form for every job; ring_cap 8/16/32 for exact)
 cudaError_t launch_count_batch(int N, int pass, uint32_t ring_cap, uint32_t threads,
@@ -216,7 +218,8 @@ cudaError_t launch_literal(const LiteralParams &p, uint32_t len_mask, uint32_t *
 cudaError_t launch_stitch_batch(const CountParams *jobs, const uint32_t *job_base,
                                 uint32_t n_jobs, uint32_t slots, uint32_t *err, cudaStream_t st);
 cudaError_t launch_stitch(const uint4 *tables, uint32_t m, uint32_t P, uint32_t *out,
-                          uint8_t *redo, uint32_t *err, cudaStream_t st);
+                          uint8_t *redo, uint32_t *err, cudaStream_t st,
+                          uint32_t classes = S_MAX);
 // info[0] |= 1 << len of every candidate; info[1] += candidates with a repeated type
 cudaError_t launch_validate_cands(const fem_episode *c, const uint32_t *gather, uint32_t m,
                                   uint32_t K, uint32_t n_ivl, uint32_t *info, uint32_t *err,

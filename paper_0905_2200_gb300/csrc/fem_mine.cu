@@ -69,23 +69,24 @@ __device__ __forceinline__ bool keep_at(const uint32_t *vals, const uint8_t *fla
 // run of segments (for every entry class of the run's first segment); the 32
 // partial functions are then composed pairwise in log2(32) shuffle rounds, the
 // tree of Concatenate steps; lane 0 evaluates the result at class "none".
+template <int SMX>
 __device__ void stitch_one(const uint4 *__restrict__ tables, uint32_t m, uint32_t P, uint32_t ci,
                            uint32_t *__restrict__ out, uint8_t *__restrict__ redo, uint32_t *err) {
     const uint32_t lane = threadIdx.x & 31;
     if (redo[ci]) return;  // the host recounts this episode
     const uint32_t a = (uint32_t)(((uint64_t)P * lane) >> 5);
     const uint32_t b = (uint32_t)(((uint64_t)P * (lane + 1)) >> 5);
-    uint32_t fk[S_MAX], fc[S_MAX], fe[S_MAX];
+    uint32_t fk[SMX], fc[SMX], fe[SMX];
     bool ident = a == b, bad = false;
 #pragma unroll
-    for (int j = 0; j < S_MAX; ++j) fk[j] = CLS_EMPTY, fc[j] = 0, fe[j] = CLS_NONE;
+    for (int j = 0; j < SMX; ++j) fk[j] = CLS_EMPTY, fc[j] = 0, fe[j] = CLS_NONE;
     // a table's slot 0 holds, in w, how many slots the counter wrote; the rest are empty
     auto load_table = [&](const uint4 *t, uint32_t *k, uint32_t *cnt, uint32_t *ex) {
         const uint4 e0 = t[0];
         const uint32_t n = e0.w;
         k[0] = e0.x, cnt[0] = e0.y, ex[0] = e0.z;
 #pragma unroll
-        for (int j = 1; j < S_MAX; ++j) {
+        for (int j = 1; j < SMX; ++j) {
             k[j] = CLS_EMPTY, cnt[j] = 0, ex[j] = CLS_NONE;
             if ((uint32_t)j < n) {
                 const uint4 e = t[j];
@@ -94,18 +95,18 @@ __device__ void stitch_one(const uint4 *__restrict__ tables, uint32_t m, uint32_
         }
     };
     if (!ident) {
-        load_table(tables + ((uint64_t)a * m + ci) * S_MAX, fk, fc, fe);
+        load_table(tables + ((uint64_t)a * m + ci) * SMX, fk, fc, fe);
         for (uint32_t q = a + 1; q < b; ++q) {
-            uint32_t gk[S_MAX], gc[S_MAX], ge[S_MAX];
-            load_table(tables + ((uint64_t)q * m + ci) * S_MAX, gk, gc, ge);
+            uint32_t gk[SMX], gc[SMX], ge[SMX];
+            load_table(tables + ((uint64_t)q * m + ci) * SMX, gk, gc, ge);
 #pragma unroll
-            for (int j = 0; j < S_MAX; ++j) {
+            for (int j = 0; j < SMX; ++j) {
                 if (fk[j] == CLS_EMPTY) continue;
                 // a class key without its own entry behaves as class "none"
                 bool hit = false, hitn = false;
                 uint32_t nc = 0, ne = CLS_NONE, ncn = 0, nen = CLS_NONE;
 #pragma unroll
-                for (int i = 0; i < S_MAX; ++i) {
+                for (int i = 0; i < SMX; ++i) {
                     if (!hit && gk[i] == fe[j]) hit = true, nc = gc[i], ne = ge[i];
                     if (!hitn && gk[i] == CLS_NONE) hitn = true, ncn = gc[i], nen = ge[i];
                 }
@@ -117,9 +118,9 @@ __device__ void stitch_one(const uint4 *__restrict__ tables, uint32_t m, uint32_
     }
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        uint32_t pk[S_MAX], pc[S_MAX], pe[S_MAX];
+        uint32_t pk[SMX], pc[SMX], pe[SMX];
 #pragma unroll
-        for (int i = 0; i < S_MAX; ++i) {
+        for (int i = 0; i < SMX; ++i) {
             pk[i] = __shfl_down_sync(0xffffffffu, fk[i], d);
             pc[i] = __shfl_down_sync(0xffffffffu, fc[i], d);
             pe[i] = __shfl_down_sync(0xffffffffu, fe[i], d);
@@ -128,16 +129,16 @@ __device__ void stitch_one(const uint4 *__restrict__ tables, uint32_t m, uint32_
         if ((lane & (2 * d - 1)) == 0 && lane + d < 32 && !pident) {
             if (ident) {
 #pragma unroll
-                for (int i = 0; i < S_MAX; ++i) fk[i] = pk[i], fc[i] = pc[i], fe[i] = pe[i];
+                for (int i = 0; i < SMX; ++i) fk[i] = pk[i], fc[i] = pc[i], fe[i] = pe[i];
                 ident = false;
             } else {
 #pragma unroll
-                for (int j = 0; j < S_MAX; ++j) {
+                for (int j = 0; j < SMX; ++j) {
                     if (fk[j] == CLS_EMPTY) continue;
                     bool hit = false, hitn = false;
                     uint32_t nc = 0, ne = CLS_NONE, ncn = 0, nen = CLS_NONE;
 #pragma unroll
-                    for (int i = 0; i < S_MAX; ++i) {
+                    for (int i = 0; i < SMX; ++i) {
                         if (!hit && pk[i] == fe[j]) hit = true, nc = pc[i], ne = pe[i];
                         if (!hitn && pk[i] == CLS_NONE) hitn = true, ncn = pc[i], nen = pe[i];
                     }
@@ -153,7 +154,7 @@ __device__ void stitch_one(const uint4 *__restrict__ tables, uint32_t m, uint32_
         bool found = false;
         uint32_t total = 0;
 #pragma unroll
-        for (int j = 0; j < S_MAX; ++j)
+        for (int j = 0; j < SMX; ++j)
             if (!found && fk[j] == CLS_NONE) found = true, total = fc[j];
         if (bad || !found) {
             redo[ci] = 1;
@@ -164,11 +165,12 @@ __device__ void stitch_one(const uint4 *__restrict__ tables, uint32_t m, uint32_
     }
 }
 
+template <int SMX>
 __global__ void __launch_bounds__(256) k_stitch(const uint4 *__restrict__ tables, uint32_t m,
                                                 uint32_t P, uint32_t *__restrict__ out,
                                                 uint8_t *__restrict__ redo, uint32_t *err) {
     const uint32_t ci = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (ci < m) stitch_one(tables, m, P, ci, out, redo, err);
+    if (ci < m) stitch_one<SMX>(tables, m, P, ci, out, redo, err);
 }
 
 // One warp per episode slot of a batch of jobs (each job its own tables and outputs).
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(256) k_stitch_batch(const CountParams *__restr
     }
     const CountParams &p = jobs[lo];
     const uint32_t ci = e - job_base[lo];
-    if (ci < p.m && p.P > 0) stitch_one(p.tables, p.m, p.P, ci, p.out, p.redo, err);
+    if (ci < p.m && p.P > 0) stitch_one<S_MAX>(p.tables, p.m, p.P, ci, p.out, p.redo, err);
 }
 
 cudaError_t launch_stitch_batch(const CountParams *jobs, const uint32_t *job_base,
@@ -199,10 +201,15 @@ cudaError_t launch_stitch_batch(const CountParams *jobs, const uint32_t *job_bas
 }
 
 cudaError_t launch_stitch(const uint4 *tables, uint32_t m, uint32_t P, uint32_t *out,
-                          uint8_t *redo, uint32_t *err, cudaStream_t st) {
+                          uint8_t *redo, uint32_t *err, cudaStream_t st, uint32_t classes) {
     if (m == 0) return cudaSuccess;
     const uint32_t blocks = (uint32_t)(((uint64_t)m * 32 + 255) / 256);
-    k_stitch<<<blocks, 256, 0, st>>>(tables, m, P, out, redo, err);
+    if (classes == 2 * S_MAX)
+        k_stitch<2 * S_MAX><<<blocks, 256, 0, st>>>(tables, m, P, out, redo, err);
+    else if (classes == S_MAX)
+        k_stitch<S_MAX><<<blocks, 256, 0, st>>>(tables, m, P, out, redo, err);
+    else
+        return cudaErrorInvalidValue;
     note_launch();
     return cudaGetLastError();
 }
