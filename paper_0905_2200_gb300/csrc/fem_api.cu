@@ -436,9 +436,9 @@ int count_finish(fem_ctx *c, const StreamDev &s, const PassLaunch &pl, uint32_t 
         RET(dbuf(c, "redo2", r, &q.redo));
         CK(cudaMemsetAsync(q.redo, 0, r, st));
         const uint32_t Rq = pass == FEM_PASS_EXACT ? tr.R : 1;
-        // the segmented recount has twice the entry-class slots (episodes come here
-        // when a window held more classes than a table could)
-        const uint32_t cls = tr.mc && s.n_chunks > 1 ? 2 * S_MAX : S_MAX;
+        // the segmented recount has four times the entry-class slots (episodes come
+        // here when a window held more classes than a table could)
+        const uint32_t cls = tr.mc && s.n_chunks > 1 ? S_RECOUNT : S_MAX;
         if (tr.mc && s.n_chunks > 1) {
             q.P = s.n_chunks;
             q.cps = 1;

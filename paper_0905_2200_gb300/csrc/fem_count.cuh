@@ -629,7 +629,8 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                         c_start[0] != gidx + 1) {
                         // entry class r = gidx (the serial machine's last completion was r);
                         // when class "none" completed at r too, it is that class: no slot
-                        const uint32_t free_slots = ~used & (((1u << SC) - 1u) & ~1u);
+                        constexpr uint32_t all_slots = SC >= 32 ? 0xFFFFFFFFu : (1u << SC) - 1u;
+                        const uint32_t free_slots = ~used & (all_slots & ~1u);
                         if (free_slots) {
                             const int q0 = __ffs(free_slots) - 1;
                             set_key(q0, gidx);
@@ -923,7 +924,8 @@ constexpr int count_budget() {  // 0: compiler default, 3: three blocks per SM, 
 }
 template <int N, int PASS, bool MC, int R, int SMX = S_MAX>
 constexpr auto count_kernel() {
-    if constexpr (count_budget<N, PASS>() == 3) return k_count_exact<N, PASS, MC, R, SMX>;
+    if constexpr (SMX > S_MAX) return k_count_wide<N, PASS, MC, R, SMX>;  // recount tables
+    else if constexpr (count_budget<N, PASS>() == 3) return k_count_exact<N, PASS, MC, R, SMX>;
     else if constexpr (count_budget<N, PASS>() == 1) return k_count_wide<N, PASS, MC, R, SMX>;
     else return k_count<N, PASS, MC, R, SMX>;
 }

@@ -83,10 +83,10 @@ cudaError_t run(const CountParams &p, uint32_t threads, cudaStream_t st) {
 template <int N, int PASS, bool MC>
 cudaError_t run_r(uint32_t R, const CountParams &p, uint32_t threads, cudaStream_t st,
                   uint32_t classes) {
-    if (classes == 2 * S_MAX) {
+    if (classes == S_RECOUNT) {
         if constexpr (MC) {
-            if constexpr (PASS == FEM_PASS_RELAXED) return run<N, PASS, MC, 1, 2 * S_MAX>(p, threads, st);
-            else if (R == 32) return run<N, PASS, MC, 32, 2 * S_MAX>(p, threads, st);
+            if constexpr (PASS == FEM_PASS_RELAXED) return run<N, PASS, MC, 1, S_RECOUNT>(p, threads, st);
+            else if (R == 32) return run<N, PASS, MC, 32, S_RECOUNT>(p, threads, st);
         }
         return cudaErrorInvalidValue;
     }

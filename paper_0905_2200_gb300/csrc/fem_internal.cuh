@@ -25,6 +25,7 @@ constexpr uint32_t KEY_END = 0xFFFFFFFFu;   // "list exhausted"
 constexpr uint32_t CLS_NONE = 0xFFFFFFFFu;  // MapConcatenate class "no recent completion"
 constexpr uint32_t CLS_EMPTY = 0xFFFFFFFEu; // unused transfer-table slot
 constexpr int S_MAX = 8;                    // MapConcatenate entry classes per table
+constexpr int S_RECOUNT = 32;               // the same, in the segmented recount
 
 // device error word bits
 constexpr uint32_t ERR_TIMEOUT = 1u;       // a bounded mbarrier wait gave up

@@ -204,8 +204,8 @@ cudaError_t launch_stitch(const uint4 *tables, uint32_t m, uint32_t P, uint32_t 
                           uint8_t *redo, uint32_t *err, cudaStream_t st, uint32_t classes) {
     if (m == 0) return cudaSuccess;
     const uint32_t blocks = (uint32_t)(((uint64_t)m * 32 + 255) / 256);
-    if (classes == 2 * S_MAX)
-        k_stitch<2 * S_MAX><<<blocks, 256, 0, st>>>(tables, m, P, out, redo, err);
+    if (classes == S_RECOUNT)
+        k_stitch<S_RECOUNT><<<blocks, 256, 0, st>>>(tables, m, P, out, redo, err);
     else if (classes == S_MAX)
         k_stitch<S_MAX><<<blocks, 256, 0, st>>>(tables, m, P, out, redo, err);
     else
