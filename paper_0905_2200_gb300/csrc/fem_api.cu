@@ -1139,7 +1139,7 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
         fem_level_stats ls{};
         ls.level = N;
         ls.candidates = m;
-        uint32_t *rel, *idx_s, *ex, *idx_f, *fidx, *fcnt, *scratch;
+        uint32_t *rel, *idx_s, *ex, *idx_f, *fcnt, *scratch;
         fem_episode *F;
         RETF(dbuf(c, "rel", m, &rel));
         RETF(dbuf(c, "idx_s", m, &idx_s));
@@ -1188,12 +1188,9 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
         ls.frequent = f;
         c->stats.push_back(ls);
         if (f == 0) break;
-        RETF(dbuf(c, "fidx", f, &fidx));
         RETF(dbuf(c, "fcnt", f, &fcnt));
         RETF(dbuf(c, "F", f, &F));
-        CKF(launch_compose_idx(idx_s, idx_f, f, fidx, st));
-        CKF(launch_gather_episodes(cands, fidx, f, F, nullptr, nullptr, st));
-        CKF(launch_gather_episodes(nullptr, idx_f, f, nullptr, ex, fcnt, st));
+        CKF(launch_gather_frequent(cands, idx_s, idx_f, f, ex, F, fcnt, st));
         void *h;
         RETF(pinbuf(c, N, (size_t)f * (sizeof(fem_episode) + 4), st, &h));
         CKF(cudaMemcpyAsync(h, F, (size_t)f * sizeof(fem_episode), cudaMemcpyDeviceToHost, st));
@@ -1206,13 +1203,13 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
         RETF(dbuf(c, "jc", f, &jc));
         RETF(dbuf(c, "joff", f, &joff));
         cudaEventRecord(c->ev[0], st);
-        CKF(launch_join_count(F, f, N, repeats, jc, st));
+        CKF(launch_join_count(F, f, N, repeats, jc, c->sm_count, st));
         CKF(launch_exclusive_scan(jc, f, joff, c->d_small + W_COUNT2, scratch, st));
         uint32_t mn;
         RETF(read_words(c, c->d_small + W_COUNT2, 1, &mn, st));
         cur ^= 1;
         RETF(dbuf(c, cname[cur], std::max<uint32_t>(mn, 1), &cands));
-        CKF(launch_join_emit(F, f, N, repeats, joff, cands, st));
+        CKF(launch_join_emit(F, f, N, repeats, joff, cands, c->sm_count, st));
         cudaEventRecord(c->ev[1], st);
         m = mn;
     }

@@ -237,6 +237,9 @@ cudaError_t launch_compact(const uint32_t *vals, const uint8_t *flags, uint32_t 
                            uint32_t *idx_out, uint32_t *count_out, uint32_t *block_scratch,
                            cudaStream_t st);
 size_t compact_scratch_words(uint32_t m);
+cudaError_t launch_gather_frequent(const fem_episode *cands, const uint32_t *surv,
+                                   const uint32_t *idx, uint32_t f, const uint32_t *counts,
+                                   fem_episode *F, uint32_t *fcnt, cudaStream_t st);
 cudaError_t launch_gather_episodes(const fem_episode *src, const uint32_t *idx, uint32_t m,
                                    fem_episode *dst, const uint32_t *vals, uint32_t *vals_dst,
                                    cudaStream_t st);
@@ -246,11 +249,11 @@ cudaError_t launch_fill_flags(const uint32_t *idx, uint32_t m, uint8_t *flags, c
 cudaError_t launch_level2(const uint32_t *ftypes, uint32_t f, uint32_t n_ivl, bool repeats,
                           fem_episode *out, cudaStream_t st);
 cudaError_t launch_join_count(const fem_episode *F, uint32_t f, uint32_t N, bool repeats,
-                              uint32_t *cnt, cudaStream_t st);
+                              uint32_t *cnt, int sm_count, cudaStream_t st);
 cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t m, uint32_t *out,
                                   uint32_t *total, uint32_t *scratch, cudaStream_t st);
 cudaError_t launch_join_emit(const fem_episode *F, uint32_t f, uint32_t N, bool repeats,
-                             const uint32_t *off, fem_episode *out, cudaStream_t st);
+                             const uint32_t *off, fem_episode *out, int sm_count, cudaStream_t st);
 cudaError_t launch_repeat_flags(const fem_episode *c, const uint32_t *gather, uint32_t m, bool invert,
                                 uint8_t *flags, cudaStream_t st);
 // fem_batch.cu

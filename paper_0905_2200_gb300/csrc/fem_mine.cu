@@ -3,6 +3,8 @@
 // and level-wise candidate generation.
 #include <string.h>
 
+#include <algorithm>
+
 #include "fem_internal.cuh"
 
 namespace fem {
@@ -65,28 +67,25 @@ __device__ __forceinline__ bool keep_at(const uint32_t *vals, const uint8_t *fla
 }  // namespace
 
 // ------------------------------------------------------------------ MapConcatenate stitch
-// One warp per episode.  Lane l composes the transfer tables of its contiguous
-// run of segments (for every entry class of the run's first segment); the 32
-// partial functions are then composed pairwise in log2(32) shuffle rounds, the
-// tree of Concatenate steps; lane 0 evaluates the result at class "none".
-template <int SMX>
-__device__ void stitch_one(const uint4 *__restrict__ tables, uint32_t m, uint32_t P, uint32_t ci,
-                           uint32_t *__restrict__ out, uint8_t *__restrict__ redo, uint32_t *err) {
+// stitch_run<SMX, SU>: the composition with tables of SMX slots (the layout) of which
+// at most SU can hold a class anywhere in the warp's tables; every loop is unrolled
+// and branch-free over SU slots.
+template <int SMX, int SU>
+__device__ __forceinline__ void stitch_run(const uint4 *__restrict__ tables, uint32_t m, uint32_t a,
+                                           uint32_t b, uint32_t ci, uint32_t *__restrict__ out,
+                                           uint8_t *__restrict__ redo, uint32_t *err) {
     const uint32_t lane = threadIdx.x & 31;
-    if (redo[ci]) return;  // the host recounts this episode
-    const uint32_t a = (uint32_t)(((uint64_t)P * lane) >> 5);
-    const uint32_t b = (uint32_t)(((uint64_t)P * (lane + 1)) >> 5);
-    uint32_t fk[SMX], fc[SMX], fe[SMX];
+    uint32_t fk[SU], fc[SU], fe[SU];
     bool ident = a == b, bad = false;
 #pragma unroll
-    for (int j = 0; j < SMX; ++j) fk[j] = CLS_EMPTY, fc[j] = 0, fe[j] = CLS_NONE;
+    for (int j = 0; j < SU; ++j) fk[j] = CLS_EMPTY, fc[j] = 0, fe[j] = CLS_NONE;
     // a table's slot 0 holds, in w, how many slots the counter wrote; the rest are empty
     auto load_table = [&](const uint4 *t, uint32_t *k, uint32_t *cnt, uint32_t *ex) {
         const uint4 e0 = t[0];
         const uint32_t n = e0.w;
         k[0] = e0.x, cnt[0] = e0.y, ex[0] = e0.z;
 #pragma unroll
-        for (int j = 1; j < SMX; ++j) {
+        for (int j = 1; j < SU; ++j) {
             k[j] = CLS_EMPTY, cnt[j] = 0, ex[j] = CLS_NONE;
             if ((uint32_t)j < n) {
                 const uint4 e = t[j];
@@ -94,33 +93,37 @@ __device__ void stitch_one(const uint4 *__restrict__ tables, uint32_t m, uint32_
             }
         }
     };
+    // f := f followed by g: each class of f goes on through g's row for f's exit; a
+    // key without its own row behaves as class "none"
+    auto compose = [&](const uint32_t *gk, const uint32_t *gc, const uint32_t *ge) {
+#pragma unroll
+        for (int j = 0; j < SU; ++j) {
+            if (fk[j] == CLS_EMPTY) continue;
+            bool hit = false, hitn = false;
+            uint32_t nc = 0, ne = CLS_NONE, ncn = 0, nen = CLS_NONE;
+#pragma unroll
+            for (int i = 0; i < SU; ++i) {
+                if (!hit && gk[i] == fe[j]) hit = true, nc = gc[i], ne = ge[i];
+                if (!hitn && gk[i] == CLS_NONE) hitn = true, ncn = gc[i], nen = ge[i];
+            }
+            if (!hit && !hitn) bad = true;
+            fc[j] += hit ? nc : ncn;
+            fe[j] = hit ? ne : nen;
+        }
+    };
     if (!ident) {
         load_table(tables + ((uint64_t)a * m + ci) * SMX, fk, fc, fe);
         for (uint32_t q = a + 1; q < b; ++q) {
-            uint32_t gk[SMX], gc[SMX], ge[SMX];
+            uint32_t gk[SU], gc[SU], ge[SU];
             load_table(tables + ((uint64_t)q * m + ci) * SMX, gk, gc, ge);
-#pragma unroll
-            for (int j = 0; j < SMX; ++j) {
-                if (fk[j] == CLS_EMPTY) continue;
-                // a class key without its own entry behaves as class "none"
-                bool hit = false, hitn = false;
-                uint32_t nc = 0, ne = CLS_NONE, ncn = 0, nen = CLS_NONE;
-#pragma unroll
-                for (int i = 0; i < SMX; ++i) {
-                    if (!hit && gk[i] == fe[j]) hit = true, nc = gc[i], ne = ge[i];
-                    if (!hitn && gk[i] == CLS_NONE) hitn = true, ncn = gc[i], nen = ge[i];
-                }
-                if (!hit && !hitn) bad = true;
-                fc[j] += hit ? nc : ncn;
-                fe[j] = hit ? ne : nen;
-            }
+            compose(gk, gc, ge);
         }
     }
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        uint32_t pk[SMX], pc[SMX], pe[SMX];
+        uint32_t pk[SU], pc[SU], pe[SU];
 #pragma unroll
-        for (int i = 0; i < SMX; ++i) {
+        for (int i = 0; i < SU; ++i) {
             pk[i] = __shfl_down_sync(0xffffffffu, fk[i], d);
             pc[i] = __shfl_down_sync(0xffffffffu, fc[i], d);
             pe[i] = __shfl_down_sync(0xffffffffu, fe[i], d);
@@ -129,23 +132,10 @@ __device__ void stitch_one(const uint4 *__restrict__ tables, uint32_t m, uint32_
         if ((lane & (2 * d - 1)) == 0 && lane + d < 32 && !pident) {
             if (ident) {
 #pragma unroll
-                for (int i = 0; i < SMX; ++i) fk[i] = pk[i], fc[i] = pc[i], fe[i] = pe[i];
+                for (int i = 0; i < SU; ++i) fk[i] = pk[i], fc[i] = pc[i], fe[i] = pe[i];
                 ident = false;
             } else {
-#pragma unroll
-                for (int j = 0; j < SMX; ++j) {
-                    if (fk[j] == CLS_EMPTY) continue;
-                    bool hit = false, hitn = false;
-                    uint32_t nc = 0, ne = CLS_NONE, ncn = 0, nen = CLS_NONE;
-#pragma unroll
-                    for (int i = 0; i < SMX; ++i) {
-                        if (!hit && pk[i] == fe[j]) hit = true, nc = pc[i], ne = pe[i];
-                        if (!hitn && pk[i] == CLS_NONE) hitn = true, ncn = pc[i], nen = pe[i];
-                    }
-                    if (!hit && !hitn) bad = true;
-                    fc[j] += hit ? nc : ncn;
-                    fe[j] = hit ? ne : nen;
-                }
+                compose(pk, pc, pe);
             }
         }
     }
@@ -154,7 +144,7 @@ __device__ void stitch_one(const uint4 *__restrict__ tables, uint32_t m, uint32_
         bool found = false;
         uint32_t total = 0;
 #pragma unroll
-        for (int j = 0; j < SMX; ++j)
+        for (int j = 0; j < SU; ++j)
             if (!found && fk[j] == CLS_NONE) found = true, total = fc[j];
         if (bad || !found) {
             redo[ci] = 1;
@@ -163,6 +153,35 @@ __device__ void stitch_one(const uint4 *__restrict__ tables, uint32_t m, uint32_
             out[ci] = total;
         }
     }
+}
+
+// One warp per episode.  Lane l composes the transfer tables of its contiguous
+// run of segments (for every entry class of the run's first segment); the 32
+// partial functions are then composed pairwise in log2(32) shuffle rounds, the
+// tree of Concatenate steps; lane 0 evaluates the result at class "none".
+// Most tables hold one or two classes: the warp first reads how many slots its
+// tables use and composes over that many only (1, 2, 4, 8 or all), a choice the
+// same on every lane, so the composition stays unrolled and free of branches.
+template <int SMX>
+__device__ void stitch_one(const uint4 *__restrict__ tables, uint32_t m, uint32_t P, uint32_t ci,
+                           uint32_t *__restrict__ out, uint8_t *__restrict__ redo, uint32_t *err) {
+    const uint32_t lane = threadIdx.x & 31;
+    if (redo[ci]) return;  // the host recounts this episode
+    const uint32_t a = (uint32_t)(((uint64_t)P * lane) >> 5);
+    const uint32_t b = (uint32_t)(((uint64_t)P * (lane + 1)) >> 5);
+    uint32_t n = 1;
+    for (uint32_t q = a; q < b; ++q) n = max(n, tables[((uint64_t)q * m + ci) * SMX].w);
+    n = __reduce_max_sync(0xffffffffu, n);
+    if (n <= 1)
+        stitch_run<SMX, 1>(tables, m, a, b, ci, out, redo, err);
+    else if (n <= 2)
+        stitch_run<SMX, 2>(tables, m, a, b, ci, out, redo, err);
+    else if (n <= 4)
+        stitch_run<SMX, (SMX < 4 ? SMX : 4)>(tables, m, a, b, ci, out, redo, err);
+    else if (SMX > 8 && n <= 8)
+        stitch_run<SMX, (SMX < 8 ? SMX : 8)>(tables, m, a, b, ci, out, redo, err);
+    else
+        stitch_run<SMX, SMX>(tables, m, a, b, ci, out, redo, err);
 }
 
 template <int SMX>
@@ -341,10 +360,67 @@ __global__ void __launch_bounds__(CT) k_keep_scatter(const uint32_t *vals, const
         if (kp[k]) idx[pos++] = base + k;
 }
 
+// Up to ST * SI items (the candidate sets of most levels) are compacted or scanned
+// by one block of ST threads, each on a contiguous run of SI items: one launch
+// instead of three, which matters in the stretches between host waits, where the
+// host issues short kernels one after another.
+constexpr uint32_t ST = 1024, SI = 16;
+static_assert(SI == 16, "k_compact_small takes half a keep-bit word per thread");
+
+__global__ void __launch_bounds__(ST) k_compact_small(const uint32_t *vals, const uint8_t *flags,
+                                                      uint32_t theta, uint32_t m, uint32_t *idx,
+                                                      uint32_t *count) {
+    // keep bits, one word per 32 items, from coalesced reads (item r * ST + thread)
+    __shared__ uint32_t keep_bits[ST * SI / 32];
+    const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+    for (uint32_t r = 0; r < SI; ++r) {
+        const uint32_t i = r * ST + threadIdx.x;
+        const uint32_t w = __ballot_sync(0xffffffffu, i < m && keep_at(vals, flags, theta, i));
+        if (lane == 0) keep_bits[i >> 5] = w;
+    }
+    __syncthreads();
+    // thread t then owns items t * SI .. t * SI + SI - 1 (SI = 16: half a word)
+    const uint32_t base = threadIdx.x * SI;
+    uint32_t bits = (keep_bits[base >> 5] >> (base & 31u)) & 0xFFFFu;
+    uint32_t tot;
+    uint32_t pos = block_exclusive_scan(__popc(bits), &tot);
+    while (bits) {
+        const uint32_t k = __ffs(bits) - 1;
+        bits &= bits - 1;
+        idx[pos++] = base + k;
+    }
+    if (threadIdx.x == 0) *count = tot;
+}
+
+__global__ void __launch_bounds__(ST) k_scan_one_block(const uint32_t *in, uint32_t m,
+                                                       uint32_t *out, uint32_t *total) {
+    const uint32_t base = threadIdx.x * SI;
+    uint32_t v[SI], c = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < SI; ++k) {
+        v[k] = base + k < m ? in[base + k] : 0u;
+        c += v[k];
+    }
+    uint32_t tot;
+    uint32_t pos = block_exclusive_scan(c, &tot);
+#pragma unroll
+    for (uint32_t k = 0; k < SI; ++k) {
+        if (base + k < m) out[base + k] = pos;
+        pos += v[k];
+    }
+    if (threadIdx.x == 0 && total) *total = tot;
+}
+
 cudaError_t launch_compact(const uint32_t *vals, const uint8_t *flags, uint32_t theta, uint32_t m,
                            uint32_t *idx_out, uint32_t *count_out, uint32_t *scratch,
                            cudaStream_t st) {
     if (m == 0) return cudaMemsetAsync(count_out, 0, sizeof(uint32_t), st);
+    if (m <= ST * SI) {
+        k_compact_small<<<1, ST, 0, st>>>(vals, flags, theta, m, idx_out, count_out);
+        note_launch();
+        return cudaGetLastError();
+    }
     const uint32_t nb = (m + CB - 1) / CB;
     k_keep_count<<<nb, CT, 0, st>>>(vals, flags, theta, m, scratch);
     note_launch();
@@ -388,6 +464,11 @@ __global__ void __launch_bounds__(CT) k_scan_apply(const uint32_t *in, uint32_t 
 cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t m, uint32_t *out, uint32_t *total,
                                   uint32_t *scratch, cudaStream_t st) {
     if (m == 0) return cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
+    if (m <= ST * SI) {
+        k_scan_one_block<<<1, ST, 0, st>>>(in, m, out, total);
+        note_launch();
+        return cudaGetLastError();
+    }
     const uint32_t nb = (m + CB - 1) / CB;
     k_sum_blocks<<<nb, CT, 0, st>>>(in, m, scratch);
     note_launch();
@@ -414,6 +495,29 @@ cudaError_t launch_gather_episodes(const fem_episode *src, const uint32_t *idx, 
                                    cudaStream_t st) {
     if (m == 0) return cudaSuccess;
     k_gather_ep<<<(m + 255) / 256, 256, 0, st>>>(src, idx, m, dst, vals, vals_dst);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// The frequent set of a level in one launch: F[i] = cands[surv[idx[i]]] and
+// fcnt[i] = counts[idx[i]], where surv lists the survivors of the first pass and idx
+// the survivors of the second (both ascending, so F keeps the candidates' order).
+__global__ void k_gather_frequent(const fem_episode *__restrict__ cands,
+                                  const uint32_t *__restrict__ surv, const uint32_t *__restrict__ idx,
+                                  uint32_t f, const uint32_t *__restrict__ counts,
+                                  fem_episode *__restrict__ F, uint32_t *__restrict__ fcnt) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= f) return;
+    const uint32_t j = idx[i];
+    st_ep(F, i, ld_ep(cands, surv[j]));
+    fcnt[i] = counts[j];
+}
+
+cudaError_t launch_gather_frequent(const fem_episode *cands, const uint32_t *surv,
+                                   const uint32_t *idx, uint32_t f, const uint32_t *counts,
+                                   fem_episode *F, uint32_t *fcnt, cudaStream_t st) {
+    if (f == 0) return cudaSuccess;
+    k_gather_frequent<<<(f + 255) / 256, 256, 0, st>>>(cands, surv, idx, f, counts, F, fcnt);
     note_launch();
     return cudaGetLastError();
 }
@@ -603,6 +707,10 @@ __device__ __forceinline__ bool has_type(const fem_episode &a, uint32_t N, uint3
 // Up to this many frequent episodes (48 KB) are staged in each block's shared memory,
 // so the binary searches and the scans of matching ranges read no global memory.
 constexpr uint32_t JOIN_SMEM_MAX = 3072;
+// One warp per alpha: its lanes take the matching betas 32 at a time, so an alpha
+// with a long range (a type that starts many frequent episodes) does not hold up the
+// launch (level 2 -> 3 of the 64-type recording: 66 us with one thread per alpha).
+constexpr uint32_t JOIN_WARPS = 8;  // warps per block
 
 __device__ __forceinline__ const fem_episode *stage_frequent(const fem_episode *F, uint32_t f) {
     extern __shared__ uint4 s_freq[];
@@ -615,55 +723,84 @@ __device__ __forceinline__ const fem_episode *stage_frequent(const fem_episode *
 
 // The child alpha + beta's last node is kept if that type is new to alpha, or
 // always when `repeats`.
-__global__ void k_join_count(const fem_episode *__restrict__ Fg, uint32_t f, uint32_t N,
-                             uint32_t repeats, uint32_t *__restrict__ cnt) {
+__global__ void __launch_bounds__(JOIN_WARPS * 32)
+    k_join_count(const fem_episode *__restrict__ Fg, uint32_t f, uint32_t N, uint32_t repeats,
+                 uint32_t *__restrict__ cnt) {
     const fem_episode *F = stage_frequent(Fg, f);
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= f) return;
-    const fem_episode a = ld_ep(F, i);
-    uint32_t lo, hi;
-    join_range(F, f, N, a, &lo, &hi);
-    uint32_t c = 0;
-    for (uint32_t j = lo; j < hi; ++j) c += repeats || !has_type(a, N, ld_ep(F, j).types[N - 1]);
-    cnt[i] = c;
-}
-
-__global__ void k_join_emit(const fem_episode *__restrict__ Fg, uint32_t f, uint32_t N,
-                            uint32_t repeats, const uint32_t *__restrict__ off,
-                            fem_episode *__restrict__ out) {
-    const fem_episode *F = stage_frequent(Fg, f);
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= f) return;
-    const fem_episode a = ld_ep(F, i);
-    uint32_t lo, hi;
-    join_range(F, f, N, a, &lo, &hi);
-    uint32_t pos = off[i];
-    for (uint32_t j = lo; j < hi; ++j) {
-        const fem_episode b = ld_ep(F, j);
-        const uint32_t x = b.types[N - 1];
-        if (!repeats && has_type(a, N, x)) continue;
-        fem_episode c = a;
-        c.types[N] = (uint8_t)x;
-        c.ivl[N - 1] = b.ivl[N - 2];
-        c.len = (uint8_t)(N + 1);
-        st_ep(out, pos++, c);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t nw = gridDim.x * JOIN_WARPS;
+    for (uint32_t i = blockIdx.x * JOIN_WARPS + (threadIdx.x >> 5); i < f; i += nw) {
+        const fem_episode a = ld_ep(F, i);
+        uint32_t lo, hi;
+        join_range(F, f, N, a, &lo, &hi);  // the same on every lane
+        uint32_t c = 0;
+        for (uint32_t j = lo + lane; j < hi; j += 32)
+            c += repeats || !has_type(a, N, ld_ep(F, j).types[N - 1]);
+        c = __reduce_add_sync(0xFFFFFFFFu, c);
+        if (lane == 0) cnt[i] = c;
     }
 }
 
+__global__ void __launch_bounds__(JOIN_WARPS * 32)
+    k_join_emit(const fem_episode *__restrict__ Fg, uint32_t f, uint32_t N, uint32_t repeats,
+                const uint32_t *__restrict__ off, fem_episode *__restrict__ out) {
+    const fem_episode *F = stage_frequent(Fg, f);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint32_t nw = gridDim.x * JOIN_WARPS;
+    for (uint32_t i = blockIdx.x * JOIN_WARPS + (threadIdx.x >> 5); i < f; i += nw) {
+        const fem_episode a = ld_ep(F, i);
+        uint32_t lo, hi;
+        join_range(F, f, N, a, &lo, &hi);
+        uint32_t pos = off[i];
+        for (uint32_t j0 = lo; j0 < hi; j0 += 32) {  // warp-uniform trip count
+            const uint32_t j = j0 + lane;
+            bool keep = false;
+            fem_episode b;
+            if (j < hi) {
+                b = ld_ep(F, j);
+                keep = repeats || !has_type(a, N, b.types[N - 1]);
+            }
+            // kept children of this batch go out in beta order, one per lane
+            const uint32_t kept = __ballot_sync(0xFFFFFFFFu, keep);
+            if (keep) {
+                fem_episode c = a;
+                c.types[N] = b.types[N - 1];
+                c.ivl[N - 1] = b.ivl[N - 2];
+                c.len = (uint8_t)(N + 1);
+                st_ep(out, pos + __popc(kept & below), c);
+            }
+            pos += __popc(kept);
+        }
+    }
+}
+
+namespace {
+// Blocks of a join launch: one warp per alpha, at most `per_sm` blocks per SM (with F
+// staged, every block copies it once; without, more blocks hide global latency).
+uint32_t join_blocks(uint32_t f, int sm_count) {
+    const uint32_t per_sm = f <= JOIN_SMEM_MAX ? 1u : 8u;
+    const uint32_t cap = (uint32_t)std::max(sm_count, 1) * per_sm;
+    return std::max(1u, std::min((f + JOIN_WARPS - 1) / JOIN_WARPS, cap));
+}
+}  // namespace
+
 cudaError_t launch_join_count(const fem_episode *F, uint32_t f, uint32_t N, bool repeats,
-                              uint32_t *cnt, cudaStream_t st) {
+                              uint32_t *cnt, int sm_count, cudaStream_t st) {
     if (f == 0) return cudaSuccess;
     const size_t sm = f <= JOIN_SMEM_MAX ? (size_t)f * sizeof(fem_episode) : 0;
-    k_join_count<<<(f + 127) / 128, 128, sm, st>>>(F, f, N, repeats ? 1u : 0u, cnt);
+    k_join_count<<<join_blocks(f, sm_count), JOIN_WARPS * 32, sm, st>>>(F, f, N, repeats ? 1u : 0u,
+                                                                         cnt);
     note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_join_emit(const fem_episode *F, uint32_t f, uint32_t N, bool repeats,
-                             const uint32_t *off, fem_episode *out, cudaStream_t st) {
+                             const uint32_t *off, fem_episode *out, int sm_count, cudaStream_t st) {
     if (f == 0) return cudaSuccess;
     const size_t sm = f <= JOIN_SMEM_MAX ? (size_t)f * sizeof(fem_episode) : 0;
-    k_join_emit<<<(f + 127) / 128, 128, sm, st>>>(F, f, N, repeats ? 1u : 0u, off, out);
+    k_join_emit<<<join_blocks(f, sm_count), JOIN_WARPS * 32, sm, st>>>(
+        F, f, N, repeats ? 1u : 0u, off, out);
     note_launch();
     return cudaGetLastError();
 }

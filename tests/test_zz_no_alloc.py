@@ -60,3 +60,23 @@ def test_select_noalloc_rejects_oversize_request():
     p = ctypes.c_void_p(buf.data_ptr())
     rc = lib.fem_select_noalloc(p, (1 << 26) + 1, 0, p, p, None)
     assert rc == -1
+
+
+@pytest.mark.parametrize("m", [1, 1000, 16383, 16384, 16385, 70001])
+def test_select_noalloc_sizes_match_numpy(m):
+    """Both compaction forms (one block up to 16,384 values, three launches above) keep
+    exactly the values >= theta, in ascending order, at and around the switch-over."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(m)
+    host = rng.integers(0, 1000, m).astype(np.int32)
+    theta = 500
+    vals = torch.from_numpy(host).cuda()
+    idx = torch.full((m,), -1, dtype=torch.int32, device="cuda")
+    nsel = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    fem.fem_select_noalloc(vals, theta, idx, nsel)
+    torch.cuda.synchronize()
+    want = np.nonzero(host >= theta)[0]
+    k = int(nsel.item())
+    assert k == want.size
+    assert np.array_equal(idx[:k].cpu().numpy(), want)
+    assert np.all(idx[k:].cpu().numpy() == -1)
