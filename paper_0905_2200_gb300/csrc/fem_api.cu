@@ -40,10 +40,17 @@ struct fem_ctx {
     fem_config cfg{};
     int sm_count = 152;
     std::map<int32_t, StreamDev> streams;
+    // per loaded stream, its type histogram (the level-1 counts), read back in the
+    // load's own round trip so that mining needs no wait for it
+    std::map<int32_t, std::vector<uint32_t>> hist_h;
     int32_t next_id = 1;
     uint32_t *d_err = nullptr;    // device error word
     uint32_t *d_small = nullptr;  // 64 device words for counters
     uint32_t *h_small = nullptr;  // 64 pinned host words
+    // pinned staging of an interval set (so that its upload is asynchronous), and the
+    // event after the last upload from it (the next one waits for that copy to leave)
+    fem_interval *h_ivl = nullptr;
+    cudaEvent_t ivl_ev = nullptr;
     std::map<std::string, DevBuf> bufs;
     std::vector<fem_level_stats> stats;
     std::vector<StreamDev> pool;  // buffers of freed streams, reused by later loads
@@ -184,7 +191,15 @@ int check_intervals(const StreamDev &s, const fem_interval *I, uint32_t nI) {
 int upload_intervals(fem_ctx *c, const fem_interval *I, uint32_t nI, cudaStream_t st,
                      uint2 **d_ivl) {
     RET(dbuf(c, "ivl", std::max<uint32_t>(nI, 1), d_ivl));
-    if (nI) CK(cudaMemcpyAsync(*d_ivl, I, nI * sizeof(uint2), cudaMemcpyHostToDevice, st));
+    if (!nI) return FEM_OK;
+    if (nI > FEM_MAX_INTERVALS + 1) {
+        CK(cudaMemcpyAsync(*d_ivl, I, nI * sizeof(uint2), cudaMemcpyHostToDevice, st));
+        return FEM_OK;
+    }
+    CK(cudaEventSynchronize(c->ivl_ev));  // the previous upload has left the staging
+    std::memcpy(c->h_ivl, I, nI * sizeof(fem_interval));
+    CK(cudaMemcpyAsync(*d_ivl, c->h_ivl, nI * sizeof(uint2), cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(c->ivl_ev, st));
     return FEM_OK;
 }
 
@@ -603,6 +618,8 @@ int fem_create(fem_ctx **out, int device) {
         cudaMalloc(&c->d_err, sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&c->d_small, 64 * sizeof(uint32_t)) != cudaSuccess ||
         cudaMallocHost(&c->h_small, 64 * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost(&c->h_ivl, (FEM_MAX_INTERVALS + 1) * sizeof(fem_interval)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ivl_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreate(&c->kev[0]) != cudaSuccess || cudaEventCreate(&c->kev[1]) != cudaSuccess ||
         cudaEventCreate(&c->kev[2]) != cudaSuccess || cudaEventCreate(&c->tev[0]) != cudaSuccess ||
         cudaEventCreate(&c->tev[1]) != cudaSuccess) {
@@ -631,6 +648,8 @@ int fem_destroy(fem_ctx *c) {
     if (c->d_err) cudaFree(c->d_err);
     if (c->d_small) cudaFree(c->d_small);
     if (c->h_small) cudaFreeHost(c->h_small);
+    if (c->h_ivl) cudaFreeHost(c->h_ivl);
+    if (c->ivl_ev) cudaEventDestroy(c->ivl_ev);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
     for (auto &e : c->kev)
@@ -753,6 +772,7 @@ int fem_load_stream(fem_ctx *c, const uint8_t *types, const uint32_t *t_us, uint
     }
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     int rc = FEM_OK;
+    std::vector<uint32_t> hist_host;
     do {
         if (cudaMemsetAsync(c->d_err, 0, 4, st) != cudaSuccess ||
             cudaMemsetAsync(s.hist, 0, 256 * 4, st) != cudaSuccess ||
@@ -768,17 +788,22 @@ int fem_load_stream(fem_ctx *c, const uint8_t *types, const uint32_t *t_us, uint
                 break;
             }
         }
-        // error word and last time in one round trip
-        uint32_t *hw = c->h_small;
+        // error word, last time and type histogram in one round trip
+        void *hp;
+        if ((rc = pinbuf(c, 0, (2 + 256) * sizeof(uint32_t), st, &hp)) != FEM_OK) break;
+        uint32_t *hw = static_cast<uint32_t *>(hp);
         if (cudaMemcpyAsync(hw, c->d_err, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             (n && cudaMemcpyAsync(hw + 1, s.t + (n - 1), 4, cudaMemcpyDeviceToHost, st) !=
                       cudaSuccess) ||
+            cudaMemcpyAsync(hw + 2, s.hist, n_types * 4, cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             rc = FEM_ECUDA;
             break;
         }
         if ((rc = err_status(hw[0])) != FEM_OK) break;
         if (n) s.t_max = hw[1];
+        hist_host.assign(hw + 2, hw + 2 + n_types);
     } while (0);
     if (rc != FEM_OK) {
         cudaGetLastError();
@@ -788,6 +813,7 @@ int fem_load_stream(fem_ctx *c, const uint8_t *types, const uint32_t *t_us, uint
     }
     const int32_t id = c->next_id++;
     c->streams[id] = s;
+    c->hist_h[id] = std::move(hist_host);
     *id_out = id;
     return FEM_OK;
 }
@@ -802,6 +828,7 @@ int fem_free_stream(fem_ctx *c, int32_t id) {
     cudaDeviceSynchronize();
     c->pool.push_back(it->second);
     c->streams.erase(it);
+    c->hist_h.erase(id);
     while (c->pool.size() > 4) {
         free_stream_buffers(c->pool.front());
         c->pool.erase(c->pool.begin());
@@ -1079,26 +1106,25 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
     unsigned long long *touched;
     RETF(dbuf(c, "touched", 2 * (FEM_MAX_LEN + 1), &touched));
     CKF(cudaMemsetAsync(touched, 0, 2 * (FEM_MAX_LEN + 1) * sizeof(unsigned long long), st));
-    // level 1: the count of a one-node episode is the number of events of its type
+    // level 1: the count of a one-node episode is the number of events of its type.
+    // The device keeps the frequent types for generating level 2; the host takes the
+    // same types (the same comparison) from the histogram the load read back, so it
+    // needs no round trip to size level 2.
     uint32_t *ftypes;
     RETF(dbuf(c, "ftypes", 256, &ftypes));
     CKF(launch_type_filter(s.hist, s.K, theta, ftypes, c->d_small + W_COUNT0, st));
-    // histogram, frequent types and their number in one round trip (pinned staging)
-    void *h1;
-    RETF(pinbuf(c, 1, (2 * 256 + 1) * sizeof(uint32_t), st, &h1));
-    uint32_t *hist = static_cast<uint32_t *>(h1), *ft = hist + 256;
-    CKF(cudaMemcpyAsync(hist, s.hist, s.K * 4, cudaMemcpyDeviceToHost, st));
-    CKF(cudaMemcpyAsync(ft, ftypes, 256 * 4, cudaMemcpyDeviceToHost, st));
-    CKF(cudaMemcpyAsync(ft + 256, c->d_small + W_COUNT0, 4, cudaMemcpyDeviceToHost, st));
-    CKF(cudaStreamSynchronize(st));
-    const uint32_t f1 = ft[256];
-    for (uint32_t i = 0; i < f1; ++i) {
+    const std::vector<uint32_t> &hist = c->hist_h[id];
+    if (hist.size() != s.K) return fail(FEM_EINVAL);
+    uint32_t f1 = 0;
+    for (uint32_t a = 0; a < s.K; ++a) {
+        if (!(hist[a] >= theta)) continue;
         fem_episode e;
         std::memset(&e, 0, sizeof(e));
-        e.types[0] = (uint8_t)ft[i];
+        e.types[0] = (uint8_t)a;
         e.len = 1;
         res->eps[0].push_back(e);
-        res->counts[0].push_back(hist[ft[i]]);
+        res->counts[0].push_back(hist[a]);
+        ++f1;
     }
     if (max_len < 2 || f1 < (repeats ? 1u : 2u) || nI == 0) {
         *out = res;

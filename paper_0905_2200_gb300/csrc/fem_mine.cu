@@ -625,8 +625,6 @@ cudaError_t launch_type_filter(const uint32_t *hist, uint32_t K, uint32_t theta,
     return cudaGetLastError();
 }
 
-// Level 2: every ordered pair (a, b) of distinct frequent types, once per interval,
-// in canonical order (a, interval, b).
 // Level 2: ordered pairs (a, b) of frequent types, a != b unless `repeats`, once per
 // interval, in canonical order (a, interval, b).
 __global__ void k_level2(const uint32_t *__restrict__ ftypes, uint32_t f, uint32_t n_ivl,

@@ -182,10 +182,10 @@ def _stream_handle(stream):
 
 
 def _intervals(intervals):
-    iv = np.asarray(intervals, dtype=np.uint32).reshape(-1, 2)
+    iv = np.ascontiguousarray(np.asarray(intervals, dtype=np.uint32).reshape(-1, 2))
     arr = (fem_interval * max(len(iv), 1))()
-    for i, (lo, hi) in enumerate(iv):
-        arr[i].lo_us, arr[i].hi_us = int(lo), int(hi)
+    if len(iv):
+        ctypes.memmove(arr, iv.ctypes.data, iv.nbytes)
     return arr, len(iv)
 
 
@@ -369,10 +369,10 @@ def fem_mine_levelwise(ctx, sid, intervals, theta, max_len, stream=None, raw=Fal
             f = m.value
             if f == 0:
                 continue
-            rec = np.ctypeslib.as_array(ctypes.cast(pe, ctypes.POINTER(ctypes.c_uint8)),
-                                        shape=(f, 16)).copy()
-            cnt = np.ctypeslib.as_array(ctypes.cast(pcn, ctypes.POINTER(ctypes.c_uint32)),
-                                        shape=(f,)).copy()
+            rec = np.empty((f, 16), np.uint8)
+            cnt = np.empty(f, np.uint32)
+            ctypes.memmove(rec.ctypes.data, pe, f * 16)
+            ctypes.memmove(cnt.ctypes.data, pcn, f * 4)
             if raw:
                 out[level] = (rec, cnt)
             else:
