@@ -774,9 +774,11 @@ int fem_load_stream(fem_ctx *c, const uint8_t *types, const uint32_t *t_us, uint
     int rc = FEM_OK;
     std::vector<uint32_t> hist_host;
     do {
+        // the histogram is cleared here (k_bucket accumulates into it); the chunk start
+        // times are all written by k_bucket, and need filling only for an empty stream
         if (cudaMemsetAsync(c->d_err, 0, 4, st) != cudaSuccess ||
             cudaMemsetAsync(s.hist, 0, 256 * 4, st) != cudaSuccess ||
-            cudaMemsetAsync(s.cfirst, 0xFF, (nc + 1) * 4, st) != cudaSuccess) {
+            (!n && cudaMemsetAsync(s.cfirst, 0xFF, (nc + 1) * 4, st) != cudaSuccess)) {
             rc = FEM_ECUDA;
             break;
         }
@@ -1179,10 +1181,12 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
             RETF(count_launch(c, s, cands, nullptr, m, (int)N, d_ivl, nI, FEM_PASS_RELAXED, rel,
                               true, st, &plr));
         cudaEventRecord(c->ev[3], st);
-        CKF(launch_touched(cands, nullptr, m, s.hist, touched + 2 * N, st));
         cudaEventRecord(c->ev[4], st);
         uint32_t ms;
         RETF(compact_and_read(rel, m, idx_s, W_COUNT0, scratch, plr, &ms, c->ev[5]));
+        // work statistics, queued after the wait: the device would otherwise sit idle
+        // while the host prepares the next launch
+        CKF(launch_touched(cands, nullptr, m, s.hist, touched + 2 * N, st));
         PassInfo pi;
         pass_info(c, plr, &pi);
         cudaEventElapsedTime(&ls.ms_generate, c->ev[0], c->ev[1]);
@@ -1202,9 +1206,9 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
             RETF(count_launch(c, s, cands, idx_s, ms, (int)N, d_ivl, nI, FEM_PASS_EXACT, ex, true,
                               st, &plx));
         cudaEventRecord(c->ev[7], st);
-        CKF(launch_touched(cands, idx_s, ms, s.hist, touched + 2 * N + 1, st));
         uint32_t f = 0;
         if (ms) RETF(compact_and_read(ex, ms, idx_f, W_COUNT1, scratch, plx, &f, nullptr));
+        CKF(launch_touched(cands, idx_s, ms, s.hist, touched + 2 * N + 1, st));
         PassInfo pe;
         pass_info(c, plx, &pe);
         cudaEventElapsedTime(&ls.ms_compact, c->ev[4], c->ev[5]);

@@ -112,8 +112,6 @@ cudaError_t launch_load_stream(StreamDev &s, cudaStream_t st, uint32_t *d_err) {
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(s.hist, 0, sizeof(uint32_t) * s.K, st);
-    if (e != cudaSuccess) return e;
     k_bucket<<<s.n_chunks, 256, 0, st>>>(s.t, s.type, s.n, s.K, s.offs, s.n_chunks, s.bev, s.boff,
                                          s.cfirst, s.hist, 0);
     note_launch();
