@@ -770,7 +770,6 @@ int fem_load_stream(fem_ctx *c, const uint8_t *types, const uint32_t *t_us, uint
         release();
         return FEM_ENOMEM;
     }
-    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     int rc = FEM_OK;
     std::vector<uint32_t> hist_host;
     do {
@@ -782,9 +781,14 @@ int fem_load_stream(fem_ctx *c, const uint8_t *types, const uint32_t *t_us, uint
             rc = FEM_ECUDA;
             break;
         }
-        if (n) {
-            if (cudaMemcpyAsync(s.t, t_us, n * 4, kind, st) != cudaSuccess ||
-                cudaMemcpyAsync(s.type, types, n, kind, st) != cudaSuccess ||
+        if (n && on_device) {  // one kernel reads, checks, copies and groups the events
+            if (launch_load_stream(s, st, c->d_err, t_us, types) != cudaSuccess) {
+                rc = FEM_ECUDA;
+                break;
+            }
+        } else if (n) {
+            if (cudaMemcpyAsync(s.t, t_us, n * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                cudaMemcpyAsync(s.type, types, n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
                 launch_load_stream(s, st, c->d_err) != cudaSuccess) {
                 rc = FEM_ECUDA;
                 break;

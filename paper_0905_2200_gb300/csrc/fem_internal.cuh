@@ -172,7 +172,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
 void note_launch(uint32_t k = 1);
 
 // fem_stream.cu
-cudaError_t launch_load_stream(StreamDev &s, cudaStream_t st, uint32_t *d_err);
+// Validate and group a stream already in s.t / s.type, or (src_t given) one in other
+// device memory, copying it into s.t / s.type on the way.
+cudaError_t launch_load_stream(StreamDev &s, cudaStream_t st, uint32_t *d_err,
+                               const uint32_t *src_t = nullptr, const uint8_t *src_type = nullptr);
 // regroup chunks [c0, c1) of a stream that grew to s.n events (type histogram untouched)
 cudaError_t launch_bucket_chunks(StreamDev &s, uint32_t c0, uint32_t c1, cudaStream_t st);
 // dst[idx[i]] = src[i] and flags[idx[i]] = 1 for i < *m_dev (grid sized for m_max)

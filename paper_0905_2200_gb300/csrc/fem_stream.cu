@@ -10,28 +10,23 @@
 
 namespace fem {
 
-__global__ void k_validate(const uint32_t *__restrict__ t, const uint8_t *__restrict__ ty,
-                           uint64_t n, uint32_t K, uint32_t *err) {
-    uint32_t bad = 0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        if (ty[i] >= K) bad |= ERR_TYPE;
-        if (i + 1 < n && t[i] > t[i + 1]) bad |= ERR_UNSORTED;
-    }
-    bad = __reduce_or_sync(0xffffffffu, bad);
-    if (bad && (threadIdx.x & 31) == 0) atomicOr(err, bad);
-}
-
 // One block of 256 threads per chunk.  Warp w ranks events [256w, 256w+256) of the
 // chunk within their type (match.any per 32-event round), the per-(warp, type)
-// counts are scanned type-major, and each event is written to its slot.
+// counts are scanned type-major, and each event is written to its slot.  The events
+// are read from (t, ty); with `err` the block also checks them (types < K, times
+// non-decreasing, the pair across the chunk's end included) and ORs the findings in;
+// with `t_out` it also copies them there (the library's own copy of a stream loaded
+// from device memory), so that a load takes one kernel.  Event types are bytes, so
+// the grouping stays in bounds whatever K is; a load that finds bad events fails.
 __global__ void __launch_bounds__(256) k_bucket(const uint32_t *__restrict__ t,
                                                 const uint8_t *__restrict__ ty, uint64_t n,
                                                 uint32_t K, uint32_t offs, uint32_t n_chunks,
                                                 uint2 *__restrict__ bev,
                                                 uint16_t *__restrict__ boff,
                                                 uint32_t *__restrict__ cfirst,
-                                                uint32_t *__restrict__ hist, uint32_t c0) {
+                                                uint32_t *__restrict__ hist, uint32_t c0,
+                                                uint32_t *err, uint32_t *__restrict__ t_out,
+                                                uint8_t *__restrict__ ty_out) {
     __shared__ uint16_t wcnt[8][256];
     __shared__ uint32_t tbase[257];
     __shared__ uint32_t wsum[8];
@@ -42,7 +37,7 @@ __global__ void __launch_bounds__(256) k_bucket(const uint32_t *__restrict__ t,
     for (uint32_t i = threadIdx.x; i < 8 * 256; i += 256) (&wcnt[0][0])[i] = 0;
     __syncthreads();
 
-    uint32_t myty[8], myrank[8];
+    uint32_t myty[8], myrank[8], bad = 0;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         const uint32_t li = w * 256 + r * 32 + lane;
@@ -51,6 +46,15 @@ __global__ void __launch_bounds__(256) k_bucket(const uint32_t *__restrict__ t,
         const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
         myty[r] = v;
         myrank[r] = 0;
+        if (valid && err) {
+            const uint64_t gi = base + li;
+            if (v >= K) bad |= ERR_TYPE;
+            if (gi + 1 < n && t[gi] > t[gi + 1]) bad |= ERR_UNSORTED;
+        }
+        if (valid && t_out) {
+            t_out[base + li] = t[base + li];
+            ty_out[base + li] = (uint8_t)v;
+        }
         if (valid) {
             const uint32_t peers = __match_any_sync(vmask, v);
             const uint32_t below = __popc(peers & ((1u << lane) - 1u));
@@ -102,18 +106,21 @@ __global__ void __launch_bounds__(256) k_bucket(const uint32_t *__restrict__ t,
         cfirst[c] = t[base];
         if (c + 1 == n_chunks) cfirst[n_chunks] = 0xFFFFFFFFu;
     }
+    if (err) {
+        bad = __reduce_or_sync(0xffffffffu, bad);
+        if (bad && lane == 0) atomicOr(err, bad);
+    }
 }
 
-cudaError_t launch_load_stream(StreamDev &s, cudaStream_t st, uint32_t *d_err) {
+cudaError_t launch_load_stream(StreamDev &s, cudaStream_t st, uint32_t *d_err,
+                               const uint32_t *src_t, const uint8_t *src_type) {
     if (s.n == 0) return cudaSuccess;
-    const uint64_t want = (s.n + 255) / 256;
-    const uint32_t vb = (uint32_t)(want < 2432ull ? want : 2432ull);
-    k_validate<<<vb, 256, 0, st>>>(s.t, s.type, s.n, s.K, d_err);
-    note_launch();
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    k_bucket<<<s.n_chunks, 256, 0, st>>>(s.t, s.type, s.n, s.K, s.offs, s.n_chunks, s.bev, s.boff,
-                                         s.cfirst, s.hist, 0);
+    if (src_t)  // device input: read it where it is and copy it while grouping
+        k_bucket<<<s.n_chunks, 256, 0, st>>>(src_t, src_type, s.n, s.K, s.offs, s.n_chunks, s.bev,
+                                             s.boff, s.cfirst, s.hist, 0, d_err, s.t, s.type);
+    else
+        k_bucket<<<s.n_chunks, 256, 0, st>>>(s.t, s.type, s.n, s.K, s.offs, s.n_chunks, s.bev,
+                                             s.boff, s.cfirst, s.hist, 0, d_err, nullptr, nullptr);
     note_launch();
     return cudaGetLastError();
 }
@@ -121,7 +128,7 @@ cudaError_t launch_load_stream(StreamDev &s, cudaStream_t st, uint32_t *d_err) {
 cudaError_t launch_bucket_chunks(StreamDev &s, uint32_t c0, uint32_t c1, cudaStream_t st) {
     if (c1 <= c0) return cudaSuccess;
     k_bucket<<<c1 - c0, 256, 0, st>>>(s.t, s.type, s.n, s.K, s.offs, s.n_chunks, s.bev, s.boff,
-                                      s.cfirst, nullptr, c0);
+                                      s.cfirst, nullptr, c0, nullptr, nullptr, nullptr);
     note_launch();
     return cudaGetLastError();
 }

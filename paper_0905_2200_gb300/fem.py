@@ -367,8 +367,8 @@ def fem_mine_levelwise(ctx, sid, intervals, theta, max_len, stream=None, raw=Fal
             _check(lib.fem_result_level(res, level, ctypes.byref(m), ctypes.byref(pe),
                                         ctypes.byref(pcn)), "fem_result_level")
             f = m.value
-            if f == 0:
-                continue
+            if f == 0:  # level N + 1 is generated from level N's frequent set only
+                break
             rec = np.empty((f, 16), np.uint8)
             cnt = np.empty(f, np.uint32)
             ctypes.memmove(rec.ctypes.data, pe, f * 16)

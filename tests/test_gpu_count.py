@@ -194,6 +194,37 @@ def test_device_tensors_in_and_out(ctx, mid):
     fem.fem_free_stream(ctx, sid2)
 
 
+def test_device_load_checks_and_copies(ctx):
+    """A stream loaded from device memory is checked, copied and grouped by one kernel:
+    an inversion across a chunk's end and a type >= K are rejected, and a valid stream
+    has the type counts and episode counts of the same stream loaded from host memory."""
+    torch = pytest.importorskip("torch")
+    K = 5
+    ty, t = synth.tiny_stream(7, 5000, K, 300, tie_prob=0.2)
+    assert t[2047] > 0
+    t_bad = t.copy()
+    t_bad[2048] = t_bad[2047] - 1  # the pair across the first chunk's end
+    ty_bad = ty.copy()
+    ty_bad[4999] = K  # the last event of the ragged last chunk
+    for tt, yy, status in ((t_bad, ty, -2), (t, ty_bad, -3)):
+        with pytest.raises(fem.FemError) as e:
+            fem.fem_load_stream(ctx, torch.from_numpy(yy).cuda(), torch.from_numpy(tt).cuda(), K)
+        assert e.value.status == status
+    sid_d = fem.fem_load_stream(ctx, torch.from_numpy(ty).cuda(), torch.from_numpy(t).cuda(), K)
+    sid_h = fem.fem_load_stream(ctx, ty, t, K)
+    assert np.array_equal(fem.fem_type_counts(ctx, sid_d, K), np.bincount(ty, minlength=K))
+    L, E, iv = synth.random_candidates(4, 300, K, [1, 2, 3], 2)
+    rec = fem.pack_episodes(L, E, iv)
+    I = np.array([[0, 400], [200, 900]], np.uint32)
+    for p in PASSES:
+        got_d = fem.fem_count_candidates(ctx, sid_d, rec, I, p)
+        got_h = fem.fem_count_candidates(ctx, sid_h, rec, I, p)
+        assert np.array_equal(got_d, got_h)
+        assert_counts_equal(got_d, oracle_counts(ty, t, L, E, iv, I, p), "device load")
+    fem.fem_free_stream(ctx, sid_d)
+    fem.fem_free_stream(ctx, sid_h)
+
+
 # ------------------------------------------------------------------------ edge cases
 def test_empty_and_tiny_streams(ctx):
     I = np.array([[0, 1000]], np.uint32)
