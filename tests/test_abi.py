@@ -59,3 +59,17 @@ def test_episode_record_layout():
     assert list(rec[0]) == [1, 2, 3, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 3]
     L, E, iv = fem.unpack_episodes(rec)
     assert L[0] == 3 and list(E[0, :3]) == [1, 2, 3] and list(iv[0, :2]) == [0, 1]
+
+
+def test_interval_marshalling():
+    """Interval sets reach the C ABI as fem_interval records in the given order (lists,
+    uint32 arrays, non-contiguous views, and the empty set)."""
+    import numpy as np
+    want = [(0, 2000), (2000, 5000), (5000, 10000), (10000, 20000)]
+    arr = np.array(want, np.uint32)
+    for given in (want, arr, np.asfortranarray(arr), arr[::-1][::-1]):
+        recs, n = fem._intervals(given)
+        assert n == 4
+        assert [(recs[i].lo_us, recs[i].hi_us) for i in range(n)] == want
+    recs, n = fem._intervals(np.zeros((0, 2), np.uint32))
+    assert n == 0
