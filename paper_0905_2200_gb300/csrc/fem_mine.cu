@@ -69,14 +69,17 @@ __device__ __forceinline__ bool keep_at(const uint32_t *vals, const uint8_t *fla
 // ------------------------------------------------------------------ MapConcatenate stitch
 // stitch_run<SMX, SU>: the composition with tables of SMX slots (the layout) of which
 // at most SU can hold a class anywhere in the warp's tables; every loop is unrolled
-// and branch-free over SU slots.
+// and branch-free over SU slots.  G lanes (a power of two) work on one episode; lane
+// gl of the group holds segments [a, b); `live` is false for a group past the end of
+// the candidates or flagged for a recount (it only takes part in the shuffles).
 template <int SMX, int SU>
 __device__ __forceinline__ void stitch_run(const uint4 *__restrict__ tables, uint32_t m, uint32_t a,
-                                           uint32_t b, uint32_t ci, uint32_t *__restrict__ out,
+                                           uint32_t b, uint32_t ci, uint32_t G, uint32_t gl,
+                                           bool live, uint32_t *__restrict__ out,
                                            uint8_t *__restrict__ redo, uint32_t *err) {
     const uint32_t lane = threadIdx.x & 31;
     uint32_t fk[SU], fc[SU], fe[SU];
-    bool ident = a == b, bad = false;
+    bool ident = !live || a == b, bad = false;
 #pragma unroll
     for (int j = 0; j < SU; ++j) fk[j] = CLS_EMPTY, fc[j] = 0, fe[j] = CLS_NONE;
     // a table's slot 0 holds, in w, how many slots the counter wrote; the rest are empty
@@ -120,16 +123,17 @@ __device__ __forceinline__ void stitch_run(const uint4 *__restrict__ tables, uin
         }
     }
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
+    for (uint32_t d = 1; d < 32; d <<= 1) {
+        if (d >= G) break;  // the same on every lane
         uint32_t pk[SU], pc[SU], pe[SU];
 #pragma unroll
         for (int i = 0; i < SU; ++i) {
-            pk[i] = __shfl_down_sync(0xffffffffu, fk[i], d);
-            pc[i] = __shfl_down_sync(0xffffffffu, fc[i], d);
-            pe[i] = __shfl_down_sync(0xffffffffu, fe[i], d);
+            pk[i] = __shfl_down_sync(0xffffffffu, fk[i], d, G);
+            pc[i] = __shfl_down_sync(0xffffffffu, fc[i], d, G);
+            pe[i] = __shfl_down_sync(0xffffffffu, fe[i], d, G);
         }
-        const bool pident = __shfl_down_sync(0xffffffffu, (int)ident, d) != 0;
-        if ((lane & (2 * d - 1)) == 0 && lane + d < 32 && !pident) {
+        const bool pident = __shfl_down_sync(0xffffffffu, (int)ident, d, G) != 0;
+        if ((gl & (2 * d - 1)) == 0 && gl + d < G && !pident) {
             if (ident) {
 #pragma unroll
                 for (int i = 0; i < SU; ++i) fk[i] = pk[i], fc[i] = pc[i], fe[i] = pe[i];
@@ -139,8 +143,10 @@ __device__ __forceinline__ void stitch_run(const uint4 *__restrict__ tables, uin
             }
         }
     }
-    bad = __any_sync(0xffffffffu, bad);
-    if (lane == 0) {
+    // a composition step of any lane of the group that found no row makes it fail
+    const uint32_t gmask = G >= 32 ? 0xFFFFFFFFu : ((1u << G) - 1u) << (lane & ~(G - 1));
+    bad = (__ballot_sync(0xffffffffu, bad) & gmask) != 0;
+    if (gl == 0 && live) {
         bool found = false;
         uint32_t total = 0;
 #pragma unroll
@@ -155,41 +161,46 @@ __device__ __forceinline__ void stitch_run(const uint4 *__restrict__ tables, uin
     }
 }
 
-// One warp per episode.  Lane l composes the transfer tables of its contiguous
-// run of segments (for every entry class of the run's first segment); the 32
-// partial functions are then composed pairwise in log2(32) shuffle rounds, the
-// tree of Concatenate steps; lane 0 evaluates the result at class "none".
-// Most tables hold one or two classes: the warp first reads how many slots its
-// tables use and composes over that many only (1, 2, 4, 8 or all), a choice the
-// same on every lane, so the composition stays unrolled and free of branches.
+// G lanes per episode (a power of two up to 32, G = 32 / 2^k episodes per warp).  Lane
+// gl of a group composes the transfer tables of its contiguous run of segments (for
+// every entry class of the run's first segment); the G partial functions are then
+// composed pairwise in log2(G) shuffle rounds, the tree of Concatenate steps; lane 0 of
+// the group evaluates the result at class "none".  Most tables hold one or two
+// classes: the warp first reads how many slots its tables use and composes over that
+// many only (1, 2, 4, 8 or all), a choice the same on every lane, so the composition
+// stays unrolled and free of branches.
 template <int SMX>
 __device__ void stitch_one(const uint4 *__restrict__ tables, uint32_t m, uint32_t P, uint32_t ci,
-                           uint32_t *__restrict__ out, uint8_t *__restrict__ redo, uint32_t *err) {
-    const uint32_t lane = threadIdx.x & 31;
-    if (redo[ci]) return;  // the host recounts this episode
-    const uint32_t a = (uint32_t)(((uint64_t)P * lane) >> 5);
-    const uint32_t b = (uint32_t)(((uint64_t)P * (lane + 1)) >> 5);
+                           uint32_t G, bool live, uint32_t *__restrict__ out,
+                           uint8_t *__restrict__ redo, uint32_t *err) {
+    const uint32_t gl = threadIdx.x & (G - 1), lg = __ffs(G) - 1;
+    live = live && !redo[ci];  // a flagged episode is recounted by the host
+    const uint32_t a = (uint32_t)(((uint64_t)P * gl) >> lg);
+    const uint32_t b = (uint32_t)(((uint64_t)P * (gl + 1)) >> lg);
     uint32_t n = 1;
-    for (uint32_t q = a; q < b; ++q) n = max(n, tables[((uint64_t)q * m + ci) * SMX].w);
+    if (live)
+        for (uint32_t q = a; q < b; ++q) n = max(n, tables[((uint64_t)q * m + ci) * SMX].w);
     n = __reduce_max_sync(0xffffffffu, n);
     if (n <= 1)
-        stitch_run<SMX, 1>(tables, m, a, b, ci, out, redo, err);
+        stitch_run<SMX, 1>(tables, m, a, b, ci, G, gl, live, out, redo, err);
     else if (n <= 2)
-        stitch_run<SMX, 2>(tables, m, a, b, ci, out, redo, err);
+        stitch_run<SMX, 2>(tables, m, a, b, ci, G, gl, live, out, redo, err);
     else if (n <= 4)
-        stitch_run<SMX, (SMX < 4 ? SMX : 4)>(tables, m, a, b, ci, out, redo, err);
+        stitch_run<SMX, (SMX < 4 ? SMX : 4)>(tables, m, a, b, ci, G, gl, live, out, redo, err);
     else if (SMX > 8 && n <= 8)
-        stitch_run<SMX, (SMX < 8 ? SMX : 8)>(tables, m, a, b, ci, out, redo, err);
+        stitch_run<SMX, (SMX < 8 ? SMX : 8)>(tables, m, a, b, ci, G, gl, live, out, redo, err);
     else
-        stitch_run<SMX, SMX>(tables, m, a, b, ci, out, redo, err);
+        stitch_run<SMX, SMX>(tables, m, a, b, ci, G, gl, live, out, redo, err);
 }
 
 template <int SMX>
 __global__ void __launch_bounds__(256) k_stitch(const uint4 *__restrict__ tables, uint32_t m,
-                                                uint32_t P, uint32_t *__restrict__ out,
+                                                uint32_t P, uint32_t G, uint32_t *__restrict__ out,
                                                 uint8_t *__restrict__ redo, uint32_t *err) {
-    const uint32_t ci = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (ci < m) stitch_one<SMX>(tables, m, P, ci, out, redo, err);
+    const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, lg = __ffs(G) - 1;
+    if (((gt & ~31u) >> lg) >= m) return;  // the whole warp is past the end
+    const uint32_t ci = gt >> lg;
+    stitch_one<SMX>(tables, m, P, ci, G, ci < m, out, redo, err);
 }
 
 // One warp per episode slot of a batch of jobs (each job its own tables and outputs).
@@ -207,7 +218,7 @@ __global__ void __launch_bounds__(256) k_stitch_batch(const CountParams *__restr
     }
     const CountParams &p = jobs[lo];
     const uint32_t ci = e - job_base[lo];
-    if (ci < p.m && p.P > 0) stitch_one<S_MAX>(p.tables, p.m, p.P, ci, p.out, p.redo, err);
+    stitch_one<S_MAX>(p.tables, p.m, p.P, ci, 32u, ci < p.m && p.P > 0, p.out, p.redo, err);
 }
 
 cudaError_t launch_stitch_batch(const CountParams *jobs, const uint32_t *job_base,
@@ -222,11 +233,15 @@ cudaError_t launch_stitch_batch(const CountParams *jobs, const uint32_t *job_bas
 cudaError_t launch_stitch(const uint4 *tables, uint32_t m, uint32_t P, uint32_t *out,
                           uint8_t *redo, uint32_t *err, cudaStream_t st, uint32_t classes) {
     if (m == 0) return cudaSuccess;
-    const uint32_t blocks = (uint32_t)(((uint64_t)m * 32 + 255) / 256);
+    // lanes per episode: about four segments per lane, so that a short cut (the relaxed
+    // passes' 20-odd segments) takes a quarter of a warp rather than a whole one
+    uint32_t G = 1;
+    while (G < 32 && G * 4 < P) G <<= 1;
+    const uint32_t blocks = (uint32_t)(((uint64_t)m * G + 255) / 256);
     if (classes == S_RECOUNT)
-        k_stitch<S_RECOUNT><<<blocks, 256, 0, st>>>(tables, m, P, out, redo, err);
+        k_stitch<S_RECOUNT><<<blocks, 256, 0, st>>>(tables, m, P, G, out, redo, err);
     else if (classes == S_MAX)
-        k_stitch<S_MAX><<<blocks, 256, 0, st>>>(tables, m, P, out, redo, err);
+        k_stitch<S_MAX><<<blocks, 256, 0, st>>>(tables, m, P, G, out, redo, err);
     else
         return cudaErrorInvalidValue;
     note_launch();
