@@ -47,9 +47,9 @@ NCU_TRAFFIC = {
     # current counting kernels, ncu --set full of the first mining step with the rule's
     # launch shapes (--no-tune; the tuned step uses the same shape for its dominant launch,
     # level 3 relaxed): dram__bytes_read.sum + dram__bytes_write.sum per launch
-    "e058eb043f174144": {
-        "single_recording_64types_300s": {"2/relaxed": 13680128, "2/exact": 8621568,
-                                          "3/relaxed": 12858112, "3/exact": 3724288},
+    "9205ba36a7e74875": {
+        "single_recording_64types_300s": {"2/relaxed": 13687040, "2/exact": 8607744,
+                                          "3/relaxed": 12857856, "3/exact": 3724288},
     },
 }
 
