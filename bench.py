@@ -70,6 +70,13 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def dom_kernel(level: int, ps: str) -> str:
+    """Name of the library's counting kernel for a (length, pass) launch."""
+    if ps == "exact":
+        return "k_count_exact" if level <= 2 else "k_count_wide"
+    return "k_count_wide" if level >= 4 else "k_count"
+
+
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi clock and throttle-reason samples taken during the timed region."""
@@ -170,9 +177,26 @@ def workload(rank: int, deep: bool = False):
     return cfg
 
 
-def cpu_baseline(cfg, budget_s=12.0, seed=0):
-    """The oracle, as it stands, on a bounded sample of the level-2 two-pass count."""
+def host_cpu():
+    """(CPU model, logical cores) of this host, from lscpu (falls back to os)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return model or "unknown", os.cpu_count() or 1
+
+
+def cpu_baseline(cfg, budget_s=10.0, seed=0):
+    """The oracle, as it stands, on bounded samples of the level-2 two-pass count:
+    single-threaded, then as one independent oracle process per host core over shards
+    of a sample (the pool is spawned, so it is safe after the GPU was used)."""
     import oracle
+    from oracle.shards import ShardPool
     from paper_0905_2200_gb300 import synth
     s = cfg["stream"]
     I = cfg["intervals"]
@@ -188,10 +212,38 @@ def cpu_baseline(cfg, budget_s=12.0, seed=0):
         units += len(pick) * s.n
         done += len(pick)
         m = min(m * 2, 1024)
-    return {"value": units / t_used, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{done} random level-2 candidates of the 16,128 (Algorithm 4: relaxed "
+    rate1 = units / t_used
+    model, cores = host_cpu()
+    # all cores: a sample sized for about budget_s of wall time
+    m_all = int(min(len(L), max(cores, rate1 * budget_s * cores / s.n)))
+    pick = np.sort(rng.choice(len(L), m_all, replace=False))
+    with ShardPool(s.types, s.t, cores) as pool:
+        pool.two_pass(L[pick[:cores]], E[pick[:cores]], iv[pick[:cores]], I, cfg["theta"])  # start-up
+        t0 = time.perf_counter()
+        pool.two_pass(L[pick], E[pick], iv[pick], I, cfg["theta"])
+        t_all = time.perf_counter() - t0
+    return {"value": m_all * s.n / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "cpu": model,
+            "sample": (f"{m_all} random level-2 candidates of the 16,128 (Algorithm 4: relaxed "
                        f"count, eliminate below theta={cfg['theta']}, exact count of survivors) "
-                       f"over the full {s.n}-event stream, single-threaded C, {t_used:.1f} s")}
+                       f"over the full {s.n}-event stream, {cores} independent single-threaded "
+                       f"C oracle processes over candidate shards, {t_all:.1f} s"),
+            "single_core": {"value": rate1, "cores": 1,
+                            "sample": f"{done} random level-2 candidates, one process, "
+                                      f"{t_used:.1f} s"}}
+
+
+def step_config(cfg, args):
+    """The workload a default-line step processes (shared by both arms)."""
+    s = cfg["stream"]
+    return {"workload": cfg["name"], "n_events": s.n, "n_types": s.n_types,
+            "intervals_us": cfg["intervals"].tolist(), "theta": cfg["theta"],
+            "max_len": cfg["max_len"], "level2_candidates": s.n_types * (s.n_types - 1) *
+            len(cfg["intervals"]),
+            "l2": "flushed between steps (256 MiB device write outside the step events)",
+            "step": "device staging of the resident stream + two-pass level-wise mining "
+                    "+ frequent sets copied to host",
+            "parallelism": f"{args.gpus} independent recordings (one per GPU)"}
 
 
 # --------------------------------------------------------------------------- our arm
@@ -270,15 +322,24 @@ def run_ours(args, rank, world, local):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = n_sm * 128 * sm_mhz * 1e6 / 1e12
     ops = OPS_PER_TOUCHED[dom[1]]
-    achieved = touched[dom] * ops / (avg_ms[dom] * 1e-3) / 1e12
-    all_ops = sum(touched[k] * OPS_PER_TOUCHED[k[1]] for k in avg_ms)
-    all_ach = all_ops / (sum(avg_ms.values()) * 1e-3) / 1e12
+
+    def unit_ops(level, ps, lv):
+        """Algorithmic integer operations of one launch on the unit basis: (candidates
+        in the pass x stream events) x (1 + (N / K) u), one type test per unit plus u
+        operations for the fraction N / K of events that match a node."""
+        m_pass = lv["candidates"] if ps == "relaxed" else lv["survivors"]
+        return m_pass * n * (1.0 + level / s.n_types * OPS_PER_TOUCHED[ps])
+
+    achieved = unit_ops(dom[0], dom[1], dom_lv) / (avg_ms[dom] * 1e-3) / 1e12
+    t_achieved = touched[dom] * ops / (avg_ms[dom] * 1e-3) / 1e12
+    lv_of = {lv["level"]: lv for lv in stats_all[-1]}
+    all_ms = sum(avg_ms.values())
+    all_ach = sum(unit_ops(k[0], k[1], lv_of[k[0]]) for k in avg_ms) / (all_ms * 1e-3) / 1e12
+    all_t = sum(touched[k] * OPS_PER_TOUCHED[k[1]] for k in avg_ms) / (all_ms * 1e-3) / 1e12
     traffic = NCU_TRAFFIC.get(kernel_source_hash(), {}).get(cfg["name"], {}).get(
         f"{dom[0]}/{dom[1]}")
-    # the library's kernel for that (length, pass): three register budgets
-    kfn = ("k_count_exact" if dom[1] == "exact" and dom[0] <= 2 else
-           "k_count_wide" if dom[1] == "exact" or dom[0] >= 4 else "k_count")
-    kname = f"{kfn}<{dom[0]}, {dom[1]}{', MapConcatenate' if dom_seg > 1 else ''}>"
+    kname = f"{dom_kernel(dom[0], dom[1])} (level {dom[0]} {dom[1]} pass" + (
+        f", {dom_seg} MapConcatenate segments)" if dom_seg > 1 else ")")
 
     # end to end through the public API with host (pinned) buffers
     h_types = torch.from_numpy(s.types.copy()).pin_memory()
@@ -313,26 +374,26 @@ def run_ours(args, rank, world, local):
         "warmup": args.warmup, "ms_per_step": tmax, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded Poisson spike trains with embedded cascades)",
-        "config": {"workload": cfg["name"], "n_events": n, "n_types": s.n_types,
-                   "intervals_us": I.tolist(), "theta": theta, "max_len": max_len,
-                   "level2_candidates": stats_all[-1][0]["candidates"] if stats_all[-1] else 0,
-                   "l2": "flushed between steps (256 MiB device write outside the step events)",
-                   "step": "device staging of the resident stream + two-pass level-wise mining "
-                           "+ frequent sets copied to host",
-                   "parallelism": f"{world} independent recordings (one per GPU)",
-                   "mapping": ("rule (segments for ~2048 threads per SM)" if args.no_tune else
-                               "measured: launch shapes tuned during the warm-up steps, "
-                               f"{tuned} classes cached")},
+        "config": dict(step_config(cfg, args),
+                       mapping=("rule (segments for ~2048 threads per SM)" if args.no_tune else
+                                "measured: launch shapes tuned during the warm-up steps, "
+                                f"{tuned} classes cached")),
         "levels": per_level,
-        "roofline": {"bound": "alu", "kernel": f"{kname} (level {dom[0]} {dom[1]} pass)",
+        "roofline": {"bound": "alu", "kernel": kname,
                      "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                      "traffic": traffic,
-                     "basis": (f"{touched[dom]:.4g} touched (episode, matching event) updates x "
-                               f"{ops} int ops / {avg_ms[dom]:.4f} ms avg launch; peak = "
-                               f"{n_sm} SMs x 128 lanes x {sm_mhz:.0f} MHz (median SM clock "
-                               f"sampled during the timed steps)"),
+                     "basis": (f"unit basis: {dom_lv['candidates'] if dom[1] == 'relaxed' else dom_lv['survivors']}"
+                               f" candidates x {n} events x (1 + {dom[0]}/{s.n_types} x {ops}) "
+                               f"int ops / {avg_ms[dom]:.4f} ms avg launch (CUDA events on the "
+                               f"launching stream); peak = SM issue ceiling {n_sm} SMs x 128 "
+                               f"lanes x {sm_mhz:.0f} MHz (median SM clock sampled during the "
+                               f"timed steps), not a measured integer-pipe peak"),
+                     "touched": {"achieved": t_achieved, "frac": t_achieved / peak,
+                                 "basis": (f"{touched[dom]:.4g} touched (episode, matching "
+                                           f"event) updates x {ops} int ops")},
                      "all_counting_launches": {"achieved": all_ach, "frac": all_ach / peak,
-                                               "ms_per_step": sum(avg_ms.values())}},
+                                               "touched_frac": all_t / peak,
+                                               "ms_per_step": all_ms}},
         "cpu_baseline": base,
         "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_max,
                 "h2d_bytes_per_step": int(5 * n + 8 * len(I)), "d2h_bytes_per_step": int(d2h)},
@@ -479,6 +540,8 @@ def run_large(args, rank, world, local):
     res = {}
     n_chunks = (s.n + 2047) // 2048
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    clocks = ClockSampler(local)
+    clocks.start()
     for name, seg in (("autotuned", 0), ("one_segment_per_chunk", n_chunks)):
         fem.fem_set_config(ctx, segments=seg)
         for _ in range(args.warmup):
@@ -493,6 +556,7 @@ def run_large(args, rank, world, local):
             e1.record()
         torch.cuda.synchronize()
         res[name] = (sum(a.elapsed_time(b) for a, b in evs) / args.steps, ex.clone(), sv.clone())
+    clk = clocks.stop()
     same = torch.equal(res["autotuned"][1], res["one_segment_per_chunk"][1])
     survivors = int(res["autotuned"][2].sum().item())
     frequent = int((res["autotuned"][1].view(torch.int32) >= theta).sum().item())
@@ -515,6 +579,7 @@ def run_large(args, rank, world, local):
         "forced_segments": {"segments_per_episode": n_chunks,
                             "ms_per_step": res["one_segment_per_chunk"][0],
                             "identical_results": bool(same)},
+        "clocks": clk,
     }
     print(json.dumps(line), flush=True)
 
@@ -564,8 +629,11 @@ def run_literal(args, rank, world, local):
     def lit():
         diag[0] = fem.fem_count_mapconcat_literal(ctx, sid, rec, I, P, out=out_l)[1]
 
+    clocks = ClockSampler(local)
+    clocks.start()
     ms_x = timed(lambda: fem.fem_count_candidates(ctx, sid, rec, I, fem.PASS_EXACT, out=out_x))
     ms_l = timed(lit)
+    clk = clocks.stop()
     ex = out_x.cpu().numpy().view(np.uint32)
     li = out_l.cpu().numpy().view(np.uint32)
     fem.fem_destroy(ctx)
@@ -589,6 +657,7 @@ def run_literal(args, rank, world, local):
                              "overcounted": int((li > ex).sum()),
                              "boundaries_no_match": diag[0][0],
                              "boundaries_several_matches": diag[0][1]},
+        "clocks": clk,
     }
     print(json.dumps(line), flush=True)
 
@@ -617,6 +686,9 @@ def run_windows(args, rank, world, local):
     for _ in range(args.warmup):
         fem.fem_count_windows(ctx, sid, rec, I, args.window_us, out=out)
     torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
     for i, (e0, e1) in enumerate(evs):
@@ -626,6 +698,7 @@ def run_windows(args, rank, world, local):
         e1.record()
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    clk = clocks.stop()
     cnt = out.cpu().numpy()
     fem.fem_destroy(ctx)
     if rank != 0:
@@ -642,6 +715,7 @@ def run_windows(args, rank, world, local):
                    "step": "fem_count_windows over all level-2 candidates"},
         "window_fraction": {"min": float(cnt.min() / span), "median": float(np.median(cnt) / span),
                             "max": float(cnt.max() / span)},
+        "clocks": clk,
     }
     print(json.dumps(line), flush=True)
 
@@ -790,9 +864,14 @@ def run_serving(args, rank, world, local):
 
 # --------------------------------------------------------------------------- reference arm
 def run_reference(args, rank, world, local):
+    """The oracle (the only reference this method has: the paper ships no code), as it
+    stands, on every host core: per step a bounded random sample of the mining step's
+    level-2 candidates through Algorithm 4 over the full stream, sharded over one
+    single-threaded oracle process per core.  Rank 0 alone runs it."""
     if rank != 0:
         return
     import oracle
+    from oracle.shards import ShardPool
     from paper_0905_2200_gb300 import synth
     oracle.build()
     cfg = workload(0)
@@ -800,31 +879,32 @@ def run_reference(args, rank, world, local):
     I = cfg["intervals"]
     L, E, iv = synth.level2_candidates(range(s.n_types), len(I))
     rng = np.random.default_rng(123)
-    per_step = 96
+    model, cores = host_cpu()
+    per_step = 64 * cores
+    with ShardPool(s.types, s.t, cores) as pool:
+        def step():
+            pick = np.sort(rng.choice(len(L), per_step, replace=False))
+            pool.two_pass(L[pick], E[pick], iv[pick], I, cfg["theta"])
 
-    def step():
-        pick = rng.choice(len(L), per_step, replace=False)
-        oracle.two_pass(s.types, s.t, L[pick], E[pick], iv[pick], I, cfg["theta"])
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    sec = time.perf_counter() - t0
+        for _ in range(args.warmup):
+            step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        sec = time.perf_counter() - t0
     value = per_step * s.n * args.steps / sec
     sample = (f"per step {per_step} random level-2 candidates of the 16,128, Algorithm 4 "
               f"(relaxed, eliminate below theta={cfg['theta']}, exact on survivors) over the "
-              f"full {s.n}-event stream; single-threaded C oracle")
+              f"full {s.n}-event stream; {cores} independent single-threaded C oracle "
+              f"processes over candidate shards")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded Poisson spike trains with embedded cascades)",
-        "config": {"workload": cfg["name"], "n_events": s.n, "n_types": s.n_types,
-                   "theta": cfg["theta"], "max_len": cfg["max_len"]},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "config": step_config(cfg, args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "cpu": model, "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

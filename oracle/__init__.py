@@ -301,7 +301,7 @@ def join(frequent, repeated_types=False):
 
 
 def mine(types, t, n_types, intervals, theta, max_len, two_pass_counting=True,
-         repeated_types=False):
+         repeated_types=False, counter=None):
     """Problem 1 (Section 2), level by level.
 
     Level 1: the count of a one-node episode is the number of events of its
@@ -311,6 +311,10 @@ def mine(types, t, n_types, intervals, theta, max_len, two_pass_counting=True,
     if ``two_pass_counting`` is False, with the exact pass alone.  An episode is
     frequent iff its exact count is >= theta.  With ``repeated_types`` a type may
     appear at several nodes (level 2 includes (a, a); the join keeps repeats).
+
+    ``counter``: an object with ``two_pass`` and ``count_batch`` methods taking
+    the arguments of the module functions minus the stream (``oracle.shards.
+    ShardPool``, the same counters run over candidate shards); None counts here.
 
     Returns {level: [(types tuple, interval-index tuple, count), ...]} with
     each level in canonical order; level 1 lists (type,), (), count.
@@ -326,10 +330,16 @@ def mine(types, t, n_types, intervals, theta, max_len, two_pass_counting=True,
     while cands and level <= max_len:
         lens, E, iv = _pack(cands)
         if two_pass_counting:
-            _, exact, sv = two_pass(types, t, lens, E, iv, intervals, theta)
+            if counter is None:
+                _, exact, sv = two_pass(types, t, lens, E, iv, intervals, theta)
+            else:
+                _, exact, sv = counter.two_pass(lens, E, iv, intervals, theta)
             keep = (sv != 0) & (exact >= theta)
         else:
-            exact = count_batch(types, t, lens, E, iv, intervals, EXACT)
+            if counter is None:
+                exact = count_batch(types, t, lens, E, iv, intervals, EXACT)
+            else:
+                exact = counter.count_batch(lens, E, iv, intervals, EXACT)
             keep = exact >= theta
         freq = [(cands[c][0], cands[c][1], int(exact[c])) for c in range(len(cands)) if keep[c]]
         if not freq:

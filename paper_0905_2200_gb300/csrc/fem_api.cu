@@ -36,6 +36,9 @@ struct DevBuf {
 
 struct fem_ctx {
     int device = 0;
+    // device memory the context holds for streams, working buffers and batches, and
+    // the caller's bound on it (0: none)
+    size_t mem_budget = 0, mem_used = 0;
     cudaStream_t own = nullptr;
     fem_config cfg{};
     int sm_count = 152;
@@ -98,20 +101,56 @@ void report_cuda(cudaError_t e, int line) {
 // d_small word assignment
 enum { W_COUNT0 = 0, W_COUNT1 = 1, W_COUNT2 = 2, W_INFO = 8 /* 2 words */ };
 
+size_t stream_bytes(const StreamDev &s) {
+    if (!s.t) return 0;
+    return s.cap_events * 5 + s.cap_chunks * CHUNK * 8 + (size_t)s.cap_offs * 2 +
+           (s.cap_chunks + 1) * 4 + 256 * 4;
+}
+
+void free_stream_buffers(StreamDev &s);
+
+// Room for `bytes` more under the context's memory budget: over budget, the buffers
+// kept from freed streams are released first; FEM_ENOMEM if it still does not fit.
+int reserve(fem_ctx *c, size_t bytes) {
+    if (!c->mem_budget) return FEM_OK;
+    while (c->mem_used + bytes > c->mem_budget && !c->pool.empty()) {
+        c->mem_used -= std::min(stream_bytes(c->pool.front()), c->mem_used);
+        free_stream_buffers(c->pool.front());
+        c->pool.erase(c->pool.begin());
+    }
+    return c->mem_used + bytes > c->mem_budget ? FEM_ENOMEM : FEM_OK;
+}
+
+// Device allocation charged to the context's memory budget.
+int cmalloc(fem_ctx *c, void **p, size_t bytes) {
+    *p = nullptr;
+    RET(reserve(c, bytes));
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return FEM_ENOMEM;
+    }
+    c->mem_used += bytes;
+    return FEM_OK;
+}
+
+void cfree(fem_ctx *c, void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    c->mem_used -= std::min(bytes, c->mem_used);
+}
+
 template <typename T>
 int dbuf(fem_ctx *c, const char *name, size_t count, T **out) {
     const size_t bytes = std::max<size_t>(count * sizeof(T), 256);
     DevBuf &b = c->bufs[name];
     if (b.cap < bytes) {
         size_t nb = std::max(bytes, (size_t)(b.cap * 3 / 2));
-        if (b.p) cudaFree(b.p);
+        cfree(c, b.p, b.cap);
         b.p = nullptr;
         b.cap = 0;
         nb = (nb + 4095) & ~(size_t)4095;
-        if (cudaMalloc(&b.p, nb) != cudaSuccess) {
-            cudaGetLastError();
-            return FEM_ENOMEM;
-        }
+        RET(cmalloc(c, &b.p, nb));
         b.cap = nb;
     }
     *out = static_cast<T *>(b.p);
@@ -571,6 +610,29 @@ void free_stream_buffers(StreamDev &s) {
     s = StreamDev{};
 }
 
+// Buffers for a stream of up to ne events in nc chunks (offs per chunk), charged to
+// the context's budget as one block.
+int alloc_stream(fem_ctx *c, StreamDev &s, size_t ne, size_t nc) {
+    StreamDev q;
+    q.cap_events = ne, q.cap_chunks = nc, q.cap_offs = (uint32_t)(nc * s.offs);
+    q.t = reinterpret_cast<uint32_t *>(1);  // stream_bytes of the capacities
+    const size_t bytes = stream_bytes(q);
+    RET(reserve(c, bytes));
+    s.cap_events = ne, s.cap_chunks = nc, s.cap_offs = q.cap_offs;
+    const bool ok = cudaMalloc(&s.t, ne * 4) == cudaSuccess && cudaMalloc(&s.type, ne) == cudaSuccess &&
+                    cudaMalloc(&s.bev, nc * CHUNK * 8) == cudaSuccess &&
+                    cudaMalloc(&s.boff, nc * s.offs * 2) == cudaSuccess &&
+                    cudaMalloc(&s.cfirst, (nc + 1) * 4) == cudaSuccess &&
+                    cudaMalloc(&s.hist, 256 * 4) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_stream_buffers(s);
+        return FEM_ENOMEM;
+    }
+    c->mem_used += bytes;
+    return FEM_OK;
+}
+
 }  // namespace
 
 // ============================================================================ C ABI
@@ -605,7 +667,7 @@ const char *fem_strerror(int s) {
     }
 }
 
-int fem_create(fem_ctx **out, int device) {
+int fem_create(fem_ctx **out, int device, size_t mem_budget_bytes) {
     if (!out) return FEM_EINVAL;
     *out = nullptr;
     int ndev = 0;
@@ -616,6 +678,7 @@ int fem_create(fem_ctx **out, int device) {
     fem_ctx *c = new (std::nothrow) fem_ctx;
     if (!c) return FEM_ENOMEM;
     c->device = device;
+    c->mem_budget = mem_budget_bytes;
     if (cudaSetDevice(device) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) !=
             cudaSuccess ||
@@ -761,20 +824,12 @@ int fem_load_stream(fem_ctx *c, const uint8_t *types, const uint32_t *t_us, uint
             break;
         }
     }
-    if (!okm) {
-        s.cap_events = nn, s.cap_chunks = nc, s.cap_offs = (uint32_t)(nc * s.offs);
-        okm = cudaMalloc(&s.t, nn * 4) == cudaSuccess && cudaMalloc(&s.type, nn) == cudaSuccess &&
-              cudaMalloc(&s.bev, nc * CHUNK * 8) == cudaSuccess &&
-              cudaMalloc(&s.boff, nc * s.offs * 2) == cudaSuccess &&
-              cudaMalloc(&s.cfirst, (nc + 1) * 4) == cudaSuccess &&
-              cudaMalloc(&s.hist, 256 * 4) == cudaSuccess;
-    }
-    auto release = [&] { free_stream_buffers(s); };
-    if (!okm) {
-        cudaGetLastError();
-        release();
-        return FEM_ENOMEM;
-    }
+    if (!okm) okm = alloc_stream(c, s, nn, nc) == FEM_OK;
+    auto release = [&] {
+        c->mem_used -= std::min(stream_bytes(s), c->mem_used);
+        free_stream_buffers(s);
+    };
+    if (!okm) return FEM_ENOMEM;
     int rc = FEM_OK;
     std::vector<uint32_t> hist_host;
     do {
@@ -829,6 +884,92 @@ int fem_load_stream(fem_ctx *c, const uint8_t *types, const uint32_t *t_us, uint
     return FEM_OK;
 }
 
+int fem_append_stream(fem_ctx *c, int32_t id, const uint8_t *types, const uint32_t *t_us,
+                      uint64_t n, int on_device, void *cuda_stream) {
+    if (!c || (n && (!types || !t_us))) return FEM_EINVAL;
+    auto it = c->streams.find(id);
+    if (it == c->streams.end()) return FEM_ENOSTREAM;
+    if (n == 0) return FEM_OK;
+    StreamDev &s = it->second;
+    const uint64_t n_old = s.n, n_new = s.n + n;
+    if (n_new >= 0xFFFFFFF0ull) return FEM_EINVAL;
+    cudaSetDevice(c->device);
+    cudaStream_t st = pick(c, cuda_stream);
+    const uint32_t ch_old = s.n_chunks, K = s.K, t_max_old = s.t_max;
+    const uint32_t ch_new = (uint32_t)((n_new + CHUNK - 1) / CHUNK);
+    if (n_new > s.cap_events || ch_new > s.cap_chunks || (uint64_t)ch_new * s.offs > s.cap_offs) {
+        // grow by half at least, keeping what is grouped already
+        StreamDev g;
+        g.offs = s.offs;
+        RET(alloc_stream(c, g, std::max<uint64_t>(n_new, s.cap_events * 3 / 2),
+                         std::max<uint64_t>(ch_new, s.cap_chunks * 3 / 2)));
+        bool ok = true;
+        if (n_old) {
+            ok = cudaMemcpyAsync(g.t, s.t, n_old * 4, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+                 cudaMemcpyAsync(g.type, s.type, n_old, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+                 cudaMemcpyAsync(g.bev, s.bev, (size_t)ch_old * CHUNK * 8, cudaMemcpyDeviceToDevice,
+                                 st) == cudaSuccess &&
+                 cudaMemcpyAsync(g.boff, s.boff, (size_t)ch_old * s.offs * 2,
+                                 cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+                 cudaMemcpyAsync(g.cfirst, s.cfirst, ((size_t)ch_old + 1) * 4,
+                                 cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+        }
+        ok = ok && cudaMemcpyAsync(g.hist, s.hist, 256 * 4, cudaMemcpyDeviceToDevice, st) ==
+                       cudaSuccess &&
+             cudaStreamSynchronize(st) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            c->mem_used -= std::min(stream_bytes(g), c->mem_used);
+            free_stream_buffers(g);
+            return FEM_ECUDA;
+        }
+        c->mem_used -= std::min(stream_bytes(s), c->mem_used);
+        free_stream_buffers(s);
+        g.n = n_old, g.K = K, g.n_chunks = ch_old, g.t_max = t_max_old;
+        s = g;
+    }
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemsetAsync(c->d_err, 0, 4, st));
+    CK(cudaMemcpyAsync(s.t + n_old, t_us, n * 4, kind, st));
+    CK(cudaMemcpyAsync(s.type + n_old, types, n, kind, st));
+    s.n = n_new;
+    s.n_chunks = ch_new;
+    // regroup from the chunk holding the old last event, so that the pair across the old
+    // end is checked with the new events
+    const uint32_t c0 = n_old ? (uint32_t)((n_old - 1) / CHUNK) : 0u;
+    CK(launch_bucket_chunks(s, c0, ch_new, st, c->d_err));
+    CK(launch_hist_add(s.type + n_old, n, s.K, +1, s.hist, st));
+    void *hp;
+    RET(pinbuf(c, 0, (2 + 256) * sizeof(uint32_t), st, &hp));
+    uint32_t *hw = static_cast<uint32_t *>(hp);
+    CK(cudaMemcpyAsync(hw, c->d_err, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hw + 1, s.t + (n_new - 1), 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hw + 2, s.hist, s.K * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int rc = err_status(hw[0]);
+    if (rc != FEM_OK) {
+        // undo: the old events' grouping, histogram and size
+        CK(launch_hist_add(s.type + n_old, n, s.K, -1, s.hist, st));
+        s.n = n_old;
+        s.n_chunks = ch_old;
+        if (n_old) CK(launch_bucket_chunks(s, c0, ch_old, st));
+        else CK(cudaMemsetAsync(s.cfirst, 0xFF, 8, st));
+        CK(cudaStreamSynchronize(st));
+        s.t_max = t_max_old;
+        return rc;
+    }
+    s.t_max = hw[1];
+    c->hist_h[id].assign(hw + 2, hw + 2 + s.K);
+    return FEM_OK;
+}
+
+int fem_mem_usage(fem_ctx *c, size_t *used_out, size_t *budget_out) {
+    if (!c) return FEM_EINVAL;
+    if (used_out) *used_out = c->mem_used;
+    if (budget_out) *budget_out = c->mem_budget;
+    return FEM_OK;
+}
+
 int fem_free_stream(fem_ctx *c, int32_t id) {
     if (!c) return FEM_EINVAL;
     auto it = c->streams.find(id);
@@ -841,6 +982,7 @@ int fem_free_stream(fem_ctx *c, int32_t id) {
     c->streams.erase(it);
     c->hist_h.erase(id);
     while (c->pool.size() > 4) {
+        c->mem_used -= std::min(stream_bytes(c->pool.front()), c->mem_used);
         free_stream_buffers(c->pool.front());
         c->pool.erase(c->pool.begin());
     }
@@ -1345,6 +1487,7 @@ struct fem_batch {
     std::vector<fem_job> jobs;
     std::vector<BatchGroup> groups;
     std::vector<void *> allocs;
+    std::vector<size_t> alloc_bytes;
     uint2 *ivl = nullptr;
     uint32_t nI = 0;
     cudaStream_t cap_stream = nullptr;
@@ -1358,11 +1501,10 @@ namespace {
 template <typename T>
 int balloc(fem_batch *b, size_t count, T **out) {
     void *p = nullptr;
-    if (cudaMalloc(&p, std::max<size_t>(count * sizeof(T), 256)) != cudaSuccess) {
-        cudaGetLastError();
-        return FEM_ENOMEM;
-    }
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 256);
+    RET(cmalloc(b->ctx, &p, bytes));
     b->allocs.push_back(p);
+    b->alloc_bytes.push_back(bytes);
     *out = static_cast<T *>(p);
     return FEM_OK;
 }
@@ -1371,7 +1513,7 @@ void batch_free(fem_batch *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    for (void *p : b->allocs) cudaFree(p);
+    for (size_t i = 0; i < b->allocs.size(); ++i) cfree(b->ctx, b->allocs[i], b->alloc_bytes[i]);
     delete b;
 }
 

@@ -176,8 +176,13 @@ void note_launch(uint32_t k = 1);
 // device memory, copying it into s.t / s.type on the way.
 cudaError_t launch_load_stream(StreamDev &s, cudaStream_t st, uint32_t *d_err,
                                const uint32_t *src_t = nullptr, const uint8_t *src_type = nullptr);
-// regroup chunks [c0, c1) of a stream that grew to s.n events (type histogram untouched)
-cudaError_t launch_bucket_chunks(StreamDev &s, uint32_t c0, uint32_t c1, cudaStream_t st);
+// regroup chunks [c0, c1) of a stream that grew to s.n events (type histogram untouched);
+// with d_err the chunks' events are also checked (types < K, times non-decreasing)
+cudaError_t launch_bucket_chunks(StreamDev &s, uint32_t c0, uint32_t c1, cudaStream_t st,
+                                 uint32_t *d_err = nullptr);
+// hist[ty[i]] += sign (+1 or -1) for i < n
+cudaError_t launch_hist_add(const uint8_t *ty, uint64_t n, uint32_t K, int sign, uint32_t *hist,
+                            cudaStream_t st);
 // dst[idx[i]] = src[i] and flags[idx[i]] = 1 for i < *m_dev (grid sized for m_max)
 cudaError_t launch_scatter_dev(const uint32_t *src, const uint32_t *idx, const uint32_t *m_dev,
                                uint32_t m_max, uint32_t *dst, uint8_t *flags, cudaStream_t st);
@@ -236,9 +241,15 @@ cudaError_t launch_touched(const fem_episode *cands, const uint32_t *gather, uin
 cudaError_t launch_compose_idx(const uint32_t *outer, const uint32_t *inner, uint32_t m,
                                uint32_t *dst, cudaStream_t st);
 // stable compaction: keep[i] = (vals[i] >= theta) (or flags[i] != 0 if vals == NULL)
+// block_scratch holds compact_scratch_words(m) words: one partial sum per block of
+// COMPACT_ITEMS_PER_BLOCK items plus a slack of 32
 cudaError_t launch_compact(const uint32_t *vals, const uint8_t *flags, uint32_t theta, uint32_t m,
                            uint32_t *idx_out, uint32_t *count_out, uint32_t *block_scratch,
                            cudaStream_t st);
+constexpr uint32_t COMPACT_ITEMS_PER_BLOCK = 1024;
+constexpr size_t compact_scratch_words_for(uint64_t m) {
+    return (size_t)((m + COMPACT_ITEMS_PER_BLOCK - 1) / COMPACT_ITEMS_PER_BLOCK) + 32;
+}
 size_t compact_scratch_words(uint32_t m);
 cudaError_t launch_gather_frequent(const fem_episode *cands, const uint32_t *surv,
                                    const uint32_t *idx, uint32_t f, const uint32_t *counts,

@@ -58,6 +58,7 @@ __device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *total) {
 constexpr uint32_t CT = 256;          // threads per compaction block
 constexpr uint32_t CI = 4;            // items per thread
 constexpr uint32_t CB = CT * CI;      // items per block
+static_assert(CB == COMPACT_ITEMS_PER_BLOCK, "compaction block size is declared in fem_internal.cuh");
 
 __device__ __forceinline__ bool keep_at(const uint32_t *vals, const uint8_t *flags, uint32_t theta,
                                         uint32_t i) {
@@ -325,7 +326,7 @@ cudaError_t launch_len_flags(const fem_episode *c, const uint32_t *gather, uint3
 }
 
 // ------------------------------------------------------------------ stable compaction
-size_t compact_scratch_words(uint32_t m) { return (m + CB - 1) / CB + 32; }
+size_t compact_scratch_words(uint32_t m) { return compact_scratch_words_for(m); }
 
 __global__ void __launch_bounds__(CT) k_keep_count(const uint32_t *vals, const uint8_t *flags,
                                                     uint32_t theta, uint32_t m,

@@ -6,6 +6,8 @@
 // and local index, plus the group offsets.  Within a group the events keep
 // stream order, so a thread that merges its episode's groups by local index
 // sees exactly the subsequence of the stream made of its episode's types.
+#include <algorithm>
+
 #include "fem_internal.cuh"
 
 namespace fem {
@@ -125,10 +127,34 @@ cudaError_t launch_load_stream(StreamDev &s, cudaStream_t st, uint32_t *d_err,
     return cudaGetLastError();
 }
 
-cudaError_t launch_bucket_chunks(StreamDev &s, uint32_t c0, uint32_t c1, cudaStream_t st) {
+cudaError_t launch_bucket_chunks(StreamDev &s, uint32_t c0, uint32_t c1, cudaStream_t st,
+                                 uint32_t *d_err) {
     if (c1 <= c0) return cudaSuccess;
     k_bucket<<<c1 - c0, 256, 0, st>>>(s.t, s.type, s.n, s.K, s.offs, s.n_chunks, s.bev, s.boff,
-                                      s.cfirst, nullptr, c0, nullptr, nullptr, nullptr);
+                                      s.cfirst, nullptr, c0, d_err, nullptr, nullptr);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// hist[ty[i]] += sign for the n events (types >= K are skipped: a load that holds
+// them fails and is undone)
+__global__ void __launch_bounds__(256) k_hist_add(const uint8_t *__restrict__ ty, uint64_t n,
+                                                  uint32_t K, int sign, uint32_t *hist) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint64_t i = (uint64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (uint64_t)gridDim.x * 256)
+        atomicAdd(&h[ty[i]], 1u);
+    __syncthreads();
+    const uint32_t v = h[threadIdx.x];
+    if (v && threadIdx.x < K) atomicAdd(&hist[threadIdx.x], sign > 0 ? v : 0u - v);
+}
+
+cudaError_t launch_hist_add(const uint8_t *ty, uint64_t n, uint32_t K, int sign, uint32_t *hist,
+                            cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    const uint64_t blocks = std::min<uint64_t>((n + 255) / 256, 1024);
+    k_hist_add<<<(uint32_t)blocks, 256, 0, st>>>(ty, n, K, sign, hist);
     note_launch();
     return cudaGetLastError();
 }

@@ -66,7 +66,7 @@ class fem_server_config(ctypes.Structure):
 
 REQ_ONESHOT, REQ_STANDING = 0, 1
 
-EXPORTS = ["fem_create", "fem_destroy", "fem_set_config", "fem_load_stream", "fem_free_stream",
+EXPORTS = ["fem_create", "fem_destroy", "fem_mem_usage", "fem_append_stream", "fem_set_config", "fem_load_stream", "fem_free_stream",
            "fem_type_counts", "fem_count_candidates", "fem_count_two_pass",
            "fem_mine_levelwise", "fem_result_level", "fem_result_max_level", "fem_result_free",
            "fem_last_mine_stats", "fem_strerror", "fem_kernel_launches", "fem_select_noalloc",
@@ -92,7 +92,9 @@ def load(path: str | None = None):
     vp, u32, i32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64
     I = ctypes.c_int
     sig = {
-        "fem_create": (I, [ctypes.POINTER(vp), I]),
+        "fem_create": (I, [ctypes.POINTER(vp), I, ctypes.c_size_t]),
+        "fem_mem_usage": (I, [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+        "fem_append_stream": (I, [vp, i32, vp, vp, u64, I, vp]),
         "fem_destroy": (I, [vp]),
         "fem_set_config": (I, [vp, ctypes.POINTER(fem_config)]),
         "fem_load_stream": (I, [vp, vp, vp, u64, u32, I, vp, ctypes.POINTER(i32)]),
@@ -206,11 +208,19 @@ def unpack_episodes(rec):
 
 
 # --------------------------------------------------------------------------- calls
-def fem_create(device: int = 0):
+def fem_create(device: int = 0, mem_budget_bytes: int = 0):
+    """A context on `device`; mem_budget_bytes bounds its device memory (0: no bound)."""
     lib = load()
     h = ctypes.c_void_p()
-    _check(lib.fem_create(ctypes.byref(h), int(device)), "fem_create")
+    _check(lib.fem_create(ctypes.byref(h), int(device), int(mem_budget_bytes)), "fem_create")
     return h
+
+
+def fem_mem_usage(ctx):
+    """(device bytes the context holds, its budget or 0)."""
+    used, budget = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(load().fem_mem_usage(ctx, ctypes.byref(used), ctypes.byref(budget)), "fem_mem_usage")
+    return int(used.value), int(budget.value)
 
 
 def fem_destroy(ctx):
@@ -290,6 +300,24 @@ def fem_load_stream(ctx, types, t_us, n_types, stream=None) -> int:
     _check(lib.fem_load_stream(ctx, pt, pu, n, int(n_types), dt, _stream_handle(stream),
                                ctypes.byref(sid)), "fem_load_stream")
     return sid.value
+
+
+def fem_append_stream(ctx, sid, types, t_us, stream=None):
+    """Append events (numpy host arrays or CUDA tensors) to a resident stream."""
+    lib = load()
+    if not _is_torch(types):
+        types = np.ascontiguousarray(types, dtype=np.uint8)
+    if not _is_torch(t_us):
+        t_us = np.ascontiguousarray(t_us, dtype=np.uint32)
+    pt, dt = _ptr(types)
+    pu, du = _ptr(t_us)
+    if dt != du:
+        raise ValueError("types and t_us must both be host or both be device")
+    n = int(types.shape[0])
+    if int(t_us.shape[0]) != n:
+        raise ValueError("types and t_us differ in length")
+    _check(lib.fem_append_stream(ctx, int(sid), pt, pu, n, dt, _stream_handle(stream)),
+           "fem_append_stream")
 
 
 def fem_free_stream(ctx, sid):
@@ -400,6 +428,15 @@ def fem_select_noalloc(values, theta, idx_out, count_out, stream=None):
     pc, dc = _ptr(count_out)
     if not (dv and di and dc):
         raise ValueError("values, idx_out and count_out must be device tensors")
+    for name, x in (("values", values), ("idx_out", idx_out), ("count_out", count_out)):
+        if x.element_size() != 4:
+            raise ValueError(f"{name} must hold 4-byte elements")
+    if idx_out.numel() < values.numel() or count_out.numel() < 1:
+        raise ValueError("idx_out needs values.numel() elements and count_out one")
+    import torch
+    cur = torch.cuda.current_device()
+    if any(x.device.index != cur for x in (values, idx_out, count_out)):
+        raise ValueError("values, idx_out and count_out must be on the current CUDA device")
     _check(load().fem_select_noalloc(pv, int(values.shape[0]), int(theta), pi, pc,
                                      _stream_handle(stream)), "fem_select_noalloc")
 
@@ -508,8 +545,8 @@ def fem_strerror(status: int) -> str:
 class Context:
     """Small convenience owner of a context (destroyed on close/exit)."""
 
-    def __init__(self, device=0):
-        self.h = fem_create(device)
+    def __init__(self, device=0, mem_budget_bytes=0):
+        self.h = fem_create(device, mem_budget_bytes)
 
     def close(self):
         if self.h:

@@ -288,3 +288,15 @@ def serving_requests(seed, rate_per_s, duration_s, n_streams, stream_types, m_ra
                          seed=int(rng.integers(0, 2**31)), K=stream_types[sidx], lens=lens))
     return reqs
 
+
+
+def digest(*arrays) -> str:
+    """SHA-256 over the bytes of the given arrays (shapes and dtypes included), so that
+    a stored expected result can name the exact inputs it was computed from."""
+    import hashlib
+    h = hashlib.sha256()
+    for a in arrays:
+        a = np.ascontiguousarray(a)
+        h.update(str((a.dtype.str, a.shape)).encode())
+        h.update(a.tobytes())
+    return h.hexdigest()
