@@ -71,9 +71,14 @@ struct fem_ctx {
     struct Shape {
         uint32_t P, T;
         float ms;
+        uint32_t kernel;  // FEM_KERNEL_MACHINE or FEM_KERNEL_CHAIN
     };
     std::map<std::string, Shape> tune;
     bool tune_on = false, tuning = false;
+    // the candidate set being counted comes in runs of shared prefixes (mining's sets
+    // always do; count_any measures it): where it does not, the latest-chain kernels
+    // would find few prefixes to share
+    bool clustered = true;
     cudaEvent_t tev[2] = {nullptr, nullptr};
 };
 
@@ -99,7 +104,7 @@ void report_cuda(cudaError_t e, int line) {
     } while (0)
 
 // d_small word assignment
-enum { W_COUNT0 = 0, W_COUNT1 = 1, W_COUNT2 = 2, W_INFO = 8 /* 2 words */ };
+enum { W_COUNT0 = 0, W_COUNT1 = 1, W_COUNT2 = 2, W_INFO = 8 /* 3 words */ };
 
 size_t stream_bytes(const StreamDev &s) {
     if (!s.t) return 0;
@@ -288,6 +293,14 @@ uint32_t ceil_log2(uint64_t v) {
     return r;
 }
 
+// The latest-chain kernels count distinct-type episodes of 2..8 nodes.
+bool chain_eligible(const fem_ctx *c, int N, bool distinct) {
+    return distinct && N >= 2 && N <= FEM_MAX_LEN && c->clustered;
+}
+
+// Block size of the latest-chain kernels: 256 threads, smaller blocks for few episodes.
+uint32_t chain_threads(uint32_t m) { return m > 128 ? 256u : m > 64 ? 128u : m > 32 ? 64u : 32u; }
+
 // The class a measured launch shape is kept for: counts of the same length,
 // pass and type structure, with m and the stream length in the same power-of-two
 // range and the same type count, map alike.
@@ -316,15 +329,30 @@ int tune_pass(fem_ctx *c, const std::string &key, const StreamDev &s, const fem_
         if (P0 * 2 <= s.n_chunks) Ps.push_back(P0 * 2);
     }
     const uint32_t R0 = pass == FEM_PASS_EXACT ? (c->cfg.ring_capacity ? c->cfg.ring_capacity : 8) : 1;
-    // the shapes to time: per segment count the rule's block size and its neighbours
+    // the shapes to time: per segment count and kernel the rule's block size and its
+    // neighbours; the rule's own shape first
+    const bool chain = chain_eligible(c, N, distinct);
+    const uint32_t k0 = c->cfg.kernel ? c->cfg.kernel : (chain ? FEM_KERNEL_CHAIN : FEM_KERNEL_MACHINE);
     std::vector<fem_ctx::Shape> shapes;
-    for (uint32_t P : Ps) {
-        const uint32_t R = (P > 1 && R0 > 32) ? 32 : R0;
-        const uint32_t T0 = choose_threads(c, N, pass, P > 1, R, s.offs, m);
-        shapes.push_back(fem_ctx::Shape{P, T0, -1.f});
-        for (uint32_t T : {128u, 256u})
-            if (T != T0 && m > T / 2 && count_smem_bytes(N, pass, P > 1, R, T, s.offs) <= 100 * 1024)
-                shapes.push_back(fem_ctx::Shape{P, T, -1.f});
+    for (uint32_t kind : {k0, k0 == FEM_KERNEL_CHAIN ? (uint32_t)FEM_KERNEL_MACHINE : (uint32_t)FEM_KERNEL_CHAIN}) {
+        if (kind == FEM_KERNEL_CHAIN && !chain) continue;
+        if (c->cfg.kernel && kind != c->cfg.kernel) continue;
+        for (uint32_t P : Ps) {
+            if (kind == FEM_KERNEL_CHAIN) {
+                const uint32_t T0 = chain_threads(m);
+                shapes.push_back(fem_ctx::Shape{P, T0, -1.f, kind});
+                for (uint32_t T : {128u, 256u})
+                    if (T != T0 && m > T / 2 && chain_smem_bytes(N, P > 1, T, s.offs) <= 200 * 1024)
+                        shapes.push_back(fem_ctx::Shape{P, T, -1.f, kind});
+                continue;
+            }
+            const uint32_t R = (P > 1 && R0 > 32) ? 32 : R0;
+            const uint32_t T0 = choose_threads(c, N, pass, P > 1, R, s.offs, m);
+            shapes.push_back(fem_ctx::Shape{P, T0, -1.f, kind});
+            for (uint32_t T : {128u, 256u})
+                if (T != T0 && m > T / 2 && count_smem_bytes(N, pass, P > 1, R, T, s.offs) <= 100 * 1024)
+                    shapes.push_back(fem_ctx::Shape{P, T, -1.f, kind});
+        }
     }
     const fem_config saved = c->cfg;
     c->tuning = true;
@@ -336,6 +364,7 @@ int tune_pass(fem_ctx *c, const std::string &key, const StreamDev &s, const fem_
         for (fem_ctx::Shape &sh : shapes) {
             c->cfg.segments = sh.P;
             c->cfg.threads_per_block = sh.T;
+            c->cfg.kernel = sh.kernel;
             cudaEventRecord(c->tev[0], st);
             rc = count_pass(c, s, cands, gather, m, N, d_ivl, nI, pass, out, distinct, st, nullptr);
             cudaEventRecord(c->tev[1], st);
@@ -350,7 +379,7 @@ int tune_pass(fem_ctx *c, const std::string &key, const StreamDev &s, const fem_
         }
     }
     // the rule's shape (the first) stays unless another is at least 2% faster
-    fem_ctx::Shape best{0, 0, 0};
+    fem_ctx::Shape best{0, 0, 0, 0};
     if (rc == FEM_OK && !shapes.empty()) {
         best = shapes[0];
         for (const fem_ctx::Shape &sh : shapes)
@@ -380,16 +409,19 @@ int count_launch(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const
     pl->N = N, pl->pass = pass, pl->distinct = distinct;
     if (m == 0) return FEM_OK;
     // a measured shape for this class, if any (explicit configuration wins)
-    uint32_t P_t = 0, T_t = 0;
-    if (!c->cfg.segments && !c->cfg.threads_per_block && !c->tuning) {
+    uint32_t P_t = 0, T_t = 0, K_t = 0;
+    if (!c->cfg.segments && !c->cfg.threads_per_block && !c->cfg.kernel && !c->tuning) {
         const std::string key = tune_key(N, pass, distinct, m, s.n_chunks, s.K);
         auto it = c->tune.find(key);
         if (it == c->tune.end() && c->tune_on) {
             RET(tune_pass(c, key, s, cands, gather, m, N, d_ivl, nI, pass, out, distinct, st));
             it = c->tune.find(key);
         }
-        if (it != c->tune.end()) P_t = it->second.P, T_t = it->second.T;
+        if (it != c->tune.end()) P_t = it->second.P, T_t = it->second.T, K_t = it->second.kernel;
     }
+    uint32_t kind = c->cfg.kernel ? c->cfg.kernel : K_t;
+    if (!kind) kind = chain_eligible(c, N, distinct) ? FEM_KERNEL_CHAIN : FEM_KERNEL_MACHINE;
+    if (kind == FEM_KERNEL_CHAIN && !chain_eligible(c, N, distinct)) kind = FEM_KERNEL_MACHINE;
     CountParams p{};
     p.bev = s.bev;
     p.boff = s.boff;
@@ -425,13 +457,19 @@ int count_launch(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const
     if (P > 1) {
         RET(dbuf(c, "tables", (size_t)P * m * S_MAX, &p.tables));
     }
-    uint32_t T = choose_threads(c, N, pass, P > 1, R, s.offs, m);
-    if (T_t && count_smem_bytes(N, pass, P > 1, R, T_t, s.offs) <= 100 * 1024) T = T_t;
-    // a configured block size whose rings would not fit in shared memory is replaced
-    if (count_smem_bytes(N, pass, P > 1, R, T, s.offs) > 200 * 1024)
-        T = auto_threads(N, pass, P > 1, R, s.offs, m);
     CK(cudaEventRecord(c->kev[0], st));
-    CK(launch_count(N, pass, P > 1, R, T, p, st));
+    if (kind == FEM_KERNEL_CHAIN) {
+        uint32_t T = c->cfg.threads_per_block ? c->cfg.threads_per_block : (T_t ? T_t : chain_threads(m));
+        if (chain_smem_bytes(N, P > 1, T, s.offs) > 200 * 1024) T = 128;
+        CK(launch_chain(N, pass, P > 1, T, p, st));
+    } else {
+        uint32_t T = choose_threads(c, N, pass, P > 1, R, s.offs, m);
+        if (T_t && count_smem_bytes(N, pass, P > 1, R, T_t, s.offs) <= 100 * 1024) T = T_t;
+        // a configured block size whose rings would not fit in shared memory is replaced
+        if (count_smem_bytes(N, pass, P > 1, R, T, s.offs) > 200 * 1024)
+            T = auto_threads(N, pass, P > 1, R, s.offs, m);
+        CK(launch_count(N, pass, P > 1, R, T, p, st));
+    }
     CK(cudaEventRecord(c->kev[1], st));
     if (P > 1) CK(launch_stitch(p.tables, m, P, out, redo, c->d_err, st));
     CK(cudaEventRecord(c->kev[2], st));
@@ -545,13 +583,20 @@ int count_any(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const ui
               uint32_t m, const uint2 *d_ivl, uint32_t nI, int pass, uint32_t *out,
               cudaStream_t st) {
     if (m == 0) return FEM_OK;
-    CK(cudaMemsetAsync(c->d_small + W_INFO, 0, 2 * sizeof(uint32_t), st));
+    CK(cudaMemsetAsync(c->d_small + W_INFO, 0, 3 * sizeof(uint32_t), st));
     CK(launch_validate_cands(cands, gather, m, s.K, nI, c->d_small + W_INFO, c->d_err, st));
-    uint32_t info[2], e;
-    RET(read_words(c, c->d_small + W_INFO, 2, info, st));
+    uint32_t info[3], e;
+    RET(read_words(c, c->d_small + W_INFO, 3, info, st));
     RET(read_err(c, st, &e));
     RET(err_status(e));
     const uint32_t lens = info[0];
+    // runs of shared prefixes at least four candidates long on average
+    struct Clustered {
+        fem_ctx *c;
+        bool saved;
+        ~Clustered() { c->clustered = saved; }
+    } restore{c, c->clustered};
+    c->clustered = (uint64_t)m >= 4ull * ((uint64_t)info[2] + 1);
     if (info[1] && info[1] < m) {
         // distinct-type and repeated-type episodes mixed: count each part on its own
         // (repeated types run with one segment), then put the counts back in place
@@ -743,6 +788,7 @@ int fem_set_config(fem_ctx *c, const fem_config *cfg) {
         return FEM_EINVAL;
     if (cfg->ring_capacity && !count_config_supported(2, FEM_PASS_EXACT, false, cfg->ring_capacity))
         return FEM_EINVAL;
+    if (cfg->kernel > FEM_KERNEL_CHAIN) return FEM_EINVAL;
     c->cfg = *cfg;
     return FEM_OK;
 }
@@ -766,8 +812,10 @@ int fem_tune_save(fem_ctx *c, const char *path) {
     FILE *f = std::fopen(path, "w");
     if (!f) return FEM_EIO;
     for (const auto &kv : c->tune)
-        std::fprintf(f, "{\"key\": \"%s\", \"segments\": %u, \"threads\": %u, \"ms\": %.6f}\n",
-                     kv.first.c_str(), kv.second.P, kv.second.T, kv.second.ms);
+        std::fprintf(f,
+                     "{\"key\": \"%s\", \"segments\": %u, \"threads\": %u, \"ms\": %.6f, "
+                     "\"kernel\": %u}\n",
+                     kv.first.c_str(), kv.second.P, kv.second.T, kv.second.ms, kv.second.kernel);
     const bool ok = std::fclose(f) == 0;
     return ok ? FEM_OK : FEM_EIO;
 }
@@ -782,15 +830,24 @@ int fem_tune_load(fem_ctx *c, const char *path) {
     while (std::fgets(line, sizeof(line), f)) {
         if (line[0] == '\n' || line[0] == 0) continue;
         char key[96];
-        unsigned P = 0, T = 0;
+        unsigned P = 0, T = 0, K = FEM_KERNEL_MACHINE;
         float ms = 0;
-        if (std::sscanf(line, " {\"key\": \"%95[0-9/]\", \"segments\": %u, \"threads\": %u, \"ms\": %f}",
-                        key, &P, &T, &ms) != 4 ||
-            P == 0 || T == 0 || T > 256 || T % 8 != 0) {
+        char close = 0;
+        const int nf = std::sscanf(
+            line, " {\"key\": \"%95[0-9/]\", \"segments\": %u, \"threads\": %u, \"ms\": %f%c",
+            key, &P, &T, &ms, &close);
+        bool good = nf == 5 && P != 0 && T != 0 && T <= 256 && T % 8 == 0;
+        if (good && close == ',') {  // with the kernel field
+            good = std::sscanf(std::strstr(line, "\"ms\""), "\"ms\": %*f, \"kernel\": %u}", &K) == 1 &&
+                   (K == FEM_KERNEL_MACHINE || K == FEM_KERNEL_CHAIN);
+        } else if (good) {
+            good = close == '}';
+        }
+        if (!good) {
             rc = FEM_EINVAL;
             break;
         }
-        got[key] = fem_ctx::Shape{P, T, ms};
+        got[key] = fem_ctx::Shape{P, T, ms, K};
     }
     std::fclose(f);
     if (rc != FEM_OK) return rc;
@@ -1055,10 +1112,10 @@ int fem_count_mapconcat_literal(fem_ctx *c, int32_t id, const fem_episode *cands
     uint32_t *dout = counts_out;
     if (!counts_on_device) RET(dbuf(c, "counts_out", m, &dout));
     // the printed scheme needs distinct types (as the exact MapConcatenate does)
-    CK(cudaMemsetAsync(c->d_small + W_INFO, 0, 2 * sizeof(uint32_t), st));
+    CK(cudaMemsetAsync(c->d_small + W_INFO, 0, 3 * sizeof(uint32_t), st));
     CK(launch_validate_cands(dc, nullptr, m, s->K, nI, c->d_small + W_INFO, c->d_err, st));
-    uint32_t info[2], e;
-    RET(read_words(c, c->d_small + W_INFO, 2, info, st));
+    uint32_t info[3], e;
+    RET(read_words(c, c->d_small + W_INFO, 3, info, st));
     RET(read_err(c, st, &e));
     RET(err_status(e));
     if (info[1]) return FEM_EINVAL;
@@ -1136,10 +1193,10 @@ int fem_count_windows(fem_ctx *c, int32_t id, const fem_episode *cands, uint32_t
     }
     uint64_t *dout = counts_out;
     if (!counts_on_device) RET(dbuf(c, "win_out", m, &dout));
-    CK(cudaMemsetAsync(c->d_small + W_INFO, 0, 2 * sizeof(uint32_t), st));
+    CK(cudaMemsetAsync(c->d_small + W_INFO, 0, 3 * sizeof(uint32_t), st));
     CK(launch_validate_cands(dc, nullptr, m, s->K, nI, c->d_small + W_INFO, c->d_err, st));
-    uint32_t info[2], e;
-    RET(read_words(c, c->d_small + W_INFO, 2, info, st));
+    uint32_t info[3], e;
+    RET(read_words(c, c->d_small + W_INFO, 3, info, st));
     RET(read_err(c, st, &e));
     RET(err_status(e));
     if (info[1]) return FEM_EINVAL;  // distinct types only

@@ -202,6 +202,11 @@ cudaError_t launch_count_batch(int N, int pass, uint32_t ring_cap, uint32_t thre
                                const uint32_t *n_items, uint32_t *queue, uint32_t SB,
                                int sm_count, cudaStream_t st);
 cudaError_t count_set_smem_limits();
+// fem_chain_*.cu: the same passes in latest-chain form (distinct types, lengths 2..8,
+// one segment or MapConcatenate; candidates sharing prefixes share their lists)
+cudaError_t launch_chain(int N, int pass, bool mc, uint32_t threads, const CountParams &p,
+                         cudaStream_t st);
+size_t chain_smem_bytes(int N, bool mc, uint32_t threads, uint32_t offs);
 // fem_windows.cu: window-based frequency, one thread per episode (distinct types)
 struct WindowParams {
     const uint2 *bev;
@@ -229,7 +234,9 @@ cudaError_t launch_stitch_batch(const CountParams *jobs, const uint32_t *job_bas
 cudaError_t launch_stitch(const uint4 *tables, uint32_t m, uint32_t P, uint32_t *out,
                           uint8_t *redo, uint32_t *err, cudaStream_t st,
                           uint32_t classes = S_MAX);
-// info[0] |= 1 << len of every candidate; info[1] += candidates with a repeated type
+// info[0] |= 1 << len of every candidate; info[1] += candidates with a repeated type;
+// info[2] += candidates whose length or prefix before the last node differs from the
+// previous candidate's (the number of prefix runs is info[2] + 1)
 cudaError_t launch_validate_cands(const fem_episode *c, const uint32_t *gather, uint32_t m,
                                   uint32_t K, uint32_t n_ivl, uint32_t *info, uint32_t *err,
                                   cudaStream_t st);

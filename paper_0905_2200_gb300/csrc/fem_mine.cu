@@ -255,10 +255,17 @@ __global__ void k_validate_cands(const fem_episode *__restrict__ c, const uint32
                                  uint32_t m, uint32_t K, uint32_t n_ivl, uint32_t *info,
                                  uint32_t *err) {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t lenbit = 0, rep = 0, bad = 0;
+    uint32_t lenbit = 0, rep = 0, bad = 0, brk = 0;
     if (i < m) {
         const fem_episode e = ld_ep(c, gather ? gather[i] : i);
         const uint32_t N = e.len;
+        // a run of candidates sharing the prefix that a last node extends ends here
+        if (i > 0) {
+            const fem_episode q = ld_ep(c, gather ? gather[i - 1] : i - 1);
+            brk = q.len != N;
+            for (uint32_t k = 0; k + 1 < N && k < FEM_MAX_LEN; ++k) brk |= q.types[k] != e.types[k];
+            for (uint32_t k = 0; k + 2 < N && k < FEM_MAX_LEN - 1; ++k) brk |= q.ivl[k] != e.ivl[k];
+        }
         if (N < 1 || N > FEM_MAX_LEN) {
             bad = ERR_BADEP;
         } else {
@@ -275,9 +282,11 @@ __global__ void k_validate_cands(const fem_episode *__restrict__ c, const uint32
     lenbit = __reduce_or_sync(0xffffffffu, lenbit);
     rep = __reduce_add_sync(0xffffffffu, rep);
     bad = __reduce_or_sync(0xffffffffu, bad);
+    brk = __reduce_add_sync(0xffffffffu, brk);
     if ((threadIdx.x & 31) == 0) {
         if (lenbit) atomicOr(&info[0], lenbit);
         if (rep) atomicAdd(&info[1], rep);
+        if (brk) atomicAdd(&info[2], brk);
         if (bad) atomicOr(err, bad);
     }
 }

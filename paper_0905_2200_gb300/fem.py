@@ -39,7 +39,10 @@ class fem_interval(ctypes.Structure):
 
 class fem_config(ctypes.Structure):
     _fields_ = [("segments", ctypes.c_uint32), ("threads_per_block", ctypes.c_uint32),
-                ("ring_capacity", ctypes.c_uint32)]
+                ("ring_capacity", ctypes.c_uint32), ("kernel", ctypes.c_uint32)]
+
+
+KERNEL_AUTO, KERNEL_MACHINE, KERNEL_CHAIN = 0, 1, 2
 
 
 class fem_level_stats(ctypes.Structure):
@@ -227,12 +230,13 @@ def fem_destroy(ctx):
     _check(load().fem_destroy(ctx), "fem_destroy")
 
 
-def fem_set_config(ctx, segments=0, threads_per_block=0, ring_capacity=0, reset=False):
+def fem_set_config(ctx, segments=0, threads_per_block=0, ring_capacity=0, kernel=KERNEL_AUTO,
+                   reset=False):
     lib = load()
     if reset:
         _check(lib.fem_set_config(ctx, None), "fem_set_config")
         return
-    cfg = fem_config(int(segments), int(threads_per_block), int(ring_capacity))
+    cfg = fem_config(int(segments), int(threads_per_block), int(ring_capacity), int(kernel))
     _check(lib.fem_set_config(ctx, ctypes.byref(cfg)), "fem_set_config")
 
 
