@@ -724,9 +724,12 @@ def run_windows(args, rank, world, local):
 def run_serving(args, rank, world, local):
     """32 live streams appended in 100 ms chunks at real-time pace after a 60 s
     resident history; Poisson-arriving requests (one-shot over the last 60 s, or
-    standing) admitted by memory and slots, retried while they wait.  Reports p50/p99
-    latency (one-shot: arrival -> result; standing: chunk append -> updated counts)
-    beside throughput."""
+    standing) admitted by memory and slots, retried while they wait.  Per offered load
+    (--req-rates): p50/p99 latency (one-shot: arrival -> result; standing: chunk append
+    -> updated counts) and sustained throughput.  Then the same one-shot requests at
+    saturation: all submitted at once to the server (continuous batching over its lanes)
+    against the plain path (one fem_count_two_pass call after another on the same
+    windows), with identical results required."""
     import torch
 
     from paper_0905_2200_gb300 import build as fembuild
@@ -734,130 +737,202 @@ def run_serving(args, rank, world, local):
 
     fembuild.build()
     torch.cuda.set_device(local)
-    hist_s, sess, tick = 60.0, args.session_s, 0.1
+    hist_s, sess, tick, win_s = 60.0, args.session_s, 0.1, 60.0
+    rates = [float(x) for x in args.req_rates.split(",")]
     streams = synth.serving_streams(seed=0xFE05 + rank, n_streams=32, duration_s=hist_s + sess)
     types_of = [x["stream"].n_types for x in streams]
-    reqs = synth.serving_requests(0xFE05 + 17 * rank, args.req_rate, sess, 32, types_of)
     I = synth.I_MS4
-    for r in reqs:
-        L, E, iv = synth.random_candidates(r["seed"], r["m"], r["K"], list(r["lens"]), len(I))
-        r["rec"] = fem.pack_episodes(L, E, iv)
-        rate = streams[r["stream"]]["rate"]
-        r["theta"] = synth.chance_theta(rate, 60.0, 0.002)
     ctx = fem.fem_create(local)
-    srv = fem.fem_server_create(ctx, mem_budget_bytes=args.serve_budget_gb << 30, max_active=64,
-                                n_lanes=8)
-    sids, edges = [], []
+
+    def make_requests(rate, seed):
+        reqs = synth.serving_requests(seed, rate, sess, 32, types_of)
+        for r in reqs:
+            L, E, iv = synth.random_candidates(r["seed"], r["m"], r["K"], list(r["lens"]), len(I))
+            r["rec"] = fem.pack_episodes(L, E, iv)
+            r["theta"] = synth.chance_theta(streams[r["stream"]]["rate"], win_s, 0.002)
+        return reqs
+
+    def session(reqs):
+        srv = fem.fem_server_create(ctx, mem_budget_bytes=args.serve_budget_gb << 30,
+                                    max_active=64, n_lanes=8)
+        sids, edges = [], []
+        for x in streams:
+            s = x["stream"]
+            sids.append(fem.fem_server_open_stream(srv, s.n_types, s.n + 16))
+            edges.append(np.searchsorted(s.t, np.arange(0, hist_s + sess + tick, tick) * 1e6))
+            h = int(np.searchsorted(s.t, hist_s * 1e6))
+            fem.fem_server_append(srv, sids[-1], s.types[:h], s.t[:h])
+        fem.fem_server_drain(srv)
+        n_fed = [int(np.searchsorted(x["stream"].t, hist_s * 1e6)) for x in streams]
+        append_log = [[(n_fed[i], 0.0)] for i in range(32)]  # (events after append, wall time)
+        st = dict(pending=[], live={}, lat_one=[], lat_stand=[], units=0.0, rejected=0,
+                  admitted=0, retries=0, nxt=0)
+        k0 = int(round(hist_s / tick))
+        n_ticks = int(round(sess / tick))
+        t0 = time.perf_counter()
+
+        def poll(now):
+            for rid in fem.fem_server_poll(srv):
+                info = st["live"][rid]
+                c, f, ev, status = fem.fem_server_result(srv, rid, info["m"])
+                if info["standing"]:
+                    end = info["first"] + ev
+                    if ev and end > info["seen"]:
+                        log = append_log[info["stream"]]
+                        w = next((wt for n, wt in log if n >= end), log[-1][1])
+                        st["lat_stand"].append(now - w)
+                        st["units"] += float(info["m"]) * (end - info["seen"])
+                        info["seen"] = end
+                else:
+                    st["lat_one"].append(now - info["arrival"])
+                    st["units"] += float(info["m"]) * ev
+                    fem.fem_server_release(srv, rid)
+
+        def admit_pending():
+            now = time.perf_counter()
+            while st["nxt"] < len(reqs) and t0 + reqs[st["nxt"]]["t"] <= now:
+                r = reqs[st["nxt"]]
+                r["arrival"] = t0 + r["t"]
+                st["pending"].append(r)
+                st["nxt"] += 1
+            still = []
+            for r in st["pending"]:
+                mode = fem.REQ_STANDING if r["standing"] else fem.REQ_ONESHOT
+                try:
+                    rid = fem.fem_server_submit(srv, sids[r["stream"]], r["rec"], I, r["theta"],
+                                                mode, int(win_s * 1e6))
+                except fem.FemError as e:
+                    if e.status != -6:
+                        raise
+                    st["retries"] += 1
+                    if time.perf_counter() - r["arrival"] > 5.0:
+                        st["rejected"] += 1
+                    else:
+                        still.append(r)
+                    continue
+                st["admitted"] += 1
+                st["live"][rid] = dict(m=r["m"], standing=r["standing"], arrival=r["arrival"],
+                                       stream=r["stream"], first=n_fed[r["stream"]],
+                                       seen=n_fed[r["stream"]])
+            st["pending"] = still
+
+        for k in range(n_ticks):
+            due = t0 + k * tick
+            while time.perf_counter() < due:
+                admit_pending()
+                poll(time.perf_counter())
+                time.sleep(0.0002)
+            for i in range(32):
+                a, b2 = int(edges[i][k0 + k]), int(edges[i][k0 + k + 1])
+                if b2 > a:
+                    s = streams[i]["stream"]
+                    fem.fem_server_append(srv, sids[i], s.types[a:b2], s.t[a:b2])
+                    n_fed[i] = b2
+                    append_log[i].append((b2, time.perf_counter()))
+            admit_pending()
+            poll(time.perf_counter())
+        while time.perf_counter() < t0 + n_ticks * tick:
+            admit_pending()
+            poll(time.perf_counter())
+        wall = time.perf_counter() - t0
+        fem.fem_server_drain(srv)
+        poll(time.perf_counter())
+        fem.fem_server_destroy(srv)
+
+        def pct(xs, q):
+            return float(np.percentile(np.asarray(xs) * 1e3, q)) if xs else None
+
+        return {"offered_req_per_s": len(reqs) / sess, "requests": len(reqs),
+                "value": st["units"] / wall,
+                "oneshot_p50_ms": pct(st["lat_one"], 50), "oneshot_p99_ms": pct(st["lat_one"], 99),
+                "standing_update_p50_ms": pct(st["lat_stand"], 50),
+                "standing_update_p99_ms": pct(st["lat_stand"], 99),
+                "oneshot_done": len(st["lat_one"]), "standing_updates": len(st["lat_stand"]),
+                "admitted": st["admitted"], "admission_retries": st["retries"],
+                "rejected_after_5s": st["rejected"]}
+
+    all_reqs = {rate: make_requests(rate, 0xFE05 + 17 * rank + int(rate * 1000)) for rate in rates}
+    clocks = ClockSampler(local)
+    clocks.start()
+    sweep = [session(all_reqs[rate]) for rate in rates]
+
+    # saturation: the one-shot requests of the busiest load over the full streams' last
+    # 60 s, all at once through the server, then one after another through the plain path
+    oneshots = [r for r in all_reqs[max(rates)] if not r["standing"]]
+    win = []
+    for x in streams:
+        s = x["stream"]
+        b2 = s.n
+        a = int(np.searchsorted(s.t, int(s.t[-1]) - int(win_s * 1e6)))
+        win.append((a, b2))
+    srv = fem.fem_server_create(ctx, mem_budget_bytes=args.serve_budget_gb << 30,
+                                max_active=max(64, len(oneshots)), n_lanes=8)
+    sids = []
     for x in streams:
         s = x["stream"]
         sids.append(fem.fem_server_open_stream(srv, s.n_types, s.n + 16))
-        b = np.searchsorted(s.t, np.arange(0, hist_s + sess + tick, tick) * 1e6)
-        edges.append(b)
-        h = int(np.searchsorted(s.t, hist_s * 1e6))
-        fem.fem_server_append(srv, sids[-1], s.types[:h], s.t[:h])
+        fem.fem_server_append(srv, sids[-1], s.types, s.t)
     fem.fem_server_drain(srv)
-    n_fed = [int(np.searchsorted(x["stream"].t, hist_s * 1e6)) for x in streams]
-    append_log = [[(n_fed[i], 0.0)] for i in range(32)]  # (events after append, wall time)
-    pending, live = [], {}
-    lat_one, lat_stand, units = [], [], 0.0
-    rejected_final, admitted, retries = 0, 0, 0
-    nxt = 0
-    k0 = int(round(hist_s / tick))
-    n_ticks = int(round(sess / tick))
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-
-    def poll(now):
-        nonlocal units
-        for rid in fem.fem_server_poll(srv):
-            info = live[rid]
-            c, f, ev, st = fem.fem_server_result(srv, rid, info["m"])
-            if info["standing"]:
-                end = info["first"] + ev
-                if ev and end > info["seen"]:
-                    log = append_log[info["stream"]]
-                    w = next((wt for n, wt in log if n >= end), log[-1][1])
-                    lat_stand.append(now - w)
-                    units += float(info["m"]) * (end - info["seen"])
-                    info["seen"] = end
-            else:
-                lat_one.append(now - info["arrival"])
-                units += float(info["m"]) * ev
-                fem.fem_server_release(srv, rid)
-
-    def admit_pending():
-        nonlocal pending, nxt, retries, rejected_final, admitted
-        now = time.perf_counter()
-        while nxt < len(reqs) and t0 + reqs[nxt]["t"] <= now:
-            r = reqs[nxt]
-            r["arrival"] = t0 + r["t"]
-            pending.append(r)
-            nxt += 1
-        still = []
-        for r in pending:
-            mode = fem.REQ_STANDING if r["standing"] else fem.REQ_ONESHOT
+    rids = []
+    for r in oneshots:
+        while True:
             try:
-                rid = fem.fem_server_submit(srv, sids[r["stream"]], r["rec"], I, r["theta"], mode,
-                                            60_000_000)
-            except fem.FemError as e:
+                rids.append(fem.fem_server_submit(srv, sids[r["stream"]], r["rec"], I, r["theta"],
+                                                  fem.REQ_ONESHOT, int(win_s * 1e6)))
+                break
+            except fem.FemError as e:  # memory or slots full: wait for work to finish
                 if e.status != -6:
                     raise
-                retries += 1
-                if time.perf_counter() - r["arrival"] > 5.0:
-                    rejected_final += 1
-                else:
-                    still.append(r)
-                continue
-            admitted += 1
-            live[rid] = dict(m=r["m"], standing=r["standing"], arrival=r["arrival"],
-                             stream=r["stream"], first=n_fed[r["stream"]], seen=n_fed[r["stream"]])
-        pending = still
-
-    for k in range(n_ticks):
-        due = t0 + k * tick
-        while time.perf_counter() < due:
-            admit_pending()
-            poll(time.perf_counter())
-            time.sleep(0.0002)
-        now = time.perf_counter()
-        for i in range(32):
-            a, b = int(edges[i][k0 + k]), int(edges[i][k0 + k + 1])
-            if b > a:
-                s = streams[i]["stream"]
-                fem.fem_server_append(srv, sids[i], s.types[a:b], s.t[a:b])
-                n_fed[i] = b
-                append_log[i].append((b, time.perf_counter()))
-        admit_pending()
-        poll(time.perf_counter())
-    while time.perf_counter() < t0 + n_ticks * tick:
-        admit_pending()
-        poll(time.perf_counter())
-    wall = time.perf_counter() - t0
+                fem.fem_server_poll(srv)
+                time.sleep(0.0002)
     fem.fem_server_drain(srv)
-    poll(time.perf_counter())
+    burst_s = time.perf_counter() - t0
+    served, burst_units = [], 0.0
+    for r, rid in zip(oneshots, rids):
+        c, f, ev, status = fem.fem_server_result(srv, rid, r["rec"].shape[0])
+        served.append((c, f, status))
+        burst_units += float(r["rec"].shape[0]) * ev
     fem.fem_server_destroy(srv)
+    # plain path: each stream's window resident once, then one two-pass call per request
+    wsid = []
+    for (a, b2), x in zip(win, streams):
+        s = x["stream"]
+        wsid.append(fem.fem_load_stream(ctx, s.types[a:b2], s.t[a:b2], s.n_types))
+    for r in oneshots[:3]:  # kernels loaded and shapes chosen before timing
+        fem.fem_count_two_pass(ctx, wsid[r["stream"]], r["rec"], I, r["theta"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = [fem.fem_count_two_pass(ctx, wsid[r["stream"]], r["rec"], I, r["theta"])
+             for r in oneshots]
+    plain_s = time.perf_counter() - t0
+    clk = clocks.stop()
+    same = all(st_ == 0 and np.array_equal(c, ex) and np.array_equal(f, sv)
+               for (c, f, st_), (ex, sv) in zip(served, plain))
     fem.fem_destroy(ctx)
-
-    def pct(xs, q):
-        return float(np.percentile(np.asarray(xs) * 1e3, q)) if xs else None
-
     if rank != 0:
         return
+    head = next(x for x, rate in zip(sweep, rates) if rate == args.req_rate) if args.req_rate in rates \
+        else sweep[0]
     line = {
-        "metric": METRIC, "value": units / wall, "unit": UNIT, "n_gpus": world,
-        "steps": n_ticks, "warmup": 0, "ms_per_step": wall * 1e3 / n_ticks,
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
+        "steps": int(round(sess / tick)), "warmup": 0, "ms_per_step": tick * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded Poisson spike trains with embedded cascades)",
         "config": {"workload": "serving_32_streams", "history_s": hist_s, "session_s": sess,
-                   "chunk_ms": tick * 1e3, "request_rate_per_s": args.req_rate,
-                   "requests": len(reqs), "m_range": [1000, 50000], "lengths": [2, 6],
-                   "standing_fraction": 0.1, "window_s": 60,
-                   "budget_gb": args.serve_budget_gb},
-        "serving": {"oneshot_p50_ms": pct(lat_one, 50), "oneshot_p99_ms": pct(lat_one, 99),
-                    "standing_update_p50_ms": pct(lat_stand, 50),
-                    "standing_update_p99_ms": pct(lat_stand, 99),
-                    "oneshot_done": len(lat_one), "standing_updates": len(lat_stand),
-                    "admitted": admitted, "admission_retries": retries,
-                    "rejected_after_5s": rejected_final},
+                   "chunk_ms": tick * 1e3, "request_rates_per_s": rates,
+                   "m_range": [1000, 50000], "lengths": [2, 6], "standing_fraction": 0.1,
+                   "window_s": win_s, "budget_gb": args.serve_budget_gb},
+        "serving": head,
+        "load_sweep": sweep,
+        "saturation": {"oneshot_requests": len(oneshots),
+                       "served": {"s": burst_s, "value": burst_units / burst_s,
+                                  "form": "all submitted at once, continuous batching over 8 lanes"},
+                       "plain": {"s": plain_s, "value": burst_units / plain_s,
+                                 "form": "one fem_count_two_pass call after another"},
+                       "identical_results": bool(same)},
+        "clocks": clk,
     }
     print(json.dumps(line), flush=True)
 
@@ -924,8 +999,11 @@ def main(argv=None):
                              "bursty", "literal", "windows"],
                     default="single_recording",
                     help="deep: the same recording mined at theta = 300 (levels 3-6 reached)")
-    ap.add_argument("--session-s", type=float, default=20.0)
-    ap.add_argument("--req-rate", type=float, default=10.0)
+    ap.add_argument("--session-s", type=float, default=10.0)
+    ap.add_argument("--req-rate", type=float, default=10.0,
+                    help="--workload serving: the offered load the line's value is quoted at")
+    ap.add_argument("--req-rates", default="5,10,20,50",
+                    help="--workload serving: offered loads swept (requests/s)")
     ap.add_argument("--serve-budget-gb", type=int, default=16)
     ap.add_argument("--recordings", type=int, default=256)
     ap.add_argument("--window-us", type=int, default=40_000,

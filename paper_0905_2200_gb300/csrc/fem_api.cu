@@ -293,9 +293,12 @@ uint32_t ceil_log2(uint64_t v) {
     return r;
 }
 
-// The latest-chain kernels count distinct-type episodes of 2..8 nodes.
-bool chain_eligible(const fem_ctx *c, int N, bool distinct) {
-    return distinct && N >= 2 && N <= FEM_MAX_LEN && c->clustered;
+// The latest-chain kernels count distinct-type episodes of 2..8 nodes in sets that come
+// in runs of shared prefixes; a few hundred candidates (a level's handful of survivors)
+// share too little for the prefix lists to pay.
+constexpr uint32_t kChainMinCandidates = 256;
+bool chain_eligible(const fem_ctx *c, int N, bool distinct, uint32_t m) {
+    return distinct && N >= 2 && N <= FEM_MAX_LEN && c->clustered && m >= kChainMinCandidates;
 }
 
 // Block size of the latest-chain kernels: 256 threads, smaller blocks for few episodes.
@@ -331,7 +334,7 @@ int tune_pass(fem_ctx *c, const std::string &key, const StreamDev &s, const fem_
     const uint32_t R0 = pass == FEM_PASS_EXACT ? (c->cfg.ring_capacity ? c->cfg.ring_capacity : 8) : 1;
     // the shapes to time: per segment count and kernel the rule's block size and its
     // neighbours; the rule's own shape first
-    const bool chain = chain_eligible(c, N, distinct);
+    const bool chain = chain_eligible(c, N, distinct, m);
     const uint32_t k0 = c->cfg.kernel ? c->cfg.kernel : (chain ? FEM_KERNEL_CHAIN : FEM_KERNEL_MACHINE);
     std::vector<fem_ctx::Shape> shapes;
     for (uint32_t kind : {k0, k0 == FEM_KERNEL_CHAIN ? (uint32_t)FEM_KERNEL_MACHINE : (uint32_t)FEM_KERNEL_CHAIN}) {
@@ -395,7 +398,7 @@ int tune_pass(fem_ctx *c, const std::string &key, const StreamDev &s, const fem_
 struct PassLaunch {
     CountParams p{};
     int N = 0, pass = 0;
-    bool distinct = true;
+    bool distinct = true, chain = false;
     uint32_t R = 1;
 };
 
@@ -420,8 +423,9 @@ int count_launch(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const
         if (it != c->tune.end()) P_t = it->second.P, T_t = it->second.T, K_t = it->second.kernel;
     }
     uint32_t kind = c->cfg.kernel ? c->cfg.kernel : K_t;
-    if (!kind) kind = chain_eligible(c, N, distinct) ? FEM_KERNEL_CHAIN : FEM_KERNEL_MACHINE;
-    if (kind == FEM_KERNEL_CHAIN && !chain_eligible(c, N, distinct)) kind = FEM_KERNEL_MACHINE;
+    if (!kind) kind = chain_eligible(c, N, distinct, m) ? FEM_KERNEL_CHAIN : FEM_KERNEL_MACHINE;
+    // (a configured or cached choice of the latest-chain kernels needs distinct types only)
+    if (kind == FEM_KERNEL_CHAIN && !(distinct && N >= 2)) kind = FEM_KERNEL_MACHINE;
     CountParams p{};
     p.bev = s.bev;
     p.boff = s.boff;
@@ -458,6 +462,7 @@ int count_launch(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const
         RET(dbuf(c, "tables", (size_t)P * m * S_MAX, &p.tables));
     }
     CK(cudaEventRecord(c->kev[0], st));
+    pl->chain = kind == FEM_KERNEL_CHAIN;
     if (kind == FEM_KERNEL_CHAIN) {
         uint32_t T = c->cfg.threads_per_block ? c->cfg.threads_per_block : (T_t ? T_t : chain_threads(m));
         if (chain_smem_bytes(N, P > 1, T, s.offs) > 200 * 1024) T = 128;
@@ -492,7 +497,7 @@ void pass_info(fem_ctx *c, const PassLaunch &pl, PassInfo *info) {
 int count_finish(fem_ctx *c, const StreamDev &s, const PassLaunch &pl, uint32_t e,
                  cudaStream_t st) {
     RET(err_status(e));
-    if (!pl.p.m || !(e & (ERR_RING | ERR_TABLE | ERR_CLASS))) return FEM_OK;
+    if (!pl.p.m || !(e & ERR_CAP)) return FEM_OK;
     const CountParams &p = pl.p;
     const uint32_t m = p.m, P = p.P, R = pl.R;
     const int N = pl.N, pass = pl.pass;
@@ -515,14 +520,21 @@ int count_finish(fem_ctx *c, const StreamDev &s, const PassLaunch &pl, uint32_t 
     RET(dbuf(c, "redo_gather", r, &rg));
     RET(dbuf(c, "redo_out", r, &rout));
     CK(launch_compose_idx(gather, ridx, r, rg, st));
-    // First retry: the flagged episodes alone, one chunk per segment (short items, so
-    // the retry costs about one chunk of work) with the largest segmented rings.
-    // Last resort: one segment per episode with the largest rings.
+    // Episodes a latest-chain launch gave up on (its prefix tables or four class slots
+    // were too small) go first to the per-thread kernels with the pass's own segments.
+    // Then: the flagged episodes alone, one chunk per segment (short items, so the retry
+    // costs about one chunk of work) with the largest segmented rings; last resort, one
+    // segment per episode with the largest rings.
     struct Try {
         bool mc;
         uint32_t R;
+        bool same_segments;
     };
-    const Try tries[] = {{true, 32u}, {false, 32u}, {false, 128u}};
+    std::vector<Try> tries;
+    if (pl.chain) tries.push_back({P > 1, 8u, true});
+    tries.push_back({true, 32u, false});
+    tries.push_back({false, 32u, false});
+    tries.push_back({false, 128u, false});
     for (const Try &tr : tries) {
         if (tr.mc && !distinct) continue;
         CK(cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), st));
@@ -535,8 +547,10 @@ int count_finish(fem_ctx *c, const StreamDev &s, const PassLaunch &pl, uint32_t 
         const uint32_t Rq = pass == FEM_PASS_EXACT ? tr.R : 1;
         // the segmented recount has four times the entry-class slots (episodes come
         // here when a window held more classes than a table could)
-        const uint32_t cls = tr.mc && s.n_chunks > 1 ? S_RECOUNT : S_MAX;
-        if (tr.mc && s.n_chunks > 1) {
+        const uint32_t cls = tr.mc && s.n_chunks > 1 && !tr.same_segments ? S_RECOUNT : S_MAX;
+        if (tr.same_segments) {
+            if (q.P > 1) RET(dbuf(c, "redo_tables", (size_t)q.P * r * cls, &q.tables));
+        } else if (tr.mc && s.n_chunks > 1) {
             q.P = s.n_chunks;
             q.cps = 1;
             RET(dbuf(c, "redo_tables", (size_t)q.P * r * cls, &q.tables));
@@ -555,7 +569,7 @@ int count_finish(fem_ctx *c, const StreamDev &s, const PassLaunch &pl, uint32_t 
         RET(err_status(e));
         if (std::getenv("FEM_DEBUG"))
             std::fprintf(stderr, "fem:   retry P=%u R=%u: err %#x\n", q.P, Rq, e);
-        if (!(e & (ERR_RING | ERR_TABLE | ERR_CLASS))) {
+        if (!(e & ERR_CAP)) {
             CK(launch_scatter_u32(rout, ridx, r, out, st));
             return FEM_OK;
         }
@@ -1364,7 +1378,7 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
         if (done) CK(cudaEventRecord(done, st));
         uint32_t e;
         RET(read_count_err(c, c->d_small + word, kept, &e, st));
-        if (e & (ERR_RING | ERR_TABLE | ERR_CLASS)) {
+        if (e & ERR_CAP) {
             RET(count_finish(c, s, pl, e, st));
             CK(launch_compact(vals, nullptr, theta, mm, idx, c->d_small + word, scratch, st));
             RET(read_count_err(c, c->d_small + word, kept, &e, st));
@@ -1654,7 +1668,7 @@ int batch_tune(fem_batch *b, cudaStream_t st) {
                         RET(err_status(e));
                         float t = 0;
                         CK(cudaEventElapsedTime(&t, c->tev[0], c->tev[1]));
-                        if (e & (ERR_RING | ERR_TABLE | ERR_CLASS)) t *= 4;  // needs recounts
+                        if (e & ERR_CAP) t *= 4;  // needs recounts
                         if (ms < 0 || t < ms) ms = t;
                     }
                     if (best < 0 || ms < best) best = ms, bc = cpi, br = Tr, bx = Tx;
@@ -1858,7 +1872,7 @@ int fem_batch_run(fem_batch *b, void *cuda_stream) {
     uint32_t e;
     RET(read_err(c, st, &e));
     RET(err_status(e));
-    if (!(e & (ERR_RING | ERR_TABLE | ERR_CLASS))) return FEM_OK;
+    if (!(e & ERR_CAP)) return FEM_OK;
     // A capacity guard tripped somewhere: recount the affected jobs one at a time
     // with the single-recording path, which widens rings as needed.
     std::vector<fem_interval> I(b->nI);

@@ -29,7 +29,8 @@
 // chains after r; the transfer tables are the per-thread kernel's, so the same stitch
 // composes them.  A block whose prefixes do not fit its node tables, a list longer than
 // CH_LIST in one chunk, or an exact look-up that runs past a full carried tail marks
-// its candidates for the host's recount (ERR_RING), which uses the per-thread kernels.
+// its candidates for the host's recount (ERR_NODES; more entry classes than CH_CLASSES:
+// ERR_CLASS), which uses the per-thread kernels.
 #pragma once
 
 #include "fem_count.cuh"
@@ -38,25 +39,32 @@ namespace fem {
 
 constexpr int CHW = CHUNK / 32;   // bitmask words per chunk
 constexpr int CH_TAIL = 8;        // entries a node carries into the next chunk
-constexpr int CH_LIST = 64;       // admitted entries per node and chunk (depth >= 2)
+constexpr int CH_LIST = 48;       // admitted entries per node and chunk (depth >= 2)
+constexpr int CH_CLASSES = 4;     // MapConcatenate entry classes per thread (table slots used)
 
+// A node's carried tail is double-buffered: lookups of chunk c read tail[c & 1] while
+// the node's build for chunk c writes tail[(c + 1) & 1], so the carry needs no barrier.
 struct ChainNode {
-    uint32_t type, lo, hi, parent, depth, len, base, tlen;
+    uint32_t type, lo, hi, parent, depth, base, tlen[2];
 };
+
+// The dynamic shared memory of a chain block (named at namespace scope, so that every
+// access through it is a shared-memory access with 32-bit addresses).
+extern __shared__ __align__(128) uint8_t fem_chain_smem[];
 
 template <int N, bool MC>
 struct ChainLayout {
-    static constexpr int NMX = N == 2 ? 16 : 32;   // nodes per block
-    static constexpr int LMX = N == 2 ? 1 : 24;    // nodes of depth >= 2 (own lists)
+    static constexpr int NMX = N == 2 ? 16 : 34;   // nodes per block
+    static constexpr int LMX = N == 2 ? 1 : 28;    // nodes of depth >= 2 (own lists)
     static constexpr int EW = MC ? 3 : 2;          // words per entry: t, S (, start time)
     static constexpr size_t META = 0;
     static constexpr size_t BITS = META + (size_t)NMX * sizeof(ChainNode);
     static constexpr size_t PRE = BITS + (size_t)NMX * CHW * 4;
     static constexpr size_t TAIL = PRE + (size_t)NMX * CHW * 2;
-    static constexpr size_t LIST = TAIL + (size_t)NMX * EW * CH_TAIL * 4;
+    static constexpr size_t LIST = TAIL + (size_t)2 * NMX * EW * CH_TAIL * 4;
     static constexpr size_t KEYS = LIST + (size_t)LMX * EW * CH_LIST * 4;
-    static constexpr bool KEYS_SMEM = MC && N >= 3;
-    static size_t bytes(uint32_t T) { return KEYS + (KEYS_SMEM ? (size_t)S_MAX * T * 4 : 0); }
+    static constexpr bool KEYS_SMEM = MC;
+    static size_t bytes(uint32_t T) { return KEYS + (KEYS_SMEM ? (size_t)CH_CLASSES * T * 4 : 0); }
 };
 
 // Block-wide exclusive scan of one value per thread (blockDim.x a multiple of 32, <= 1024).
@@ -85,15 +93,38 @@ template <int N, int PASS, bool MC>
 struct ChainBlock {
     using LY = ChainLayout<N, MC>;
     static constexpr int EW = LY::EW;
-    ChainNode *meta;
-    uint32_t *bits;     // [NMX][CHW]
-    uint16_t *pre;      // [NMX][CHW]
-    uint32_t *tail;     // [NMX][EW][CH_TAIL]
-    uint32_t *list;     // [LMX][EW][CH_LIST]
+    // byte offsets in the block's shared memory: the node tables (nb) and the staged
+    // chunk this pass reads (evb: events grouped by type, then the group offsets)
+    uint32_t nb, evb;
     uint32_t n1;        // nodes of depth 1 (list slots start after them)
-    const uint2 *ev;    // the staged chunk (events grouped by type)
-    const uint16_t *off;
     uint32_t cbase;
+    uint32_t par;       // tail buffer the lookups of this chunk read
+
+    __device__ __forceinline__ ChainNode *meta() const {
+        return reinterpret_cast<ChainNode *>(fem_chain_smem + nb + LY::META);
+    }
+    __device__ __forceinline__ uint32_t *bits() const {  // [NMX][CHW]
+        return reinterpret_cast<uint32_t *>(fem_chain_smem + nb + LY::BITS);
+    }
+    __device__ __forceinline__ uint16_t *pre() const {  // [NMX][CHW]
+        return reinterpret_cast<uint16_t *>(fem_chain_smem + nb + LY::PRE);
+    }
+    __device__ __forceinline__ uint32_t *tail() const {  // [2][NMX][EW][CH_TAIL]
+        return reinterpret_cast<uint32_t *>(fem_chain_smem + nb + LY::TAIL);
+    }
+    __device__ __forceinline__ uint32_t *list() const {  // [LMX][EW][CH_LIST]
+        return reinterpret_cast<uint32_t *>(fem_chain_smem + nb + LY::LIST);
+    }
+    __device__ __forceinline__ const uint2 *ev() const {
+        return reinterpret_cast<const uint2 *>(fem_chain_smem + evb);
+    }
+    __device__ __forceinline__ const uint16_t *off() const {
+        return reinterpret_cast<const uint16_t *>(fem_chain_smem + evb + CHUNK * 8u);
+    }
+
+    __device__ __forceinline__ uint32_t *tail_of(uint32_t nd, uint32_t which) const {
+        return tail() + (which * LY::NMX + nd) * EW * CH_TAIL;
+    }
 
     // Entry idx of node nd: idx in [-tlen, len), negative indices in the carried tail.
     // D1: the node has depth 1 (its list is its type group in the staged chunk).
@@ -101,17 +132,17 @@ struct ChainBlock {
     __device__ __forceinline__ void entry(uint32_t nd, uint32_t tlen, uint32_t base, int idx,
                                           uint32_t &t, uint32_t &S, uint32_t &St) const {
         if (idx < 0) {
-            const uint32_t *tp = tail + (size_t)nd * EW * CH_TAIL + (uint32_t)((int)tlen + idx);
+            const uint32_t *tp = tail_of(nd, par) + (uint32_t)((int)tlen + idx);
             t = tp[0];
             S = tp[CH_TAIL];
             St = MC ? tp[2 * CH_TAIL] : 0u;
         } else if (D1) {
-            const uint2 e = ev[base + (uint32_t)idx];
+            const uint2 e = ev()[base + (uint32_t)idx];
             t = e.x;
             S = cbase + e.y;
             St = e.x;
         } else {
-            const uint32_t *lp = list + (size_t)(nd - n1) * EW * CH_LIST + (uint32_t)idx;
+            const uint32_t *lp = list() + (nd - n1) * EW * CH_LIST + (uint32_t)idx;
             t = lp[0];
             S = lp[CH_LIST];
             St = MC ? lp[2 * CH_LIST] : 0u;
@@ -126,7 +157,7 @@ struct ChainBlock {
                                            uint32_t ti, uint32_t lo, uint32_t &t, uint32_t &S,
                                            uint32_t &St, bool &ovf) const {
         const uint32_t w = pos >> 5;
-        int idx = (int)pre[nd * CHW + w] + __popc(bits[nd * CHW + w] & ((1u << (pos & 31)) - 1u)) - 1;
+        int idx = (int)pre()[nd * CHW + w] + __popc(bits()[nd * CHW + w] & ((1u << (pos & 31)) - 1u)) - 1;
         const int tl = (int)tlen;
         for (;;) {
             if (idx < -tl) {
@@ -141,8 +172,8 @@ struct ChainBlock {
 
     // per-word prefix counts of node nd's bitmask (one warp)
     __device__ __forceinline__ void prefix(uint32_t nd, uint32_t lane) const {
-        const uint32_t a = __popc(bits[nd * CHW + 2 * lane]);
-        const uint32_t b = __popc(bits[nd * CHW + 2 * lane + 1]);
+        const uint32_t a = __popc(bits()[nd * CHW + 2 * lane]);
+        const uint32_t b = __popc(bits()[nd * CHW + 2 * lane + 1]);
         uint32_t inc = a + b;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -150,86 +181,77 @@ struct ChainBlock {
             if (lane >= (uint32_t)d) inc += y;
         }
         const uint32_t ex = inc - a - b;
-        pre[nd * CHW + 2 * lane] = (uint16_t)ex;
-        pre[nd * CHW + 2 * lane + 1] = (uint16_t)(ex + a);
+        pre()[nd * CHW + 2 * lane] = (uint16_t)ex;
+        pre()[nd * CHW + 2 * lane + 1] = (uint16_t)(ex + a);
     }
 
-    // This chunk's admitted list of node nd (one warp); returns true on list overflow.
+    // This chunk's admitted list of node nd (one warp), then the node's tail for the next
+    // chunk; returns true on list overflow.
     __device__ __forceinline__ bool build(uint32_t nd, uint32_t lane) const {
-        ChainNode &n = meta[nd];
-        const uint32_t g0 = off[n.type], g1 = off[n.type + 1];
-        bits[nd * CHW + lane] = 0;
-        bits[nd * CHW + lane + 32] = 0;
+        ChainNode &n = meta()[nd];
+        const uint32_t g0 = off()[n.type], g1 = off()[n.type + 1];
+        bits()[nd * CHW + lane] = 0;
+        bits()[nd * CHW + lane + 32] = 0;
         __syncwarp();
         bool ovf = false;
+        uint32_t len;
         if (n.depth == 1) {
             for (uint32_t j = g0 + lane; j < g1; j += 32) {
-                const uint32_t pos = ev[j].y;
-                atomicOr(&bits[nd * CHW + (pos >> 5)], 1u << (pos & 31));
+                const uint32_t pos = ev()[j].y;
+                atomicOr(&bits()[nd * CHW + (pos >> 5)], 1u << (pos & 31));
             }
-            __syncwarp();
-            prefix(nd, lane);
-            if (lane == 0) n.len = g1 - g0, n.base = g0;
-            __syncwarp();
-            return false;
-        }
-        const uint32_t pn = n.parent, lo = n.lo, hi = n.hi;
-        const uint32_t ptl = meta[pn].tlen, pbase = meta[pn].base;
-        const bool pd1 = meta[pn].depth == 1;
-        uint32_t *lp = list + (size_t)(nd - n1) * EW * CH_LIST;
-        uint32_t cnt = 0;
-        for (uint32_t j0 = g0; j0 < g1; j0 += 32) {
-            const uint32_t j = j0 + lane;
-            bool adm = false;
-            uint32_t ti = 0, pos = 0, t = 0, S = 0, St = 0;
-            if (j < g1) {
-                const uint2 e = ev[j];
-                ti = e.x, pos = e.y;
-                adm = (pd1 ? lookup<true>(pn, ptl, pbase, pos, ti, lo, t, S, St, ovf)
-                           : lookup<false>(pn, ptl, pbase, pos, ti, lo, t, S, St, ovf)) &&
-                      ti - t <= hi;
-            }
-            const uint32_t bal = __ballot_sync(0xffffffffu, adm);
-            const uint32_t k = cnt + __popc(bal & ((1u << lane) - 1u));
-            if (adm) {
-                if (k < (uint32_t)CH_LIST) {
-                    lp[k] = ti;
-                    lp[CH_LIST + k] = S;
-                    if (MC) lp[2 * CH_LIST + k] = St;
-                    atomicOr(&bits[nd * CHW + (pos >> 5)], 1u << (pos & 31));
-                } else {
-                    ovf = true;
+            len = g1 - g0;
+            if (lane == 0) n.base = g0;
+        } else {
+            const uint32_t pn = n.parent, lo = n.lo, hi = n.hi;
+            const uint32_t ptl = meta()[pn].tlen[par], pbase = meta()[pn].base;
+            const bool pd1 = meta()[pn].depth == 1;
+            uint32_t *lp = list() + (nd - n1) * EW * CH_LIST;
+            uint32_t cnt = 0;
+            for (uint32_t j0 = g0; j0 < g1; j0 += 32) {
+                const uint32_t j = j0 + lane;
+                bool adm = false;
+                uint32_t ti = 0, pos = 0, t = 0, S = 0, St = 0;
+                if (j < g1) {
+                    const uint2 e = ev()[j];
+                    ti = e.x, pos = e.y;
+                    adm = (pd1 ? lookup<true>(pn, ptl, pbase, pos, ti, lo, t, S, St, ovf)
+                               : lookup<false>(pn, ptl, pbase, pos, ti, lo, t, S, St, ovf)) &&
+                          ti - t <= hi;
                 }
+                const uint32_t bal = __ballot_sync(0xffffffffu, adm);
+                const uint32_t k = cnt + __popc(bal & ((1u << lane) - 1u));
+                if (adm) {
+                    if (k < (uint32_t)CH_LIST) {
+                        lp[k] = ti;
+                        lp[CH_LIST + k] = S;
+                        if (MC) lp[2 * CH_LIST + k] = St;
+                        atomicOr(&bits()[nd * CHW + (pos >> 5)], 1u << (pos & 31));
+                    } else {
+                        ovf = true;
+                    }
+                }
+                cnt += __popc(bal);
             }
-            cnt += __popc(bal);
+            len = min(cnt, (uint32_t)CH_LIST);
         }
         __syncwarp();
         prefix(nd, lane);
-        if (lane == 0) n.len = min(cnt, (uint32_t)CH_LIST);
-        __syncwarp();
-        return __any_sync(0xffffffffu, ovf);
-    }
-
-    // Carry node nd's last CH_TAIL entries (old tail followed by this chunk's list).
-    __device__ __forceinline__ void carry(uint32_t nd, uint32_t lane) const {
-        ChainNode &n = meta[nd];
-        const uint32_t tl = n.tlen, len = n.len;
+        // the next chunk's tail: the last CH_TAIL entries of this tail followed by the list
+        const uint32_t tl = n.tlen[par];
         const uint32_t nl = min((uint32_t)CH_TAIL, tl + len);
-        uint32_t t = 0, S = 0, St = 0;
         if (lane < nl) {  // index into [-tl, len)
-            if (n.depth == 1) entry<true>(nd, tl, n.base, (int)(len - nl + lane), t, S, St);
-            else entry<false>(nd, tl, n.base, (int)(len - nl + lane), t, S, St);
-        }
-        __syncwarp();
-        if (lane < nl) {
-            uint32_t *tp = tail + (size_t)nd * EW * CH_TAIL + lane;
+            uint32_t t = 0, S = 0, St = 0;
+            if (n.depth == 1) entry<true>(nd, tl, g0, (int)(len - nl + lane), t, S, St);
+            else entry<false>(nd, tl, g0, (int)(len - nl + lane), t, S, St);
+            uint32_t *tp = tail_of(nd, par ^ 1u) + lane;
             tp[0] = t;
             tp[CH_TAIL] = S;
             if (MC) tp[2 * CH_TAIL] = St;
         }
+        if (lane == 0) n.tlen[par ^ 1u] = nl;
         __syncwarp();
-        if (lane == 0) n.tlen = nl;
-        __syncwarp();
+        return __any_sync(0xffffffffu, ovf);
     }
 };
 
@@ -238,8 +260,10 @@ template <int N, int PASS, bool MC>
 __device__ __forceinline__ void chain_block(const CountParams &p) {
     static_assert(N >= 2, "one-node episodes are counted by the per-thread kernels");
     using LY = ChainLayout<N, MC>;
-    constexpr int SC = MC ? S_MAX : 1;
-    extern __shared__ __align__(128) uint8_t smem[];
+    // entry classes tracked per thread (a window holding more capable last-node events
+    // sends the episode to the recount, whose tables have S_RECOUNT slots)
+    constexpr int SC = MC ? CH_CLASSES : 1;
+    uint8_t *smem = fem_chain_smem;
     const uint32_t SB = stage_bytes(p.offs);
     const uint32_t T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t nwarps = T >> 5;
@@ -249,11 +273,8 @@ __device__ __forceinline__ void chain_block(const CountParams &p) {
     // sc[18..25] scan scratch (one word per warp is enough for 8 warps; 256 threads max)
     uint8_t *nodes = smem + 2 * SB + 128;
     ChainBlock<N, PASS, MC> cb;
-    cb.meta = reinterpret_cast<ChainNode *>(nodes + LY::META);
-    cb.bits = reinterpret_cast<uint32_t *>(nodes + LY::BITS);
-    cb.pre = reinterpret_cast<uint16_t *>(nodes + LY::PRE);
-    cb.tail = reinterpret_cast<uint32_t *>(nodes + LY::TAIL);
-    cb.list = reinterpret_cast<uint32_t *>(nodes + LY::LIST);
+    cb.nb = 2 * SB + 128;
+    cb.evb = 0;
     uint32_t *keys_s = reinterpret_cast<uint32_t *>(nodes + LY::KEYS) + tid;
 
     init_stage_bars(smem, SB);
@@ -318,13 +339,13 @@ __device__ __forceinline__ void chain_block(const CountParams &p) {
             nid[d] = n_total + ex + is_new - 1u;  // ok threads: the latest node opened at or before
             if (tid == 0) sc[2 + d] = n_total, sc[10 + d] = tot;
             if (is_new && n_total + ex < (uint32_t)LY::NMX) {
-                ChainNode *nd = cb.meta + n_total + ex;
+                ChainNode *nd = cb.meta() + n_total + ex;
                 nd->type = E[d - 1];
                 nd->lo = d >= 2 ? lo_[d - 2] : 0u;
                 nd->hi = d >= 2 ? hi_[d - 2] : 0u;
                 nd->parent = d >= 2 ? nid[d - 1] : 0u;
                 nd->depth = (uint32_t)d;
-                nd->len = 0, nd->base = 0, nd->tlen = 0;
+                nd->base = 0, nd->tlen[0] = 0, nd->tlen[1] = 0;
             }
             if (d == 1) n1 = tot;
             n_total += tot;
@@ -335,7 +356,7 @@ __device__ __forceinline__ void chain_block(const CountParams &p) {
     if (n_total > (uint32_t)LY::NMX || n_total - n1 > (uint32_t)LY::LMX) {
         // the block's prefixes do not fit: its candidates go to the host's recount
         if (ok) p.redo[ci] = 1;
-        if (tid == 0) atomicOr(p.err, ERR_RING);
+        if (tid == 0) atomicOr(p.err, ERR_NODES);
         return;
     }
     const uint32_t pn = nid[N - 1];  // the leaf's parent node
@@ -344,7 +365,7 @@ __device__ __forceinline__ void chain_block(const CountParams &p) {
     // ------------------------------------------------------------ segment and window
     const uint32_t c_seg0 = seg * p.cps;
     const uint32_t c_end = min(c_seg0 + p.cps, p.n_chunks);
-    const uint64_t L = (uint64_t)c_seg0 * CHUNK;
+    const uint32_t L = c_seg0 * CHUNK;
     uint32_t X = 0, Xn = 0, c_w = c_seg0;
     const bool last_seg = c_end >= p.n_chunks;
     if (MC) {
@@ -425,10 +446,10 @@ __device__ __forceinline__ void chain_block(const CountParams &p) {
             bail = true;
             break;
         }
-        cb.ev = reinterpret_cast<const uint2 *>(smem + s * SB);
-        cb.off = reinterpret_cast<const uint16_t *>(smem + s * SB + chunk_ev_bytes);
+        cb.evb = s * SB;
         cb.cbase = c * CHUNK;
-        // prefix lists, depth by depth
+        cb.par = (c - c_first) & 1u;
+        // prefix lists, depth by depth (each build also writes the node's next tail)
         bool bovf = false;
         for (int d = 1; d <= N - 1; ++d) {
             const uint32_t b0 = sc[2 + d], nb = sc[10 + d];
@@ -436,21 +457,66 @@ __device__ __forceinline__ void chain_block(const CountParams &p) {
             __syncthreads();
         }
         if (bovf && lane == 0) sc[1] = 1;
-        // the leaf: this thread's last node's events
+        // the leaf: this thread's last node's events, looked up in the parent's list
         if (ok && c >= c_w) {
-            const uint32_t g0 = cb.off[El], g1 = cb.off[El + 1];
-            const uint32_t ptl = cb.meta[pn].tlen, pbase = cb.meta[pn].base;
-            for (uint32_t jj = g0; jj < g1; ++jj) {
-                const uint2 e = cb.ev[jj];
-                const uint32_t ti = e.x, gidx = cb.cbase + e.y;
-                uint32_t t, S, St;
-                if (!cb.template lookup<N == 2>(pn, ptl, pbase, e.y, ti, lo, t, S, St, ovf) ||
-                    ti - t > hi)
-                    continue;
-                if constexpr (!MC) {
-                    if (S >= st) ++cnt, st = gidx + 1;
-                } else {
-                    const uint32_t inc = (uint64_t)gidx >= L ? 1u : 0u;
+            const uint32_t g0 = cb.off()[El], g1 = cb.off()[El + 1];
+            const uint32_t ptl = cb.meta()[pn].tlen[cb.par], pbase = cb.meta()[pn].base;
+            auto adm_at = [&](const uint2 e, uint32_t &S, uint32_t &St) -> bool {
+                uint32_t t;
+                return cb.template lookup<N == 2>(pn, ptl, pbase, e.y, e.x, lo, t, S, St, ovf) &&
+                       e.x - t <= hi;
+            };
+            if (!MC || (c >= c_seg0 && umask == 0)) {
+                // one class: inside the segment with every entry class merged, or one segment.
+                // Two events per step: their look-ups are independent, the greedy is not.
+                auto apply = [&](bool a, uint32_t y, uint32_t S, uint32_t St) {
+                    if (!a) return;
+                    const uint32_t gidx = cb.cbase + y;
+                    if constexpr (!MC) {
+                        if (S >= st) ++cnt, st = gidx + 1;
+                    } else {
+                        if (S >= c_st[0] && St >= X) c_st[0] = gidx + 1, ++c_cnt[0], c0_done = true;
+                    }
+                };
+                uint32_t jj = g0;
+                for (; jj + 2 <= g1; jj += 2) {
+                    const uint2 e0 = cb.ev()[jj], e1 = cb.ev()[jj + 1];
+                    uint32_t S0, St0, S1, St1;
+                    const bool a0 = adm_at(e0, S0, St0);
+                    const bool a1 = adm_at(e1, S1, St1);
+                    apply(a0, e0.y, S0, St0);
+                    apply(a1, e1.y, S1, St1);
+                }
+                if (jj < g1) {
+                    const uint2 e = cb.ev()[jj];
+                    uint32_t S, St;
+                    const bool a = adm_at(e, S, St);
+                    apply(a, e.y, S, St);
+                }
+            } else if constexpr (MC) {
+                for (uint32_t jj = g0; jj < g1; ++jj) {
+                    const uint2 e = cb.ev()[jj];
+                    uint32_t S, St, tp;
+                    const bool found = cb.template lookup<N == 2>(pn, ptl, pbase, e.y, e.x, lo, tp,
+                                                                   S, St, ovf);
+                    if (!found) continue;
+                    // Every later event of this node looks up this parent entry or a later
+                    // one, so its chain starts at S or later: a class whose threshold is at
+                    // most S admits all of them, as class "none" does when its conditions
+                    // hold for S too -- such a class behaves like class "none" from here on.
+                    if (umask && S >= c_st[0] && St >= X) {
+#pragma unroll
+                        for (int q = 1; q < SC; ++q) {
+                            if (((umask >> q) & 1u) && c_st[q] <= S) {
+                                c_cnt[q] -= c_cnt[0];
+                                umask &= ~(1u << q);
+                                if (cb.cbase + e.y < L) used &= ~(1u << q);
+                            }
+                        }
+                    }
+                    if (e.x - tp > hi) continue;
+                    const uint32_t ti = e.x, gidx = cb.cbase + e.y;
+                    const uint32_t inc = gidx >= L ? 1u : 0u;
                     if (S >= c_st[0] && St >= X) c_st[0] = gidx + 1, c_cnt[0] += inc, c0_done = true;
                     if (umask) {
 #pragma unroll
@@ -490,8 +556,6 @@ __device__ __forceinline__ void chain_block(const CountParams &p) {
             }
         }
         __syncthreads();
-        for (uint32_t nd = warp; nd < n_total; nd += nwarps) cb.carry(nd, lane);
-        __syncthreads();
         if (tid == 0 && c + 2 < c_end) {
             fence_proxy_async_smem();
             issue(c + 2, s);
@@ -514,7 +578,7 @@ __device__ __forceinline__ void chain_block(const CountParams &p) {
     }
     const bool bad = sc[1] != 0 || ovf || class_overflow;
     if (ok && bad) {
-        atomicOr(p.err, class_overflow && !ovf && sc[1] == 0 ? ERR_CLASS : ERR_RING);
+        atomicOr(p.err, (class_overflow ? ERR_CLASS : 0u) | (ovf || sc[1] != 0 ? ERR_NODES : 0u));
         p.redo[ci] = 1;
     }
     if constexpr (!MC) {
@@ -522,8 +586,9 @@ __device__ __forceinline__ void chain_block(const CountParams &p) {
     } else {
         uint4 *tab = p.tables + ((uint64_t)seg * p.m + ci) * S_MAX;
         const uint32_t n_slots = used ? 32u - __clz(used) : 1u;
+        static_assert(SC <= S_MAX, "the transfer tables hold S_MAX classes");
 #pragma unroll
-        for (int q = 0; q < S_MAX; ++q) {
+        for (int q = 0; q < SC; ++q) {
             if ((uint32_t)q >= n_slots) break;
             uint4 e = make_uint4(CLS_EMPTY, 0, CLS_NONE, q == 0 ? n_slots : 0u);
             if (ok && (q == 0 || ((used >> q) & 1u))) {
@@ -540,7 +605,7 @@ __device__ __forceinline__ void chain_block(const CountParams &p) {
 }
 
 template <int N, int PASS, bool MC>
-__global__ void __launch_bounds__(256) k_chain(const CountParams p) {
+__global__ void __launch_bounds__(256, 4) k_chain(const CountParams p) {
     chain_block<N, PASS, MC>(p);
 }
 

@@ -138,13 +138,16 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
     }
 
     // ---------------------------------------------------------------- segment and window
-    // A ranged count (single segment) covers events [ev_begin, ev_end) only.
-    const uint32_t c_seg0 = p.ranged ? (uint32_t)(p.ev_begin / CHUNK) : seg * p.cps;
-    const uint32_t c_end = p.ranged ? (uint32_t)((p.ev_end + CHUNK - 1) / CHUNK)
-                                    : min(c_seg0 + p.cps, p.n_chunks);
-    const uint32_t lo_local = p.ranged ? (uint32_t)(p.ev_begin - (uint64_t)c_seg0 * CHUNK) : 0u;
-    const uint32_t hi_local = p.ranged && c_end > 0
-                                  ? (uint32_t)(p.ev_end - (uint64_t)(c_end - 1) * CHUNK)
+    // A ranged count covers events [ev_begin, ev_end) only: the chunks cr0 .. cr1 - 1,
+    // the first from local index lo_local on, the last up to hi_local; its segments
+    // are runs of cps chunks from cr0 on, and nothing before ev_begin is read.
+    const uint32_t cr0 = p.ranged ? (uint32_t)(p.ev_begin / CHUNK) : 0u;
+    const uint32_t cr1 = p.ranged ? (uint32_t)((p.ev_end + CHUNK - 1) / CHUNK) : p.n_chunks;
+    const uint32_t c_seg0 = cr0 + seg * p.cps;
+    const uint32_t c_end = min(c_seg0 + p.cps, cr1);
+    const uint32_t lo_local = p.ranged ? (uint32_t)(p.ev_begin - (uint64_t)cr0 * CHUNK) : 0u;
+    const uint32_t hi_local = p.ranged && cr1 > 0
+                                  ? (uint32_t)(p.ev_end - (uint64_t)(cr1 - 1) * CHUNK)
                                   : KEY_END;
     const uint64_t L = (uint64_t)c_seg0 * CHUNK;
     // X: start time of the window whose last-node events are the entry classes;
@@ -152,7 +155,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
     // window is seen and only window events that can complete an occurrence become
     // classes (the serial machine's last completion before L is one of those).
     uint32_t X = 0, X2 = 0, Xn = 0, c_w = c_seg0;
-    bool last_seg = c_end >= p.n_chunks;
+    bool last_seg = c_end >= cr1;
     if (MC) {
         uint64_t W = 0;
 #pragma unroll
@@ -162,9 +165,9 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
             X = (uint64_t)tL >= W ? (uint32_t)(tL - W) : 0u;
             X2 = (uint64_t)tL >= 2 * W ? (uint32_t)(tL - 2 * W) : 0u;
             uint32_t c = c_seg0;
-            if (X2 == 0) c = 0;
+            if (X2 == 0) c = cr0;
             else
-                while (c > 0 && p.cfirst[c] >= X2) --c;
+                while (c > cr0 && p.cfirst[c] >= X2) --c;
             c_w = c;
         }
         if (!last_seg) {
@@ -605,7 +608,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                 end[k] = off[ep.E[k] + 1];
                 if (MC && c == c_w && X2 > 0)
                     while (ptr[k] < end[k] && ev[ptr[k]].x < X2) ++ptr[k];
-                if (c == c_first && lo_local > 0)
+                if (c == cr0 && lo_local > 0)
                     while (ptr[k] < end[k] && ev[ptr[k]].y < lo_local) ++ptr[k];
                 if (ptr[k] < end[k]) {
                     const uint2 e = ev[ptr[k]];
@@ -616,7 +619,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                     tv[k] = 0;
                 }
             }
-            const uint32_t lim = c + 1 == c_end ? hi_local : KEY_END;
+            const uint32_t lim = c + 1 == cr1 ? hi_local : KEY_END;
             bool lean =
                 distinct && (!MC || (c >= c_seg0 && umask == 0 && c_start[0] != 0xFFFFFFFFu));
             if (!lean) {

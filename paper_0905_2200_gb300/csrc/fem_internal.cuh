@@ -35,6 +35,9 @@ constexpr uint32_t ERR_UNSORTED = 8u;
 constexpr uint32_t ERR_TYPE = 16u;
 constexpr uint32_t ERR_TABLE = 32u;        // transfer table missing a class (internal)
 constexpr uint32_t ERR_CLASS = 64u;        // more entry classes than table slots (host retries)
+constexpr uint32_t ERR_NODES = 128u;       // a latest-chain block's prefix tables overflowed (host retries)
+// any capacity guard: the flagged episodes are recounted by the host
+constexpr uint32_t ERR_CAP = ERR_RING | ERR_TABLE | ERR_CLASS | ERR_NODES;
 
 constexpr uint64_t WAIT_NS = 2000000000ull; // bound on any single device wait (2 s)
 
@@ -77,10 +80,11 @@ struct CountParams {
     uint4 *tables;              // [P][m][S_MAX] (key, count, exit, 0) when P > 1
     uint8_t *redo;              // [m] set to 1 when a candidate must be recounted
     uint32_t *err;
-    // optional (single segment only):
+    // optional (per-thread machine kernels):
     const uint32_t *m_dev;      // candidate count read on the device (overrides m)
-    uint32_t ranged;            // count events [ev_begin, ev_end) only
+    uint32_t ranged;            // count events [ev_begin, ev_end) only (segments from its first chunk)
     uint64_t ev_begin, ev_end;
+    // (single segment only)
     uint32_t *state;            // per-candidate carried state (count, machine), in and out
     uint32_t state_stride;      // words per candidate: 1 + (N-1) relaxed, 1 + (N-1)(1 + 2R) exact
 };

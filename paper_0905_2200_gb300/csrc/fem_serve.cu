@@ -109,6 +109,8 @@ struct Request {
     uint32_t *rel = nullptr, *idx = nullptr, *ex = nullptr, *out = nullptr, *scratch = nullptr;
     uint32_t *cnt = nullptr, *err = nullptr, *state = nullptr;
     uint8_t *flags = nullptr, *redo = nullptr;
+    uint4 *tables = nullptr;     // MapConcatenate transfer tables of a one-shot relaxed pass
+    uint64_t tab_items = 0;      // (episode, segment) pairs the tables hold
     // pinned host block: out (m), flags (m), err (1), staging of candidates
     char *hblk = nullptr;
     size_t hbytes = 0;
@@ -126,6 +128,22 @@ struct Request {
 };
 
 constexpr uint32_t kServeRing = 16;  // exact-pass clusters per node in serving
+// A one-shot request's relaxed pass gives each length group about this many threads
+// per SM through MapConcatenate segments (a 1k-candidate group alone would fill a few
+// SMs); its transfer tables are part of the request's device memory.
+constexpr uint32_t kServeThreadsPerSM = 512;
+
+// Segments of a one-shot relaxed pass over nch chunks for m candidates (1: none).  Below
+// four segments the tables cost more than the parallelism they buy.  The tables of one
+// request may take an eighth of the arena at most.
+uint32_t oneshot_segments(uint32_t m, uint32_t nch, int sm_count, size_t arena_bytes) {
+    if (m == 0 || nch < 4) return 1;
+    const uint64_t target = (uint64_t)sm_count * kServeThreadsPerSM;
+    uint64_t P = std::min<uint64_t>((target + m - 1) / m, nch);
+    const uint64_t cap = arena_bytes / 8 / (S_MAX * sizeof(uint4)) / m;
+    P = std::min<uint64_t>(P, cap);
+    return P < 4 ? 1u : (uint32_t)P;
+}
 
 }  // namespace
 
@@ -203,23 +221,46 @@ CountParams base_params(const StreamDev &s, const Request &r, const Group &g, in
     return p;
 }
 
-uint32_t serve_threads(int N, int pass, uint32_t R, uint32_t offs) {
+uint32_t serve_threads(int N, int pass, uint32_t R, uint32_t offs, bool mc = false) {
     for (uint32_t T : {128u, 64u, 32u})
-        if (count_smem_bytes(N, pass, false, R, T, offs) <= 100 * 1024) return T;
+        if (count_smem_bytes(N, pass, mc, R, T, offs) <= 100 * 1024) return T;
     return 32;
 }
 
 // One-shot: Algorithm 4 over [ev_begin, ev_end) of the stream, per length group,
-// with every size on the device (no host round trip).
-int enqueue_oneshot(fem_server *v, Request &r, const StreamDev &s, uint32_t R) {
+// with every size on the device (no host round trip).  With mc, a group whose
+// candidates are few runs its relaxed pass over MapConcatenate segments of the range
+// (the exact pass counts the survivors, usually few, in one segment).
+int enqueue_oneshot(fem_server *v, Request &r, const StreamDev &s, uint32_t R, bool mc) {
     cudaStream_t st = r.lane;
+    const uint32_t cr0 = (uint32_t)(r.ev_begin / CHUNK);
+    const uint32_t cr1 = (uint32_t)((r.ev_end + CHUNK - 1) / CHUNK);
+    const uint32_t nch = cr1 > cr0 ? cr1 - cr0 : 0u;
+    // the stitch skips episodes flagged for a recount: no flag may survive from the
+    // memory's last user
+    SCK(cudaMemsetAsync(r.redo, 0, r.m, st));
     for (const Group &g : r.groups) {
         CountParams p = base_params(s, r, g, FEM_PASS_RELAXED);
         p.cands = r.cands + g.off;
         p.m = g.m;
         p.out = r.rel + g.off;
-        SCK(launch_count(g.N, FEM_PASS_RELAXED, false, 1,
-                         serve_threads(g.N, FEM_PASS_RELAXED, 1, s.offs), p, st));
+        uint32_t P = mc && r.tables ? oneshot_segments(g.m, nch, fem_ctx_sms(v->ctx),
+                                                       v->cfg.mem_budget_bytes)
+                                    : 1u;
+        if (P > 1) {
+            const uint32_t cps = (nch + P - 1) / P;
+            P = (nch + cps - 1) / cps;
+            if ((uint64_t)P * g.m > r.tab_items) P = 1;
+            if (P > 1) {
+                p.cps = cps;
+                p.P = P;
+                p.tables = r.tables;
+            }
+        }
+        SCK(launch_count(g.N, FEM_PASS_RELAXED, P > 1, 1,
+                         serve_threads(g.N, FEM_PASS_RELAXED, 1, s.offs, P > 1), p, st));
+        if (P > 1)
+            SCK(launch_stitch(r.tables, g.m, P, r.rel + g.off, r.redo + g.off, r.err, st));
         SCK(launch_compact(r.rel + g.off, nullptr, r.theta, g.m, r.idx + g.off,
                            r.cnt + (&g - r.groups.data()), r.scratch, st));
         CountParams x = base_params(s, r, g, FEM_PASS_EXACT);
@@ -235,7 +276,6 @@ int enqueue_oneshot(fem_server *v, Request &r, const StreamDev &s, uint32_t R) {
         SCK(launch_scatter_dev(r.ex + g.off, r.idx + g.off, x.m_dev, g.m, r.out + g.off,
                                r.flags + g.off, st));
     }
-    (void)v;
     return FEM_OK;
 }
 
@@ -501,11 +541,27 @@ int fem_server_submit(fem_server *v, int32_t sid, const fem_episode *cands, uint
         state_words += (uint64_t)g.m * g.stride;
     }
     auto rnd = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    // a one-shot request covers the last window_us of the stream as it is now
+    r.ev_end = s.n;
+    if (mode == FEM_REQ_ONESHOT) {
+        r.ev_begin = 0;
+        if (window_us && !ss.t_host.empty() && ss.t_host.back() >= window_us) {
+            const uint32_t t0 = ss.t_host.back() - window_us;
+            r.ev_begin = std::lower_bound(ss.t_host.begin(), ss.t_host.end(), t0) - ss.t_host.begin();
+        }
+        const uint32_t nch = (uint32_t)((r.ev_end + CHUNK - 1) / CHUNK - r.ev_begin / CHUNK);
+        for (const Group &g : r.groups) {
+            const uint32_t P =
+                oneshot_segments(g.m, nch, fem_ctx_sms(v->ctx), v->cfg.mem_budget_bytes);
+            if (P > 1) r.tab_items = std::max<uint64_t>(r.tab_items, (uint64_t)P * g.m);
+        }
+    }
     const size_t b_cands = rnd((size_t)m * 16), b_ivl = rnd(std::max<uint32_t>(nI, 1) * 8),
                  b_u32 = rnd((size_t)m * 4), b_u8 = rnd(m),
                  b_scr = rnd(compact_scratch_words(gmax) * 4), b_cnt = rnd(r.groups.size() * 4 + 4),
-                 b_state = mode == FEM_REQ_STANDING ? rnd(state_words * 4) : 0;
-    r.dbytes = b_cands + b_ivl + 4 * b_u32 + 2 * b_u8 + b_scr + b_cnt + b_state;
+                 b_state = mode == FEM_REQ_STANDING ? rnd(state_words * 4) : 0,
+                 b_tab = rnd(r.tab_items * S_MAX * sizeof(uint4));
+    r.dbytes = b_cands + b_ivl + 4 * b_u32 + 2 * b_u8 + b_scr + b_cnt + b_state + b_tab;
     r.dblk = static_cast<char *>(v->dev.alloc(r.dbytes));
     if (!r.dblk) return FEM_EADMIT;
     r.hbytes = b_u32 + b_u8 + 256 + b_cands + b_ivl;
@@ -528,6 +584,8 @@ int fem_server_submit(fem_server *v, int32_t sid, const fem_episode *cands, uint
     r.err = r.cnt + r.groups.size();
     d += b_cnt;
     if (b_state) r.state = reinterpret_cast<uint32_t *>(d);
+    d += b_state;
+    if (b_tab) r.tables = reinterpret_cast<uint4 *>(d);
     char *h = r.hblk;
     r.h_out = reinterpret_cast<uint32_t *>(h), h += b_u32;
     r.h_flags = reinterpret_cast<uint8_t *>(h), h += b_u8;
@@ -554,14 +612,8 @@ int fem_server_submit(fem_server *v, int32_t sid, const fem_episode *cands, uint
         return fail(FEM_ECUDA);
     }
     if (s.t_max > kServeMaxTime) return fail(FEM_ERANGE);
-    r.ev_end = s.n;
     if (mode == FEM_REQ_ONESHOT) {
-        r.ev_begin = 0;
-        if (window_us && !ss.t_host.empty() && ss.t_host.back() >= window_us) {
-            const uint32_t t0 = ss.t_host.back() - window_us;
-            r.ev_begin = std::lower_bound(ss.t_host.begin(), ss.t_host.end(), t0) - ss.t_host.begin();
-        }
-        int rc = enqueue_oneshot(v, r, s, kServeRing);
+        int rc = enqueue_oneshot(v, r, s, kServeRing, true);
         if (rc == FEM_OK) rc = finish_enqueue(v, r, ss);
         if (rc != FEM_OK) return fail(rc);
     } else {
@@ -602,16 +654,17 @@ int fem_server_poll(fem_server *v, uint64_t *done_ids, uint32_t cap, uint32_t *n
         const uint32_t e = *r.h_err;
         if (e & ERR_TIMEOUT) r.status = FEM_ETIMEOUT;
         else if (e & ERR_BADEP) r.status = FEM_EINVAL;
-        else if ((e & ERR_RING) && r.mode == FEM_REQ_ONESHOT && r.status == FEM_OK) {
-            // rare: recount with larger rings, synchronously on the request's lane
+        else if ((e & (ERR_RING | ERR_CLASS | ERR_TABLE)) && r.mode == FEM_REQ_ONESHOT &&
+                 r.status == FEM_OK) {
+            // rare: recount in one segment with larger rings, synchronously on the lane
             auto sit = v->streams.find(r.sid);
             int rc = cudaMemsetAsync(r.err, 0, 4, r.lane) == cudaSuccess ? FEM_OK : FEM_ECUDA;
-            if (rc == FEM_OK) rc = enqueue_oneshot(v, r, sit->second.s, 128);
+            if (rc == FEM_OK) rc = enqueue_oneshot(v, r, sit->second.s, 128, false);
             if (rc == FEM_OK) rc = finish_enqueue(v, r, sit->second);
             if (rc == FEM_OK && cudaEventSynchronize(r.done) != cudaSuccess) rc = FEM_ECUDA;
             r.in_flight = false;
             if (rc != FEM_OK) r.status = rc;
-            else if (*r.h_err & ERR_RING) r.status = FEM_EOVERFLOW;
+            else if (*r.h_err & (ERR_RING | ERR_CLASS | ERR_TABLE)) r.status = FEM_EOVERFLOW;
         } else if (e & ERR_RING) {
             r.status = FEM_EOVERFLOW;  // a standing request's carried lists overflowed
         }
