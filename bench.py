@@ -62,7 +62,8 @@ def kernel_source_hash() -> str:
     csrc = os.path.join(ROOT, "paper_0905_2200_gb300", "csrc")
     for f in ("fem_count.cuh", "fem_count_launch.cuh", "fem_count.cu", "fem_count_relaxed.cu",
               "fem_count_exact.cu", "fem_count_exact_n12.cu", "fem_count_exact_n34.cu",
-              "fem_count_exact_n56.cu", "fem_count_exact_n78.cu"):
+              "fem_count_exact_n56.cu", "fem_count_exact_n78.cu", "fem_chain.cuh",
+              "fem_chain_launch.cuh", "fem_chain_relaxed.cu", "fem_chain_exact.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     with open(os.path.join(csrc, "fem_internal.cuh"), "rb") as fh:
@@ -70,8 +71,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def dom_kernel(level: int, ps: str) -> str:
-    """Name of the library's counting kernel for a (length, pass) launch."""
+def dom_kernel(level: int, ps: str, kind: int = 1) -> str:
+    """Name of the library's counting kernel for a (length, pass) launch; kind 2 is the
+    latest-chain kernel, 1 the per-thread machine."""
+    if kind == 2:
+        return f"k_chain<{level}, {ps}>"
     if ps == "exact":
         return "k_count_exact" if level <= 2 else "k_count_wide"
     return "k_count_wide" if level >= 4 else "k_count"
@@ -338,7 +342,7 @@ def run_ours(args, rank, world, local):
     all_t = sum(touched[k] * OPS_PER_TOUCHED[k[1]] for k in avg_ms) / (all_ms * 1e-3) / 1e12
     traffic = NCU_TRAFFIC.get(kernel_source_hash(), {}).get(cfg["name"], {}).get(
         f"{dom[0]}/{dom[1]}")
-    kname = f"{dom_kernel(dom[0], dom[1])} (level {dom[0]} {dom[1]} pass" + (
+    kname = f"{dom_kernel(dom[0], dom[1], dom_lv['kernel_' + dom[1]])} (level {dom[0]} {dom[1]} pass" + (
         f", {dom_seg} MapConcatenate segments)" if dom_seg > 1 else ")")
 
     # end to end through the public API with host (pinned) buffers

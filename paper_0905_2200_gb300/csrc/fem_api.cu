@@ -284,6 +284,7 @@ uint32_t choose_threads(fem_ctx *c, int N, int pass, bool mc, uint32_t R, uint32
 
 struct PassInfo {
     uint32_t segments = 1;
+    uint32_t kernel = 0;  // FEM_KERNEL_MACHINE or FEM_KERNEL_CHAIN
     float ms_kernel = 0, ms_stitch = 0;
 };
 
@@ -294,11 +295,21 @@ uint32_t ceil_log2(uint64_t v) {
 }
 
 // The latest-chain kernels count distinct-type episodes of 2..8 nodes in sets that come
-// in runs of shared prefixes; a few hundred candidates (a level's handful of survivors)
-// share too little for the prefix lists to pay.
-constexpr uint32_t kChainMinCandidates = 256;
+// in runs of shared prefixes (a handful of scattered candidates is split into parts by
+// the kernel and still counted there).
 bool chain_eligible(const fem_ctx *c, int N, bool distinct, uint32_t m) {
-    return distinct && N >= 2 && N <= FEM_MAX_LEN && c->clustered && m >= kChainMinCandidates;
+    return distinct && N >= 2 && N <= FEM_MAX_LEN && c->clustered && m > 0;
+}
+
+// The rule's kernel where no measurement says otherwise: the latest-chain kernels for the
+// exact pass over at least a block of candidates, whose per-thread machine (sliding-window
+// lists) costs the most per event; the per-thread machine for the relaxed pass, whose
+// single slot per node makes it cheap (the two measured within a few percent of each
+// other on the 64-type recording, and the chain form pays for class and list overflows).
+uint32_t rule_kernel(const fem_ctx *c, int N, int pass, bool distinct, uint32_t m) {
+    return chain_eligible(c, N, distinct, m) && pass == FEM_PASS_EXACT && m >= 256
+               ? FEM_KERNEL_CHAIN
+               : FEM_KERNEL_MACHINE;
 }
 
 // Block size of the latest-chain kernels: 256 threads, smaller blocks for few episodes.
@@ -335,7 +346,7 @@ int tune_pass(fem_ctx *c, const std::string &key, const StreamDev &s, const fem_
     // the shapes to time: per segment count and kernel the rule's block size and its
     // neighbours; the rule's own shape first
     const bool chain = chain_eligible(c, N, distinct, m);
-    const uint32_t k0 = c->cfg.kernel ? c->cfg.kernel : (chain ? FEM_KERNEL_CHAIN : FEM_KERNEL_MACHINE);
+    const uint32_t k0 = c->cfg.kernel ? c->cfg.kernel : rule_kernel(c, N, pass, distinct, m);
     std::vector<fem_ctx::Shape> shapes;
     for (uint32_t kind : {k0, k0 == FEM_KERNEL_CHAIN ? (uint32_t)FEM_KERNEL_MACHINE : (uint32_t)FEM_KERNEL_CHAIN}) {
         if (kind == FEM_KERNEL_CHAIN && !chain) continue;
@@ -423,7 +434,7 @@ int count_launch(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const
         if (it != c->tune.end()) P_t = it->second.P, T_t = it->second.T, K_t = it->second.kernel;
     }
     uint32_t kind = c->cfg.kernel ? c->cfg.kernel : K_t;
-    if (!kind) kind = chain_eligible(c, N, distinct, m) ? FEM_KERNEL_CHAIN : FEM_KERNEL_MACHINE;
+    if (!kind) kind = rule_kernel(c, N, pass, distinct, m);
     // (a configured or cached choice of the latest-chain kernels needs distinct types only)
     if (kind == FEM_KERNEL_CHAIN && !(distinct && N >= 2)) kind = FEM_KERNEL_MACHINE;
     CountParams p{};
@@ -486,6 +497,7 @@ int count_launch(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const
 // Kernel and stitch times of the last launched pass (its events have completed).
 void pass_info(fem_ctx *c, const PassLaunch &pl, PassInfo *info) {
     info->segments = pl.p.m ? pl.p.P : 0;
+    info->kernel = pl.p.m ? (pl.chain ? FEM_KERNEL_CHAIN : FEM_KERNEL_MACHINE) : 0u;
     info->ms_kernel = info->ms_stitch = 0;
     if (!pl.p.m) return;
     cudaEventElapsedTime(&info->ms_kernel, c->kev[0], c->kev[1]);
@@ -1414,6 +1426,7 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
         cudaEventElapsedTime(&ls.ms_generate, c->ev[0], c->ev[1]);
         cudaEventElapsedTime(&ls.ms_relaxed, c->ev[2], c->ev[3]);
         ls.segments = pi.segments;
+        ls.kernel_relaxed = pi.kernel;
         ls.ms_relaxed_kernel = pi.ms_kernel;
         ls.ms_relaxed_stitch = pi.ms_stitch;
         ls.survivors = ms;
@@ -1437,6 +1450,7 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
         cudaEventElapsedTime(&ls.ms_exact, c->ev[6], c->ev[7]);
         ls.ms_exact_kernel = pe.ms_kernel;
         ls.exact_segments = ms ? pe.segments : 0;
+        ls.kernel_exact = ms ? pe.kernel : 0;
         ls.frequent = f;
         c->stats.push_back(ls);
         if (f == 0) break;

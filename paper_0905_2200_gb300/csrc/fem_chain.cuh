@@ -29,8 +29,8 @@
 // chains after r; the transfer tables are the per-thread kernel's, so the same stitch
 // composes them.  A block whose prefixes do not fit its node tables, a list longer than
 // CH_LIST in one chunk, or an exact look-up that runs past a full carried tail marks
-// its candidates for the host's recount (ERR_NODES; more entry classes than CH_CLASSES:
-// ERR_CLASS), which uses the per-thread kernels.
+// its candidates for the host's recount (ERR_NODES; more entry classes than the thread
+// tracks: ERR_CLASS), which uses the per-thread kernels.
 #pragma once
 
 #include "fem_count.cuh"
@@ -39,8 +39,14 @@ namespace fem {
 
 constexpr int CHW = CHUNK / 32;   // bitmask words per chunk
 constexpr int CH_TAIL = 8;        // entries a node carries into the next chunk
-constexpr int CH_LIST = 48;       // admitted entries per node and chunk (depth >= 2)
-constexpr int CH_CLASSES = 4;     // MapConcatenate entry classes per thread (table slots used)
+constexpr int CH_LIST = 40;       // admitted entries per node and chunk (depth >= 2)
+// MapConcatenate entry classes a thread tracks (the table slots it uses), and the blocks
+// per SM its register budget is set for: two-node episodes fit four blocks per SM in
+// shared memory and keep four classes; longer ones fit three and keep eight.
+template <int N>
+constexpr int chain_classes = N == 2 ? 4 : 8;
+template <int N>
+constexpr int chain_blocks_per_sm = N == 2 ? 4 : 3;
 
 // A node's carried tail is double-buffered: lookups of chunk c read tail[c & 1] while
 // the node's build for chunk c writes tail[(c + 1) & 1], so the carry needs no barrier.
@@ -63,8 +69,8 @@ struct ChainLayout {
     static constexpr size_t TAIL = PRE + (size_t)NMX * CHW * 2;
     static constexpr size_t LIST = TAIL + (size_t)2 * NMX * EW * CH_TAIL * 4;
     static constexpr size_t KEYS = LIST + (size_t)LMX * EW * CH_LIST * 4;
-    static constexpr bool KEYS_SMEM = MC;
-    static size_t bytes(uint32_t T) { return KEYS + (KEYS_SMEM ? (size_t)CH_CLASSES * T * 4 : 0); }
+    // per-thread rows [q][T]: the part flags (row 0) and the class keys (rows 1..)
+    static size_t bytes(uint32_t T) { return KEYS + (size_t)(MC ? chain_classes<N> : 1) * T * 4; }
 };
 
 // Block-wide exclusive scan of one value per thread (blockDim.x a multiple of 32, <= 1024).
@@ -255,14 +261,19 @@ struct ChainBlock {
     }
 };
 
-// Count one (tile of candidates, segment) in latest-chain form.
+// Count one (tile of candidates, segment) in latest-chain form.  A tile whose prefixes
+// do not fit the node tables is counted in parts, each over the candidates of a run of
+// its leaf-parent prefixes (the segment's chunks are streamed once per part).
 template <int N, int PASS, bool MC>
 __device__ __forceinline__ void chain_block(const CountParams &p) {
     static_assert(N >= 2, "one-node episodes are counted by the per-thread kernels");
     using LY = ChainLayout<N, MC>;
     // entry classes tracked per thread (a window holding more capable last-node events
     // sends the episode to the recount, whose tables have S_RECOUNT slots)
-    constexpr int SC = MC ? CH_CLASSES : 1;
+    constexpr int SC = MC ? chain_classes<N> : 1;
+    // leaf-parent prefixes per part when a tile must be split (their ancestors are few in
+    // canonical order; a part that still overflows goes to the recount)
+    constexpr uint32_t PCAP = N == 2 ? (uint32_t)LY::NMX : (uint32_t)LY::LMX;
     uint8_t *smem = fem_chain_smem;
     const uint32_t SB = stage_bytes(p.offs);
     const uint32_t T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -275,6 +286,7 @@ __device__ __forceinline__ void chain_block(const CountParams &p) {
     ChainBlock<N, PASS, MC> cb;
     cb.nb = 2 * SB + 128;
     cb.evb = 0;
+    // per-thread rows [q][T]: row 0 the part flags, rows 1.. the class keys
     uint32_t *keys_s = reinterpret_cast<uint32_t *>(nodes + LY::KEYS) + tid;
 
     init_stage_bars(smem, SB);
@@ -283,7 +295,7 @@ __device__ __forceinline__ void chain_block(const CountParams &p) {
     if (tile * T >= m_cur) return;  // uniform
     const uint32_t ci = tile * T + tid;
 
-    // ------------------------------------------------------------ candidate and its nodes
+    // ------------------------------------------------------------ candidate
     uint4 rec = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
     bool ok = false;
     uint32_t E[N], lo_[N - 1], hi_[N - 1];
@@ -315,52 +327,34 @@ __device__ __forceinline__ void chain_block(const CountParams &p) {
 #pragma unroll
         for (int k = 0; k < N - 1; ++k) lo_[k] = hi_[k] = 0;
     }
-    // neighbours' records (the stage buffer is free until the first copy is issued)
-    uint4 *recs = reinterpret_cast<uint4 *>(smem);
-    recs[tid] = rec;
-    __syncthreads();
-    const uint4 prev = tid > 0 ? recs[tid - 1] : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu,
-                                                              0xFFFFFFFFu);
-    // node of each depth d (1..N-1): the prefix E_0..E_{d-1} with its d-1 edges; a thread
-    // opens a node where its prefix differs from the previous thread's
-    uint32_t nid[N];
-    uint32_t n_total = 0, n1 = 0;
+    // which prefix depths this candidate shares with the previous thread's (the stage
+    // buffer is free until the first copy is issued)
+    uint32_t same_mask = 0;
     {
+        uint4 *recs = reinterpret_cast<uint4 *>(smem);
+        recs[tid] = rec;
+        __syncthreads();
+        const uint4 prev = tid > 0 ? recs[tid - 1] : make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu,
+                                                                  0xFFFFFFFFu, 0xFFFFFFFFu);
         const uint64_t ta = ((uint64_t)rec.y << 32) | rec.x, tb = ((uint64_t)prev.y << 32) | prev.x;
         const uint64_t ia = ((uint64_t)rec.w << 32) | rec.z, ib = ((uint64_t)prev.w << 32) | prev.z;
 #pragma unroll
         for (int d = 1; d <= N - 1; ++d) {
             const uint64_t tm = d >= 8 ? ~0ull : ((1ull << (8 * d)) - 1ull);
             const uint64_t im = (d - 1) >= 8 ? ~0ull : ((1ull << (8 * (d - 1))) - 1ull);
-            const bool same = ((ta ^ tb) & tm) == 0 && ((ia ^ ib) & im) == 0;
-            const uint32_t is_new = ok && !same;
-            uint32_t tot;
-            const uint32_t ex = chain_block_scan(is_new, &tot, sc + 18);
-            nid[d] = n_total + ex + is_new - 1u;  // ok threads: the latest node opened at or before
-            if (tid == 0) sc[2 + d] = n_total, sc[10 + d] = tot;
-            if (is_new && n_total + ex < (uint32_t)LY::NMX) {
-                ChainNode *nd = cb.meta() + n_total + ex;
-                nd->type = E[d - 1];
-                nd->lo = d >= 2 ? lo_[d - 2] : 0u;
-                nd->hi = d >= 2 ? hi_[d - 2] : 0u;
-                nd->parent = d >= 2 ? nid[d - 1] : 0u;
-                nd->depth = (uint32_t)d;
-                nd->base = 0, nd->tlen[0] = 0, nd->tlen[1] = 0;
-            }
-            if (d == 1) n1 = tot;
-            n_total += tot;
+            if (((ta ^ tb) & tm) == 0 && ((ia ^ ib) & im) == 0) same_mask |= 1u << d;
         }
     }
-    __syncthreads();  // node records and counts are visible
-    cb.n1 = n1;
-    if (n_total > (uint32_t)LY::NMX || n_total - n1 > (uint32_t)LY::LMX) {
-        // the block's prefixes do not fit: its candidates go to the host's recount
-        if (ok) p.redo[ci] = 1;
-        if (tid == 0) atomicOr(p.err, ERR_NODES);
-        return;
+    // parts: the whole tile if its prefixes fit the tables, else runs of PCAP
+    // leaf-parent prefixes
+    uint32_t lp_rank = 0, lp_total = 0;
+    {
+        const uint32_t is_new = ok && !((same_mask >> (N - 1)) & 1u);
+        const uint32_t ex = chain_block_scan(is_new, &lp_total, sc + 18);
+        lp_rank = ex + is_new - 1u;  // ok threads
     }
-    const uint32_t pn = nid[N - 1];  // the leaf's parent node
-    const uint32_t El = E[N - 1], lo = lo_[N - 2], hi = hi_[N - 2];
+    bool split = false;
+    uint32_t part = 0, nparts = 1;
 
     // ------------------------------------------------------------ segment and window
     const uint32_t c_seg0 = seg * p.cps;
@@ -386,226 +380,261 @@ __device__ __forceinline__ void chain_block(const CountParams &p) {
             const uint32_t tR = p.cfirst[c_end];
             Xn = (uint64_t)tR >= W ? (uint32_t)(tR - W) : 0u;
         }
-        if (tid == 0) sc[0] = c_seg0, sc[1] = 0;
-        __syncthreads();
-        if (ok) atomicMin(&sc[0], c_w);
-        __syncthreads();
-    } else {
-        if (tid == 0) sc[1] = 0;
-        __syncthreads();
     }
-    const uint32_t c_first = MC ? sc[0] : c_seg0;
-
-    // ------------------------------------------------------------ counting state
-    // single segment: st = last completion + 1.  MapConcatenate: per entry class its
-    // st, count and (class "none" aside) key, as in the per-thread kernel
-    uint32_t cnt = 0, st = 0;
-    uint32_t c_st[SC], c_cnt[SC], c_key[LY::KEYS_SMEM ? 1 : SC];
-#pragma unroll
-    for (int j = 0; j < SC; ++j) c_st[j] = 0, c_cnt[j] = 0;
-#pragma unroll
-    for (int j = 0; j < (LY::KEYS_SMEM ? 1 : SC); ++j) c_key[j] = CLS_NONE;
-    uint32_t used = 0, umask = 0;
-    bool c0_done = false, class_overflow = false, ovf = false;
-    auto set_key = [&](int q0, uint32_t v) {
-        if constexpr (LY::KEYS_SMEM) {
-            keys_s[(uint32_t)q0 * T] = v;
-        } else {
-#pragma unroll
-            for (int q = 1; q < SC; ++q)
-                if (q == q0) c_key[q] = v;
-        }
-    };
-    auto get_key = [&](int q) -> uint32_t {
-        if constexpr (LY::KEYS_SMEM) return q == 0 ? CLS_NONE : keys_s[(uint32_t)q * T];
-        else return c_key[q];
-    };
-
-    // ------------------------------------------------------------ chunk pipeline
+    const uint32_t El = E[N - 1], lo = lo_[N - 2], hi = hi_[N - 2];
     const uint32_t chunk_ev_bytes = CHUNK * 8u;
     const uint32_t chunk_off_bytes = p.offs * 2u;
-    const uint32_t q0 = 0;
     auto issue = [&](uint32_t c, uint32_t s) {
         uint8_t *dst = smem + s * SB;
         mbar_expect_tx(&bar[s], chunk_ev_bytes + chunk_off_bytes);
         bulk_g2s(dst, p.bev + (uint64_t)c * CHUNK, chunk_ev_bytes, &bar[s]);
         bulk_g2s(dst + chunk_ev_bytes, p.boff + (uint64_t)c * p.offs, chunk_off_bytes, &bar[s]);
     };
-    __syncthreads();  // the record exchange is done with the stage buffer
-    if (tid == 0) {
-        fence_proxy_async_smem();
-        if (c_first < c_end) issue(c_first, 0);
-        if (c_first + 1 < c_end) issue(c_first + 1, 1);
-    }
-    bool bail = false;
-    uint32_t c = c_first;
-    for (; c < c_end; ++c) {
-        const uint32_t j = q0 + (c - c_first), s = j & 1u, par = (j >> 1) & 1u;
-        const bool waited = mbar_wait_bounded(&bar[s], par, p.err);
-        if (!__syncthreads_and(waited)) {
-            bail = true;
-            break;
-        }
-        cb.evb = s * SB;
-        cb.cbase = c * CHUNK;
-        cb.par = (c - c_first) & 1u;
-        // prefix lists, depth by depth (each build also writes the node's next tail)
-        bool bovf = false;
-        for (int d = 1; d <= N - 1; ++d) {
-            const uint32_t b0 = sc[2 + d], nb = sc[10 + d];
-            for (uint32_t nd = b0 + warp; nd < b0 + nb; nd += nwarps) bovf |= cb.build(nd, lane);
-            __syncthreads();
-        }
-        if (bovf && lane == 0) sc[1] = 1;
-        // the leaf: this thread's last node's events, looked up in the parent's list
-        if (ok && c >= c_w) {
-            const uint32_t g0 = cb.off()[El], g1 = cb.off()[El + 1];
-            const uint32_t ptl = cb.meta()[pn].tlen[cb.par], pbase = cb.meta()[pn].base;
-            auto adm_at = [&](const uint2 e, uint32_t &S, uint32_t &St) -> bool {
-                uint32_t t;
-                return cb.template lookup<N == 2>(pn, ptl, pbase, e.y, e.x, lo, t, S, St, ovf) &&
-                       e.x - t <= hi;
-            };
-            if (!MC || (c >= c_seg0 && umask == 0)) {
-                // one class: inside the segment with every entry class merged, or one segment.
-                // Two events per step: their look-ups are independent, the greedy is not.
-                auto apply = [&](bool a, uint32_t y, uint32_t S, uint32_t St) {
-                    if (!a) return;
-                    const uint32_t gidx = cb.cbase + y;
-                    if constexpr (!MC) {
-                        if (S >= st) ++cnt, st = gidx + 1;
-                    } else {
-                        if (S >= c_st[0] && St >= X) c_st[0] = gidx + 1, ++c_cnt[0], c0_done = true;
-                    }
-                };
-                uint32_t jj = g0;
-                for (; jj + 2 <= g1; jj += 2) {
-                    const uint2 e0 = cb.ev()[jj], e1 = cb.ev()[jj + 1];
-                    uint32_t S0, St0, S1, St1;
-                    const bool a0 = adm_at(e0, S0, St0);
-                    const bool a1 = adm_at(e1, S1, St1);
-                    apply(a0, e0.y, S0, St0);
-                    apply(a1, e1.y, S1, St1);
-                }
-                if (jj < g1) {
-                    const uint2 e = cb.ev()[jj];
-                    uint32_t S, St;
-                    const bool a = adm_at(e, S, St);
-                    apply(a, e.y, S, St);
-                }
-            } else if constexpr (MC) {
-                for (uint32_t jj = g0; jj < g1; ++jj) {
-                    const uint2 e = cb.ev()[jj];
-                    uint32_t S, St, tp;
-                    const bool found = cb.template lookup<N == 2>(pn, ptl, pbase, e.y, e.x, lo, tp,
-                                                                   S, St, ovf);
-                    if (!found) continue;
-                    // Every later event of this node looks up this parent entry or a later
-                    // one, so its chain starts at S or later: a class whose threshold is at
-                    // most S admits all of them, as class "none" does when its conditions
-                    // hold for S too -- such a class behaves like class "none" from here on.
-                    if (umask && S >= c_st[0] && St >= X) {
-#pragma unroll
-                        for (int q = 1; q < SC; ++q) {
-                            if (((umask >> q) & 1u) && c_st[q] <= S) {
-                                c_cnt[q] -= c_cnt[0];
-                                umask &= ~(1u << q);
-                                if (cb.cbase + e.y < L) used &= ~(1u << q);
-                            }
-                        }
-                    }
-                    if (e.x - tp > hi) continue;
-                    const uint32_t ti = e.x, gidx = cb.cbase + e.y;
-                    const uint32_t inc = gidx >= L ? 1u : 0u;
-                    if (S >= c_st[0] && St >= X) c_st[0] = gidx + 1, c_cnt[0] += inc, c0_done = true;
-                    if (umask) {
-#pragma unroll
-                        for (int q = 1; q < SC; ++q) {
-                            if (!((umask >> q) & 1u)) continue;
-                            if (S >= c_st[q]) {
-                                if (!inc) {  // refuted: completes before the segment
-                                    used &= ~(1u << q), umask &= ~(1u << q);
-                                    continue;
-                                }
-                                c_st[q] = gidx + 1, ++c_cnt[q];
-                            }
-                            if (c_st[q] == c_st[0]) {
-                                c_cnt[q] -= c_cnt[0];
-                                umask &= ~(1u << q);
-                                if (!inc) used &= ~(1u << q);
-                            }
-                        }
-                    }
-                    if (!inc && ti >= X && c_st[0] != gidx + 1) {
-                        // entry class r = gidx: the chains after it
-                        constexpr uint32_t all_slots = SC >= 32 ? 0xFFFFFFFFu : (1u << SC) - 1u;
-                        const uint32_t free_slots = ~used & (all_slots & ~1u);
-                        if (free_slots) {
-                            const int qn = __ffs(free_slots) - 1;
-                            set_key(qn, gidx);
-#pragma unroll
-                            for (int q = 1; q < SC; ++q)
-                                if (q == qn) c_st[q] = gidx + 1, c_cnt[q] = 0;
-                            used |= 1u << qn;
-                            umask |= 1u << qn;
-                        } else {
-                            class_overflow = true;
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        if (tid == 0 && c + 2 < c_end) {
-            fence_proxy_async_smem();
-            issue(c + 2, s);
-        }
-    }
-    if (bail) {
-        if (tid == 0) {
-            for (uint32_t cc = c; cc < min(c + 2, c_end); ++cc) {
-                const uint32_t jq = q0 + (cc - c_first);
-                mbar_wait_bounded(&bar[jq & 1u], (jq >> 1) & 1u, p.err);
-            }
-        }
-        return;
-    }
+    uint32_t jbase = 0;  // chunk stages consumed so far (their mbarrier phases)
 
-    // ------------------------------------------------------------ results
-    if (!ok) {
-        if (ci < m_cur && !MC) p.out[ci] = 0;
-        if (ci >= m_cur) return;
-    }
-    const bool bad = sc[1] != 0 || ovf || class_overflow;
-    if (ok && bad) {
-        atomicOr(p.err, (class_overflow ? ERR_CLASS : 0u) | (ovf || sc[1] != 0 ? ERR_NODES : 0u));
-        p.redo[ci] = 1;
-    }
-    if constexpr (!MC) {
-        p.out[ci] = ok ? cnt : 0u;
-    } else {
-        uint4 *tab = p.tables + ((uint64_t)seg * p.m + ci) * S_MAX;
-        const uint32_t n_slots = used ? 32u - __clz(used) : 1u;
-        static_assert(SC <= S_MAX, "the transfer tables hold S_MAX classes");
+    for (uint32_t pt = 0; pt < nparts; ++pt) {
+        const bool act = ok && (!split || part == pt);
+        // ------------------------------------------------------------ this part's nodes
+        // node of each depth d (1..N-1): the prefix E_0..E_{d-1} with its d-1 edges; an
+        // active thread opens a node where its prefix differs from the previous thread's
+        // or the previous thread is not in this part
+        keys_s[0] = act;
+        __syncthreads();
+        const bool prev_act = tid > 0 && keys_s[-1] != 0;
+        uint32_t nid[N];
+        uint32_t n_total = 0, n1 = 0;
 #pragma unroll
-        for (int q = 0; q < SC; ++q) {
-            if ((uint32_t)q >= n_slots) break;
-            uint4 e = make_uint4(CLS_EMPTY, 0, CLS_NONE, q == 0 ? n_slots : 0u);
-            if (ok && (q == 0 || ((used >> q) & 1u))) {
-                const bool merged = q > 0 && !((umask >> q) & 1u);
-                const uint32_t cntq = merged ? c_cnt[0] + c_cnt[q] : c_cnt[q];
-                const uint32_t stq = merged ? c_st[0] : c_st[q];
-                uint32_t ex = (q == 0 && !c0_done) ? CLS_NONE : stq - 1u;
-                if (ex != CLS_NONE && !last_seg && p.t[ex] < Xn) ex = CLS_NONE;
-                e = make_uint4(get_key(q), cntq, ex, q == 0 ? n_slots : 0u);
+        for (int d = 1; d <= N - 1; ++d) {
+            const uint32_t is_new = act && !(prev_act && ((same_mask >> d) & 1u));
+            uint32_t tot;
+            const uint32_t ex = chain_block_scan(is_new, &tot, sc + 18);
+            nid[d] = n_total + ex + is_new - 1u;  // active threads: the latest node opened
+            if (tid == 0) sc[2 + d] = n_total, sc[10 + d] = tot;
+            if (is_new && n_total + ex < (uint32_t)LY::NMX) {
+                ChainNode *nd = cb.meta() + n_total + ex;
+                nd->type = E[d - 1];
+                nd->lo = d >= 2 ? lo_[d - 2] : 0u;
+                nd->hi = d >= 2 ? hi_[d - 2] : 0u;
+                nd->parent = d >= 2 ? nid[d - 1] : 0u;
+                nd->depth = (uint32_t)d;
+                nd->base = 0, nd->tlen[0] = 0, nd->tlen[1] = 0;
             }
-            tab[q] = e;
+            if (d == 1) n1 = tot;
+            n_total += tot;
+        }
+        if (tid == 0) sc[0] = c_seg0, sc[1] = 0;
+        __syncthreads();  // node records, counts and the scalars are visible
+        cb.n1 = n1;
+        if (n_total > (uint32_t)LY::NMX || n_total - n1 > (uint32_t)LY::LMX) {
+            // the whole tile does not fit: count it in parts (uniform); two-node tiles in
+            // canonical order have a few first types, so they go to the recount instead
+            if (N >= 3 && !split) {
+                split = true;
+                part = lp_rank / PCAP;
+                nparts = (lp_total + PCAP - 1) / PCAP;
+                pt = ~0u;  // the loop's increment starts the parts at 0
+                continue;
+            }
+            // even this part's prefixes do not fit: its candidates go to the host's recount
+            if (act) p.redo[ci] = 1;
+            if (tid == 0) atomicOr(p.err, ERR_NODES);
+            continue;  // uniform
+        }
+        const uint32_t pn = nid[N - 1];  // the leaf's parent node
+        if (MC && act) atomicMin(&sc[0], c_w);
+        __syncthreads();
+        const uint32_t c_first = MC ? sc[0] : c_seg0;
+
+        // ------------------------------------------------------------ counting state
+        // single segment: st = last completion + 1.  MapConcatenate: per entry class its
+        // st, count and (class "none" aside) key, as in the per-thread kernel
+        uint32_t cnt = 0, st = 0;
+        uint32_t c_st[SC], c_cnt[SC];
+#pragma unroll
+        for (int j = 0; j < SC; ++j) c_st[j] = 0, c_cnt[j] = 0;
+        uint32_t used = 0, umask = 0;
+        bool c0_done = false, class_overflow = false, ovf = false;
+        auto set_key = [&](int q0, uint32_t v) { keys_s[(uint32_t)q0 * T] = v; };
+        auto get_key = [&](int q) -> uint32_t { return q == 0 ? CLS_NONE : keys_s[(uint32_t)q * T]; };
+
+        // ------------------------------------------------------------ chunk pipeline
+        if (tid == 0) {
+            fence_proxy_async_smem();
+            if (c_first < c_end) issue(c_first, jbase & 1u);
+            if (c_first + 1 < c_end) issue(c_first + 1, (jbase + 1) & 1u);
+        }
+        bool bail = false;
+        uint32_t c = c_first;
+        for (; c < c_end; ++c) {
+            const uint32_t j = jbase + (c - c_first), s = j & 1u, par = (j >> 1) & 1u;
+            const bool waited = mbar_wait_bounded(&bar[s], par, p.err);
+            if (!__syncthreads_and(waited)) {
+                bail = true;
+                break;
+            }
+            cb.evb = s * SB;
+            cb.cbase = c * CHUNK;
+            cb.par = (c - c_first) & 1u;
+            // prefix lists, depth by depth (each build also writes the node's next tail)
+            bool bovf = false;
+            for (int d = 1; d <= N - 1; ++d) {
+                const uint32_t b0 = sc[2 + d], nb = sc[10 + d];
+                for (uint32_t nd = b0 + warp; nd < b0 + nb; nd += nwarps) bovf |= cb.build(nd, lane);
+                __syncthreads();
+            }
+            if (bovf && lane == 0) sc[1] = 1;
+            // the leaf: this thread's last node's events, looked up in the parent's list
+            if (act && c >= c_w) {
+                const uint32_t g0 = cb.off()[El], g1 = cb.off()[El + 1];
+                const uint32_t ptl = cb.meta()[pn].tlen[cb.par], pbase = cb.meta()[pn].base;
+                auto adm_at = [&](const uint2 e, uint32_t &S, uint32_t &St) -> bool {
+                    uint32_t t;
+                    return cb.template lookup<N == 2>(pn, ptl, pbase, e.y, e.x, lo, t, S, St, ovf) &&
+                           e.x - t <= hi;
+                };
+                if (!MC || (c >= c_seg0 && umask == 0)) {
+                    // one class: inside the segment with every entry class merged, or one
+                    // segment.  Two events per step: their look-ups are independent, the
+                    // greedy is not.
+                    auto apply = [&](bool a, uint32_t y, uint32_t S, uint32_t St) {
+                        if (!a) return;
+                        const uint32_t gidx = cb.cbase + y;
+                        if constexpr (!MC) {
+                            if (S >= st) ++cnt, st = gidx + 1;
+                        } else {
+                            if (S >= c_st[0] && St >= X) c_st[0] = gidx + 1, ++c_cnt[0], c0_done = true;
+                        }
+                    };
+                    uint32_t jj = g0;
+                    for (; jj + 2 <= g1; jj += 2) {
+                        const uint2 e0 = cb.ev()[jj], e1 = cb.ev()[jj + 1];
+                        uint32_t S0, St0, S1, St1;
+                        const bool a0 = adm_at(e0, S0, St0);
+                        const bool a1 = adm_at(e1, S1, St1);
+                        apply(a0, e0.y, S0, St0);
+                        apply(a1, e1.y, S1, St1);
+                    }
+                    if (jj < g1) {
+                        const uint2 e = cb.ev()[jj];
+                        uint32_t S, St;
+                        const bool a = adm_at(e, S, St);
+                        apply(a, e.y, S, St);
+                    }
+                } else if constexpr (MC) {
+                    for (uint32_t jj = g0; jj < g1; ++jj) {
+                        const uint2 e = cb.ev()[jj];
+                        uint32_t S, St, tp;
+                        const bool found = cb.template lookup<N == 2>(pn, ptl, pbase, e.y, e.x, lo,
+                                                                       tp, S, St, ovf);
+                        if (!found) continue;
+                        // Every later event of this node looks up this parent entry or a
+                        // later one, so its chain starts at S or later: a class whose
+                        // threshold is at most S admits all of them, as class "none" does
+                        // when its conditions hold for S too -- such a class behaves like
+                        // class "none" from here on.
+                        if (umask && S >= c_st[0] && St >= X) {
+#pragma unroll
+                            for (int q = 1; q < SC; ++q) {
+                                if (((umask >> q) & 1u) && c_st[q] <= S) {
+                                    c_cnt[q] -= c_cnt[0];
+                                    umask &= ~(1u << q);
+                                    if (cb.cbase + e.y < L) used &= ~(1u << q);
+                                }
+                            }
+                        }
+                        if (e.x - tp > hi) continue;
+                        const uint32_t ti = e.x, gidx = cb.cbase + e.y;
+                        const uint32_t inc = gidx >= L ? 1u : 0u;
+                        if (S >= c_st[0] && St >= X) c_st[0] = gidx + 1, c_cnt[0] += inc, c0_done = true;
+                        if (umask) {
+#pragma unroll
+                            for (int q = 1; q < SC; ++q) {
+                                if (!((umask >> q) & 1u)) continue;
+                                if (S >= c_st[q]) {
+                                    if (!inc) {  // refuted: completes before the segment
+                                        used &= ~(1u << q), umask &= ~(1u << q);
+                                        continue;
+                                    }
+                                    c_st[q] = gidx + 1, ++c_cnt[q];
+                                }
+                                if (c_st[q] == c_st[0]) {
+                                    c_cnt[q] -= c_cnt[0];
+                                    umask &= ~(1u << q);
+                                    if (!inc) used &= ~(1u << q);
+                                }
+                            }
+                        }
+                        if (!inc && ti >= X && c_st[0] != gidx + 1) {
+                            // entry class r = gidx: the chains after it
+                            constexpr uint32_t all_slots = SC >= 32 ? 0xFFFFFFFFu : (1u << SC) - 1u;
+                            const uint32_t free_slots = ~used & (all_slots & ~1u);
+                            if (free_slots) {
+                                const int qn = __ffs(free_slots) - 1;
+                                set_key(qn, gidx);
+#pragma unroll
+                                for (int q = 1; q < SC; ++q)
+                                    if (q == qn) c_st[q] = gidx + 1, c_cnt[q] = 0;
+                                used |= 1u << qn;
+                                umask |= 1u << qn;
+                            } else {
+                                class_overflow = true;
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            if (tid == 0 && c + 2 < c_end) {
+                fence_proxy_async_smem();
+                issue(c + 2, s);
+            }
+        }
+        if (bail) {
+            if (tid == 0) {
+                for (uint32_t cc = c; cc < min(c + 2, c_end); ++cc) {
+                    const uint32_t jq = jbase + (cc - c_first);
+                    mbar_wait_bounded(&bar[jq & 1u], (jq >> 1) & 1u, p.err);
+                }
+            }
+            return;
+        }
+        jbase += c_end > c_first ? c_end - c_first : 0u;
+
+        // ------------------------------------------------------------ results
+        if (ci < m_cur && !ok && !MC) p.out[ci] = 0;
+        const bool mine = act || (!ok && ci < m_cur && pt + 1 == nparts);
+        if (!mine) continue;
+        const bool bad = act && (sc[1] != 0 || ovf || class_overflow);
+        if (bad) {
+            atomicOr(p.err, (class_overflow ? ERR_CLASS : 0u) | (ovf || sc[1] != 0 ? ERR_NODES : 0u));
+            p.redo[ci] = 1;
+        }
+        if constexpr (!MC) {
+            p.out[ci] = act ? cnt : 0u;
+        } else {
+            uint4 *tab = p.tables + ((uint64_t)seg * p.m + ci) * S_MAX;
+            const uint32_t n_slots = used ? 32u - __clz(used) : 1u;
+            static_assert(SC <= S_MAX, "the transfer tables hold S_MAX classes");
+#pragma unroll
+            for (int q = 0; q < SC; ++q) {
+                if ((uint32_t)q >= n_slots) break;
+                uint4 e = make_uint4(CLS_EMPTY, 0, CLS_NONE, q == 0 ? n_slots : 0u);
+                if (act && (q == 0 || ((used >> q) & 1u))) {
+                    const bool merged = q > 0 && !((umask >> q) & 1u);
+                    const uint32_t cntq = merged ? c_cnt[0] + c_cnt[q] : c_cnt[q];
+                    const uint32_t stq = merged ? c_st[0] : c_st[q];
+                    uint32_t ex = (q == 0 && !c0_done) ? CLS_NONE : stq - 1u;
+                    if (ex != CLS_NONE && !last_seg && p.t[ex] < Xn) ex = CLS_NONE;
+                    e = make_uint4(get_key(q), cntq, ex, q == 0 ? n_slots : 0u);
+                }
+                tab[q] = e;
+            }
         }
     }
 }
 
 template <int N, int PASS, bool MC>
-__global__ void __launch_bounds__(256, 4) k_chain(const CountParams p) {
+__global__ void __launch_bounds__(256, chain_blocks_per_sm<N>) k_chain(const CountParams p) {
     chain_block<N, PASS, MC>(p);
 }
 

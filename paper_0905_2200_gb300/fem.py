@@ -53,7 +53,8 @@ class fem_level_stats(ctypes.Structure):
                 ("ms_exact", ctypes.c_float), ("ms_relaxed_kernel", ctypes.c_float),
                 ("ms_relaxed_stitch", ctypes.c_float), ("ms_exact_kernel", ctypes.c_float),
                 ("exact_segments", ctypes.c_uint32), ("touched_relaxed", ctypes.c_uint64),
-                ("touched_exact", ctypes.c_uint64)]
+                ("touched_exact", ctypes.c_uint64), ("kernel_relaxed", ctypes.c_uint32),
+                ("kernel_exact", ctypes.c_uint32)]
 
 
 class fem_job(ctypes.Structure):

@@ -93,6 +93,20 @@ def test_chain_block_sizes_and_ragged_tail(ctx, mid, pass_, threads):
 
 
 @pytest.mark.parametrize("pass_", PASSES)
+@pytest.mark.parametrize("N", [2, 3, 4])
+@pytest.mark.parametrize("segments", [1, 6])
+def test_chain_many_prefixes_counted_in_parts(ctx, mid, pass_, N, segments):
+    """A block whose candidates have more distinct prefixes than its node tables hold
+    counts them in parts (runs of prefixes, the segment streamed once per part)."""
+    ty, t, K, sid = mid
+    L, E, iv = families(0x5A + 10 * N + segments, K, N, 300, 1 if N > 2 else 3)
+    rec = fem.pack_episodes(L, E, iv)
+    fem.fem_set_config(ctx, kernel=fem.KERNEL_CHAIN, segments=segments)
+    got = fem.fem_count_candidates(ctx, sid, rec, I_MS4, pass_)
+    assert_counts_equal(got, oracle_counts(ty, t, L, E, iv, I_MS4, pass_), f"parts N={N}")
+
+
+@pytest.mark.parametrize("pass_", PASSES)
 def test_chain_unshared_prefixes_fall_back(ctx, mid, pass_):
     """Random (unsorted) candidates: a block sees more distinct prefixes than its node
     table holds; those candidates are recounted by the per-thread kernels."""
