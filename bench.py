@@ -858,7 +858,7 @@ def run_serving(args, rank, world, local):
     all_reqs = {rate: make_requests(rate, 0xFE05 + 17 * rank + int(rate * 1000)) for rate in rates}
     clocks = ClockSampler(local)
     clocks.start()
-    sweep = [session(all_reqs[rate]) for rate in rates]
+    sweep = [session(all_reqs[rate]) for rate in rates] if not args.saturation_only else []
 
     # saturation: the one-shot requests of the busiest load over the full streams' last
     # 60 s, all at once through the server, then one after another through the plain path
@@ -879,7 +879,7 @@ def run_serving(args, rank, world, local):
     fem.fem_server_drain(srv)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    rids = []
+    rids, burst_retries = [], 0
     for r in oneshots:
         while True:
             try:
@@ -889,8 +889,10 @@ def run_serving(args, rank, world, local):
             except fem.FemError as e:  # memory or slots full: wait for work to finish
                 if e.status != -6:
                     raise
+                burst_retries += 1
                 fem.fem_server_poll(srv)
                 time.sleep(0.0002)
+    submit_s = time.perf_counter() - t0
     fem.fem_server_drain(srv)
     burst_s = time.perf_counter() - t0
     served, burst_units = [], 0.0
@@ -917,8 +919,8 @@ def run_serving(args, rank, world, local):
     fem.fem_destroy(ctx)
     if rank != 0:
         return
-    head = next(x for x, rate in zip(sweep, rates) if rate == args.req_rate) if args.req_rate in rates \
-        else sweep[0]
+    head = (next(x for x, rate in zip(sweep, rates) if rate == args.req_rate)
+            if args.req_rate in rates and sweep else (sweep[0] if sweep else {"value": 0.0}))
     line = {
         "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
         "steps": int(round(sess / tick)), "warmup": 0, "ms_per_step": tick * 1e3,
@@ -932,6 +934,7 @@ def run_serving(args, rank, world, local):
         "load_sweep": sweep,
         "saturation": {"oneshot_requests": len(oneshots),
                        "served": {"s": burst_s, "value": burst_units / burst_s,
+                                  "submit_s": submit_s, "admission_retries": burst_retries,
                                   "form": "all submitted at once, continuous batching over 8 lanes"},
                        "plain": {"s": plain_s, "value": burst_units / plain_s,
                                  "form": "one fem_count_two_pass call after another"},
@@ -1008,6 +1011,8 @@ def main(argv=None):
                     help="--workload serving: the offered load the line's value is quoted at")
     ap.add_argument("--req-rates", default="5,10,20,50",
                     help="--workload serving: offered loads swept (requests/s)")
+    ap.add_argument("--saturation-only", action="store_true",
+                    help="--workload serving: skip the live sessions")
     ap.add_argument("--serve-budget-gb", type=int, default=16)
     ap.add_argument("--recordings", type=int, default=256)
     ap.add_argument("--window-us", type=int, default=40_000,

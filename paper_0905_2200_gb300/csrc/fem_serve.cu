@@ -128,21 +128,20 @@ struct Request {
 };
 
 constexpr uint32_t kServeRing = 16;  // exact-pass clusters per node in serving
-// A one-shot request's relaxed pass gives each length group about this many threads
-// per SM through MapConcatenate segments (a 1k-candidate group alone would fill a few
-// SMs); its transfer tables are part of the request's device memory.
-constexpr uint32_t kServeThreadsPerSM = 512;
+// A one-shot request's passes give each length group about this many threads per SM
+// through MapConcatenate segments (a 1k-candidate group alone would fill a few SMs), as
+// the context's counts do; the transfer tables are part of the request's device memory.
+constexpr uint32_t kServeThreadsPerSM = 2048;
 
-// Segments of a one-shot relaxed pass over nch chunks for m candidates (1: none).  Below
-// four segments the tables cost more than the parallelism they buy.  The tables of one
-// request may take an eighth of the arena at most.
+// Segments of a one-shot pass over nch chunks for m candidates (1: none).  The tables
+// of one request may take an eighth of the arena at most.
 uint32_t oneshot_segments(uint32_t m, uint32_t nch, int sm_count, size_t arena_bytes) {
-    if (m == 0 || nch < 4) return 1;
+    if (m == 0 || nch < 2) return 1;
     const uint64_t target = (uint64_t)sm_count * kServeThreadsPerSM;
     uint64_t P = std::min<uint64_t>((target + m - 1) / m, nch);
     const uint64_t cap = arena_bytes / 8 / (S_MAX * sizeof(uint4)) / m;
     P = std::min<uint64_t>(P, cap);
-    return P < 4 ? 1u : (uint32_t)P;
+    return P < 2 ? 1u : (uint32_t)P;
 }
 
 }  // namespace
@@ -263,14 +262,26 @@ int enqueue_oneshot(fem_server *v, Request &r, const StreamDev &s, uint32_t R, b
             SCK(launch_stitch(r.tables, g.m, P, r.rel + g.off, r.redo + g.off, r.err, st));
         SCK(launch_compact(r.rel + g.off, nullptr, r.theta, g.m, r.idx + g.off,
                            r.cnt + (&g - r.groups.data()), r.scratch, st));
+        // the exact pass over the survivors (their number stays on the device): a grid for
+        // all g.m, the blocks past the survivors leave at once; with the relaxed pass's
+        // segments, so that a few survivors still spread over the GPU.  The stitch runs
+        // over g.m slots too; those past the survivors hold the relaxed pass's tables and
+        // their results are never scattered.
         CountParams x = base_params(s, r, g, FEM_PASS_EXACT);
         x.cands = r.cands + g.off;
         x.gather = r.idx + g.off;
         x.m = g.m;
         x.m_dev = r.cnt + (&g - r.groups.data());
         x.out = r.ex + g.off;
-        SCK(launch_count(g.N, FEM_PASS_EXACT, false, R,
-                         serve_threads(g.N, FEM_PASS_EXACT, R, s.offs), x, st));
+        const bool xmc = P > 1 && count_config_supported(g.N, FEM_PASS_EXACT, true, R);
+        if (xmc) {
+            x.cps = p.cps;
+            x.P = P;
+            x.tables = r.tables;
+        }
+        SCK(launch_count(g.N, FEM_PASS_EXACT, xmc, R,
+                         serve_threads(g.N, FEM_PASS_EXACT, R, s.offs, xmc), x, st));
+        if (xmc) SCK(launch_stitch(r.tables, g.m, P, r.ex + g.off, r.redo + g.off, r.err, st));
         SCK(cudaMemsetAsync(r.out + g.off, 0, (size_t)g.m * 4, st));
         SCK(cudaMemsetAsync(r.flags + g.off, 0, g.m, st));
         SCK(launch_scatter_dev(r.ex + g.off, r.idx + g.off, x.m_dev, g.m, r.out + g.off,

@@ -142,3 +142,41 @@ def test_admission_by_memory(ctx):
         assert_counts_equal(c2[0], c1[0], "same request twice")
     finally:
         fem.fem_server_destroy(srv)
+
+
+def test_serving_32_stream_workload_equals_oracle(ctx):
+    """The serving workload's configuration: 32 live streams (16-128 types, 10-100 Hz,
+    embedded chains) fed in 100 ms chunks; one one-shot request per stream over its last
+    5 s and eight standing requests, submitted while the others run.  Every result equals
+    the oracle on the event range it covers."""
+    raw = synth.serving_streams(seed=0xFE05, n_streams=32, duration_s=20.0)
+    streams = [(x["stream"].types, x["stream"].t, x["stream"].n_types, None) for x in raw]
+    plan, sets = [], {}
+    for i, (ty, t, K, _) in enumerate(streams):
+        L, E, iv, rec = request_set(0x3200 + i, K, 400)
+        sets[f"o{i}"] = (L, E, iv)
+        plan.append((100 + 2 * i, i, f"o{i}", rec, 8, fem.REQ_ONESHOT, 5_000_000))
+    for k in range(8):
+        i = 4 * k
+        ty, t, K, _ = streams[i]
+        L, E, iv, rec = request_set(0x3300 + k, K, 300)
+        sets[f"s{k}"] = (L, E, iv)
+        plan.append((60 + k, i, f"s{k}", rec, 0, fem.REQ_STANDING, 0))
+    res = run_scenario(ctx, streams, plan)
+    assert len(res) == len(plan)
+    for name, (c, f, ev, status, (i, fed, mode, win)) in res.items():
+        assert status == 0, name
+        ty, t, K, _ = streams[i]
+        L, E, iv = sets[name]
+        if mode == fem.REQ_ONESHOT:
+            end = fed
+            begin = end - ev
+            assert t[begin] >= t[end - 1] - win and (begin == 0 or t[begin - 1] < t[end - 1] - win)
+            _, ex_o, sv_o = oracle.two_pass(ty[begin:end], t[begin:end], L, E, iv, I_MS4, 8)
+            assert_counts_equal(f, sv_o, f"{name} survived")
+            assert_counts_equal(c, ex_o, f"{name} exact")
+        else:
+            begin, end = fed, len(t)
+            assert ev == end - begin
+            want = oracle.count_batch(ty[begin:end], t[begin:end], L, E, iv, I_MS4, oracle.EXACT)
+            assert_counts_equal(c, want, f"{name} standing")
