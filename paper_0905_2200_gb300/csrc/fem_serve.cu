@@ -220,21 +220,27 @@ CountParams base_params(const StreamDev &s, const Request &r, const Group &g, in
     return p;
 }
 
-uint32_t serve_threads(int N, int pass, uint32_t R, uint32_t offs, bool mc = false) {
+uint32_t serve_threads(int N, int pass, uint32_t R, uint32_t offs, bool mc = false,
+                       uint32_t classes = S_MAX) {
     for (uint32_t T : {128u, 64u, 32u})
-        if (count_smem_bytes(N, pass, mc, R, T, offs) <= 100 * 1024) return T;
+        if (count_smem_bytes(N, pass, mc, R, T, offs, classes) <= 100 * 1024) return T;
     return 32;
 }
 
 // One-shot: Algorithm 4 over [ev_begin, ev_end) of the stream, per length group,
-// with every size on the device (no host round trip).  With mc, a group whose
-// candidates are few runs its relaxed pass over MapConcatenate segments of the range
-// (the exact pass counts the survivors, usually few, in one segment).
-int enqueue_oneshot(fem_server *v, Request &r, const StreamDev &s, uint32_t R, bool mc) {
+// with every size on the device (no host round trip).  A group of few candidates runs
+// both passes over MapConcatenate segments of the range (the exact pass over the
+// survivors, whose number stays on the device).  attempt 0: the rule's segments, 8
+// entry classes per table, exact lists of kServeRing clusters; attempt 1 (after a
+// capacity guard tripped): a quarter of the segments with 32 classes per table in the
+// same memory and lists of 32 clusters; attempt 2: one segment, lists of 128.
+int enqueue_oneshot(fem_server *v, Request &r, const StreamDev &s, int attempt) {
     cudaStream_t st = r.lane;
     const uint32_t cr0 = (uint32_t)(r.ev_begin / CHUNK);
     const uint32_t cr1 = (uint32_t)((r.ev_end + CHUNK - 1) / CHUNK);
     const uint32_t nch = cr1 > cr0 ? cr1 - cr0 : 0u;
+    const uint32_t R = attempt == 0 ? kServeRing : attempt == 1 ? 32u : 128u;
+    const uint32_t cls = attempt == 0 ? S_MAX : S_RECOUNT;
     // the stitch skips episodes flagged for a recount: no flag may survive from the
     // memory's last user
     SCK(cudaMemsetAsync(r.redo, 0, r.m, st));
@@ -243,23 +249,26 @@ int enqueue_oneshot(fem_server *v, Request &r, const StreamDev &s, uint32_t R, b
         p.cands = r.cands + g.off;
         p.m = g.m;
         p.out = r.rel + g.off;
-        uint32_t P = mc && r.tables ? oneshot_segments(g.m, nch, fem_ctx_sms(v->ctx),
-                                                       v->cfg.mem_budget_bytes)
-                                    : 1u;
+        uint32_t P = attempt < 2 && r.tables
+                         ? oneshot_segments(g.m, nch, fem_ctx_sms(v->ctx), v->cfg.mem_budget_bytes)
+                         : 1u;
+        if (attempt == 1) P /= S_RECOUNT / S_MAX;  // the same table memory, 4x the slots
         if (P > 1) {
             const uint32_t cps = (nch + P - 1) / P;
             P = (nch + cps - 1) / cps;
-            if ((uint64_t)P * g.m > r.tab_items) P = 1;
+            if ((uint64_t)P * g.m * cls > r.tab_items * S_MAX) P = 1;
             if (P > 1) {
                 p.cps = cps;
                 p.P = P;
                 p.tables = r.tables;
             }
         }
+        const uint32_t pcls = P > 1 ? cls : S_MAX;
         SCK(launch_count(g.N, FEM_PASS_RELAXED, P > 1, 1,
-                         serve_threads(g.N, FEM_PASS_RELAXED, 1, s.offs, P > 1), p, st));
+                         serve_threads(g.N, FEM_PASS_RELAXED, 1, s.offs, P > 1, pcls), p, st,
+                         pcls));
         if (P > 1)
-            SCK(launch_stitch(r.tables, g.m, P, r.rel + g.off, r.redo + g.off, r.err, st));
+            SCK(launch_stitch(r.tables, g.m, P, r.rel + g.off, r.redo + g.off, r.err, st, pcls));
         SCK(launch_compact(r.rel + g.off, nullptr, r.theta, g.m, r.idx + g.off,
                            r.cnt + (&g - r.groups.data()), r.scratch, st));
         // the exact pass over the survivors (their number stays on the device): a grid for
@@ -280,8 +289,10 @@ int enqueue_oneshot(fem_server *v, Request &r, const StreamDev &s, uint32_t R, b
             x.tables = r.tables;
         }
         SCK(launch_count(g.N, FEM_PASS_EXACT, xmc, R,
-                         serve_threads(g.N, FEM_PASS_EXACT, R, s.offs, xmc), x, st));
-        if (xmc) SCK(launch_stitch(r.tables, g.m, P, r.ex + g.off, r.redo + g.off, r.err, st));
+                         serve_threads(g.N, FEM_PASS_EXACT, R, s.offs, xmc, pcls), x, st,
+                         xmc ? pcls : S_MAX));
+        if (xmc)
+            SCK(launch_stitch(r.tables, g.m, P, r.ex + g.off, r.redo + g.off, r.err, st, pcls));
         SCK(cudaMemsetAsync(r.out + g.off, 0, (size_t)g.m * 4, st));
         SCK(cudaMemsetAsync(r.flags + g.off, 0, g.m, st));
         SCK(launch_scatter_dev(r.ex + g.off, r.idx + g.off, x.m_dev, g.m, r.out + g.off,
@@ -624,7 +635,7 @@ int fem_server_submit(fem_server *v, int32_t sid, const fem_episode *cands, uint
     }
     if (s.t_max > kServeMaxTime) return fail(FEM_ERANGE);
     if (mode == FEM_REQ_ONESHOT) {
-        int rc = enqueue_oneshot(v, r, s, kServeRing, true);
+        int rc = enqueue_oneshot(v, r, s, 0);
         if (rc == FEM_OK) rc = finish_enqueue(v, r, ss);
         if (rc != FEM_OK) return fail(rc);
     } else {
@@ -667,15 +678,21 @@ int fem_server_poll(fem_server *v, uint64_t *done_ids, uint32_t cap, uint32_t *n
         else if (e & ERR_BADEP) r.status = FEM_EINVAL;
         else if ((e & (ERR_RING | ERR_CLASS | ERR_TABLE)) && r.mode == FEM_REQ_ONESHOT &&
                  r.status == FEM_OK) {
-            // rare: recount in one segment with larger rings, synchronously on the lane
+            // a capacity guard tripped: recount with more entry classes per table, then
+            // in one segment with larger rings, synchronously on the request's lane
             auto sit = v->streams.find(r.sid);
-            int rc = cudaMemsetAsync(r.err, 0, 4, r.lane) == cudaSuccess ? FEM_OK : FEM_ECUDA;
-            if (rc == FEM_OK) rc = enqueue_oneshot(v, r, sit->second.s, 128, false);
-            if (rc == FEM_OK) rc = finish_enqueue(v, r, sit->second);
-            if (rc == FEM_OK && cudaEventSynchronize(r.done) != cudaSuccess) rc = FEM_ECUDA;
+            int rc = FEM_OK;
+            bool still = true;
+            for (int attempt = 1; attempt <= 2 && still && rc == FEM_OK; ++attempt) {
+                rc = cudaMemsetAsync(r.err, 0, 4, r.lane) == cudaSuccess ? FEM_OK : FEM_ECUDA;
+                if (rc == FEM_OK) rc = enqueue_oneshot(v, r, sit->second.s, attempt);
+                if (rc == FEM_OK) rc = finish_enqueue(v, r, sit->second);
+                if (rc == FEM_OK && cudaEventSynchronize(r.done) != cudaSuccess) rc = FEM_ECUDA;
+                still = (*r.h_err & (ERR_RING | ERR_CLASS | ERR_TABLE)) != 0;
+            }
             r.in_flight = false;
             if (rc != FEM_OK) r.status = rc;
-            else if (*r.h_err & (ERR_RING | ERR_CLASS | ERR_TABLE)) r.status = FEM_EOVERFLOW;
+            else if (still) r.status = FEM_EOVERFLOW;
         } else if (e & ERR_RING) {
             r.status = FEM_EOVERFLOW;  // a standing request's carried lists overflowed
         }
