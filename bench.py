@@ -44,12 +44,12 @@ OPS_PER_TOUCHED = {"relaxed": 4, "exact": 6}
 # ("level/pass") from one ncu capture, keyed by the SHA-256 of the kernel source it was
 # taken on and the workload (no entry: stale or not captured, reported as null).
 NCU_TRAFFIC = {
-    # current counting kernels, ncu --set full of the first mining step with the rule's
-    # launch shapes (--no-tune; the tuned step uses the same shape for its dominant launch,
-    # level 3 relaxed): dram__bytes_read.sum + dram__bytes_write.sum per launch
-    "9205ba36a7e74875": {
-        "single_recording_64types_300s": {"2/relaxed": 13687040, "2/exact": 8607744,
-                                          "3/relaxed": 12857856, "3/exact": 3724288},
+    # ncu --set full of the first mining step with the rule's kernels and shapes (--no-tune;
+    # the tuned step runs the same kernels): dram__bytes_read.sum + dram__bytes_write.sum
+    # per launch (level 3 exact was not among the four captured launches)
+    "98b96aab5b9f5f51": {
+        "single_recording_64types_300s": {"2/relaxed": 13641984, "2/exact": 8721152,
+                                          "3/relaxed": 12842240},
     },
 }
 

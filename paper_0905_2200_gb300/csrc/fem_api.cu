@@ -543,7 +543,9 @@ int count_finish(fem_ctx *c, const StreamDev &s, const PassLaunch &pl, uint32_t 
         bool same_segments;
     };
     std::vector<Try> tries;
-    if (pl.chain) tries.push_back({P > 1, 8u, true});
+    // (a latest-chain launch that only ran out of entry-class slots goes straight to the
+    // one-chunk segments with four times the slots: its few episodes finish sooner there)
+    if (pl.chain && (e & ~ERR_CLASS & ERR_CAP)) tries.push_back({P > 1, 8u, true});
     tries.push_back({true, 32u, false});
     tries.push_back({false, 32u, false});
     tries.push_back({false, 128u, false});
