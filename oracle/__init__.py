@@ -152,6 +152,31 @@ def count_mapconcat(types, t, ep_types, lo, hi, bounds, pass_=EXACT, return_size
     return (int(r), sizes[:P]) if return_sizes else int(r)
 
 
+def capacity_table(types, t, n_types, widths):
+    """cap[a, j]: the most events of type a inside one closed window of length widths[j]
+    (microseconds), max over x of #{i : types[i] = a, x <= t[i] <= x + widths[j]}.
+
+    It bounds the state of the counters: Algorithm 1's list for node k keeps, once the
+    entries older than hi_k are dropped, events of type E_k within hi_k of the newest
+    one, so at most cap[E_k, hi_k] of them (Section 5.1); a MapConcatenate segment
+    (Section 5.2.2) tabulates one entry class per last-node event in its look-back
+    window of length W = sum of hi, so at most 1 + cap[E_N, W] classes.  A fullest
+    window can be moved to start at one of its events, so counting forward from each
+    event of the type is enough (a sorted search over the type's times)."""
+    types, t = _stream(types, t)
+    widths = np.asarray(widths, dtype=np.uint64).reshape(-1)
+    cap = np.zeros((n_types, len(widths)), np.uint32)
+    for a in range(n_types):
+        ts = t[types == a].astype(np.uint64)
+        if len(ts) == 0:
+            continue
+        first = np.arange(len(ts))
+        for j, h in enumerate(widths):
+            last = np.searchsorted(ts, ts + h, side="right")
+            cap[a, j] = int((last - first).max())
+    return cap
+
+
 def count_windows(types, t, ep_types, lo, hi, w):
     """Window-based frequency (Section 2's alternative measure, with the episode's
     interval constraints): how many integer starts s have an occurrence inside the
