@@ -50,6 +50,9 @@ struct fem_ctx {
     uint32_t *d_err = nullptr;    // device error word
     uint32_t *d_small = nullptr;  // 64 device words for counters
     uint32_t *h_small = nullptr;  // 64 pinned host words
+    // device address of h_small[kPubWord..kPubWord+1], written by the compaction and scan
+    // kernels (count and error word); null where pinned memory is not mapped
+    uint32_t *d_pub = nullptr;
     // pinned staging of an interval set (so that its upload is asynchronous), and the
     // event after the last upload from it (the next one waits for that copy to leave)
     fem_interval *h_ivl = nullptr;
@@ -105,6 +108,8 @@ void report_cuda(cudaError_t e, int line) {
 
 // d_small word assignment
 enum { W_COUNT0 = 0, W_COUNT1 = 1, W_COUNT2 = 2, W_INFO = 8 /* 3 words */ };
+// first of the two pinned host words the kernels publish counts to
+constexpr uint32_t kPubWord = 48;
 
 size_t stream_bytes(const StreamDev &s) {
     if (!s.t) return 0;
@@ -195,9 +200,20 @@ int read_err(fem_ctx *c, cudaStream_t st, uint32_t *err) {
     return read_words(c, c->d_err, 1, err, st);
 }
 
-// A device count and the error word, in one round trip.
+// The count (and error word) a compaction or scan publishes into the mapped host words.
+Publish pub_of(const fem_ctx *c) { return Publish{c->d_pub, c->d_err}; }
+
+// A device count and the error word, in one round trip: read from the mapped words the
+// launch before published them to, else copied.
 int read_count_err(fem_ctx *c, const uint32_t *d_count, uint32_t *count, uint32_t *err,
                    cudaStream_t st) {
+    if (c->d_pub) {
+        CK(cudaStreamSynchronize(st));
+        const volatile uint32_t *h = c->h_small + kPubWord;
+        *count = h[0];
+        *err = h[1];
+        return FEM_OK;
+    }
     CK(cudaMemcpyAsync(c->h_small, d_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(c->h_small + 1, c->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -295,25 +311,32 @@ uint32_t ceil_log2(uint64_t v) {
 }
 
 // The latest-chain kernels count distinct-type episodes of 2..8 nodes in sets that come
-// in runs of shared prefixes (a handful of scattered candidates is split into parts by
-// the kernel and still counted there).
+// in runs of shared prefixes, and small sets of longer episodes however scattered (the
+// kernel splits a tile's prefixes into parts: at most three for 64 candidates).
+constexpr uint32_t kChainSmallSet = 64;
 bool chain_eligible(const fem_ctx *c, int N, bool distinct, uint32_t m) {
-    return distinct && N >= 2 && N <= FEM_MAX_LEN && c->clustered && m > 0;
+    return distinct && N >= 2 && N <= FEM_MAX_LEN && m > 0 &&
+           (c->clustered || (N >= 3 && m <= kChainSmallSet));
 }
 
 // The rule's kernel where no measurement says otherwise: the latest-chain kernels for the
-// exact pass over at least a block of candidates, whose per-thread machine (sliding-window
-// lists) costs the most per event; the per-thread machine for the relaxed pass, whose
-// single slot per node makes it cheap (the two measured within a few percent of each
-// other on the 64-type recording, and the chain form pays for class and list overflows).
+// exact pass, whose per-thread machine (sliding-window lists) costs the most per event,
+// over at least a block of candidates, or over a small set (there a block's eight warps
+// build the prefix lists together where the per-thread machine leaves a single warp per
+// block: level-3 exact of 32 survivors 0.097 -> 0.063 ms); the per-thread machine for the
+// relaxed pass, whose single slot per node makes it cheap (the two measured within a few
+// percent of each other on the 64-type recording, and the chain form pays for class and
+// list overflows).
 uint32_t rule_kernel(const fem_ctx *c, int N, int pass, bool distinct, uint32_t m) {
-    return chain_eligible(c, N, distinct, m) && pass == FEM_PASS_EXACT && m >= 256
+    return chain_eligible(c, N, distinct, m) && pass == FEM_PASS_EXACT &&
+                   (m >= 256 || m <= kChainSmallSet)
                ? FEM_KERNEL_CHAIN
                : FEM_KERNEL_MACHINE;
 }
 
-// Block size of the latest-chain kernels: 256 threads, smaller blocks for few episodes.
-uint32_t chain_threads(uint32_t m) { return m > 128 ? 256u : m > 64 ? 128u : m > 32 ? 64u : 32u; }
+// Block size of the latest-chain kernels: 256 threads, also for a few episodes (the
+// block's warps share the prefix-list builds).
+uint32_t chain_threads(uint32_t) { return 256u; }
 
 // The class a measured launch shape is kept for: counts of the same length,
 // pass and type structure, with m and the stream length in the same power-of-two
@@ -776,6 +799,12 @@ int fem_create(fem_ctx **out, int device, size_t mem_budget_bytes) {
         }
     }
     cudaMemset(c->d_err, 0, sizeof(uint32_t));
+    {
+        void *dp = nullptr;
+        if (cudaHostGetDevicePointer(&dp, c->h_small, 0) == cudaSuccess && dp)
+            c->d_pub = static_cast<uint32_t *>(dp) + kPubWord;
+        cudaGetLastError();
+    }
     *out = c;
     return FEM_OK;
 }
@@ -1084,6 +1113,38 @@ int fem_type_counts(fem_ctx *c, int32_t id, uint32_t *counts_out) {
     return FEM_OK;
 }
 
+int fem_capacity_table(fem_ctx *c, int32_t id, const uint32_t *widths, uint32_t nh,
+                       uint32_t *cap_out) {
+    if (!c || !widths || !cap_out || nh == 0 || nh > FEM_MAX_CAP_WIDTHS) return FEM_EINVAL;
+    const StreamDev *s = find_stream(c, id);
+    if (!s) return FEM_ENOSTREAM;
+    cudaSetDevice(c->device);
+    cudaStream_t st = c->own;
+    const uint32_t K = s->K;
+    // widths that reach the last time hold a type's every event: the type counts
+    std::vector<uint32_t> hw, slot;
+    for (uint32_t j = 0; j < nh; ++j)
+        if (s->n && widths[j] < s->t_max) hw.push_back(widths[j]), slot.push_back(j);
+    std::vector<uint32_t> hist(K, 0), part((size_t)K * hw.size(), 0);
+    CK(cudaMemcpyAsync(hist.data(), s->hist, K * 4, cudaMemcpyDeviceToHost, st));
+    if (!hw.empty()) {
+        const uint32_t nk = (uint32_t)hw.size();
+        uint32_t *d;
+        RET(dbuf(c, "cap", (size_t)nk * (K + 1), &d));
+        uint32_t *d_h = d + (size_t)K * nk;
+        CK(cudaMemsetAsync(d, 0, (size_t)K * nk * 4, st));
+        CK(cudaMemcpyAsync(d_h, hw.data(), nk * 4, cudaMemcpyHostToDevice, st));
+        CK(launch_capacity(*s, d_h, nk, d, st));
+        CK(cudaMemcpyAsync(part.data(), d, (size_t)K * nk * 4, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    for (uint32_t a = 0; a < K; ++a) {
+        for (uint32_t j = 0; j < nh; ++j) cap_out[(size_t)a * nh + j] = hist[a];
+        for (size_t q = 0; q < hw.size(); ++q) cap_out[(size_t)a * nh + slot[q]] = part[a * hw.size() + q];
+    }
+    return FEM_OK;
+}
+
 int fem_count_candidates(fem_ctx *c, int32_t id, const fem_episode *cands, uint32_t m,
                          int cands_on_device, const fem_interval *I, uint32_t nI, int pass,
                          uint32_t *counts_out, int counts_on_device, void *cuda_stream) {
@@ -1283,9 +1344,10 @@ int fem_count_two_pass(fem_ctx *c, int32_t id, const fem_episode *cands, uint32_
     if (!sv) RET(dbuf(c, "tp_sv", m, &sv));
     // first pass: relaxed counts, eliminate count < theta
     RET(count_any(c, *s, dc, nullptr, m, d_ivl, nI, FEM_PASS_RELAXED, rel, st));
-    CK(launch_compact(rel, nullptr, theta, m, idx, c->d_small + W_COUNT0, scratch, st));
-    uint32_t ms;
-    RET(read_words(c, c->d_small + W_COUNT0, 1, &ms, st));
+    CK(launch_compact(rel, nullptr, theta, m, idx, c->d_small + W_COUNT0, scratch, st, pub_of(c)));
+    uint32_t ms, e0;
+    RET(read_count_err(c, c->d_small + W_COUNT0, &ms, &e0, st));
+    RET(err_status(e0));
     // second pass: exact counts of the survivors
     RET(count_any(c, *s, dc, idx, ms, d_ivl, nI, FEM_PASS_EXACT, ex, st));
     CK(cudaMemsetAsync(exo, 0, (size_t)m * 4, st));
@@ -1388,13 +1450,14 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
     auto compact_and_read = [&](const uint32_t *vals, uint32_t mm, uint32_t *idx, uint32_t word,
                                 uint32_t *scratch, const PassLaunch &pl, uint32_t *kept,
                                 cudaEvent_t done) -> int {
-        CK(launch_compact(vals, nullptr, theta, mm, idx, c->d_small + word, scratch, st));
+        CK(launch_compact(vals, nullptr, theta, mm, idx, c->d_small + word, scratch, st, pub_of(c)));
         if (done) CK(cudaEventRecord(done, st));
         uint32_t e;
         RET(read_count_err(c, c->d_small + word, kept, &e, st));
         if (e & ERR_CAP) {
             RET(count_finish(c, s, pl, e, st));
-            CK(launch_compact(vals, nullptr, theta, mm, idx, c->d_small + word, scratch, st));
+            CK(launch_compact(vals, nullptr, theta, mm, idx, c->d_small + word, scratch, st,
+                              pub_of(c)));
             RET(read_count_err(c, c->d_small + word, kept, &e, st));
         }
         return err_status(e);
@@ -1472,9 +1535,10 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
         RETF(dbuf(c, "joff", f, &joff));
         cudaEventRecord(c->ev[0], st);
         CKF(launch_join_count(F, f, N, repeats, jc, c->sm_count, st));
-        CKF(launch_exclusive_scan(jc, f, joff, c->d_small + W_COUNT2, scratch, st));
-        uint32_t mn;
-        RETF(read_words(c, c->d_small + W_COUNT2, 1, &mn, st));
+        CKF(launch_exclusive_scan(jc, f, joff, c->d_small + W_COUNT2, scratch, st, pub_of(c)));
+        uint32_t mn, ej;
+        RETF(read_count_err(c, c->d_small + W_COUNT2, &mn, &ej, st));
+        RETF(err_status(ej));
         cur ^= 1;
         RETF(dbuf(c, cname[cur], std::max<uint32_t>(mn, 1), &cands));
         CKF(launch_join_emit(F, f, N, repeats, joff, cands, c->sm_count, st));

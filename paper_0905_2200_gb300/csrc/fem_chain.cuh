@@ -47,6 +47,11 @@ template <int N>
 constexpr int chain_classes = N == 2 ? 4 : 8;
 template <int N>
 constexpr int chain_blocks_per_sm = N == 2 ? 4 : 3;
+// leaf events looked up per step (independent look-ups in flight; the greedy that
+// consumes them stays in order): four measured slower than two at three nodes (the
+// MapConcatenate form then spills: level-3 relaxed 0.46 -> 0.50 ms)
+template <int N>
+constexpr int chain_leaf_step = 2;
 
 // A node's carried tail is double-buffered: lookups of chunk c read tail[c & 1] while
 // the node's build for chunk c writes tail[(c + 1) & 1], so the carry needs no barrier.
@@ -494,8 +499,8 @@ __device__ __forceinline__ void chain_block(const CountParams &p) {
                 };
                 if (!MC || (c >= c_seg0 && umask == 0)) {
                     // one class: inside the segment with every entry class merged, or one
-                    // segment.  Two events per step: their look-ups are independent, the
-                    // greedy is not.
+                    // segment.  Several events per step: their look-ups are independent,
+                    // the greedy is not.
                     auto apply = [&](bool a, uint32_t y, uint32_t S, uint32_t St) {
                         if (!a) return;
                         const uint32_t gidx = cb.cbase + y;
@@ -505,16 +510,20 @@ __device__ __forceinline__ void chain_block(const CountParams &p) {
                             if (S >= c_st[0] && St >= X) c_st[0] = gidx + 1, ++c_cnt[0], c0_done = true;
                         }
                     };
+                    constexpr int U = chain_leaf_step<N>;
                     uint32_t jj = g0;
-                    for (; jj + 2 <= g1; jj += 2) {
-                        const uint2 e0 = cb.ev()[jj], e1 = cb.ev()[jj + 1];
-                        uint32_t S0, St0, S1, St1;
-                        const bool a0 = adm_at(e0, S0, St0);
-                        const bool a1 = adm_at(e1, S1, St1);
-                        apply(a0, e0.y, S0, St0);
-                        apply(a1, e1.y, S1, St1);
+                    for (; jj + U <= g1; jj += U) {
+                        uint2 e[U];
+                        uint32_t S[U], St[U];
+                        bool a[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) e[u] = cb.ev()[jj + u];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) a[u] = adm_at(e[u], S[u], St[u]);
+#pragma unroll
+                        for (int u = 0; u < U; ++u) apply(a[u], e[u].y, S[u], St[u]);
                     }
-                    if (jj < g1) {
+                    for (; jj < g1; ++jj) {
                         const uint2 e = cb.ev()[jj];
                         uint32_t S, St;
                         const bool a = adm_at(e, S, St);
@@ -583,6 +592,8 @@ __device__ __forceinline__ void chain_block(const CountParams &p) {
                     }
                 }
             }
+            // (a barrier, not the next chunk's mbarrier wait, holds the threads that are
+            // done early: their spinning would take issue slots from the others)
             __syncthreads();
             if (tid == 0 && c + 2 < c_end) {
                 fence_proxy_async_smem();

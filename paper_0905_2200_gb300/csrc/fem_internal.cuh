@@ -185,6 +185,10 @@ cudaError_t launch_load_stream(StreamDev &s, cudaStream_t st, uint32_t *d_err,
 cudaError_t launch_bucket_chunks(StreamDev &s, uint32_t c0, uint32_t c1, cudaStream_t st,
                                  uint32_t *d_err = nullptr);
 // hist[ty[i]] += sign (+1 or -1) for i < n
+// cap[a * nh + j] (zeroed by the caller): the most type-a events in a closed window of
+// length h[j] (device array)
+cudaError_t launch_capacity(const StreamDev &s, const uint32_t *h, uint32_t nh, uint32_t *cap,
+                            cudaStream_t st);
 cudaError_t launch_hist_add(const uint8_t *ty, uint64_t n, uint32_t K, int sign, uint32_t *hist,
                             cudaStream_t st);
 // dst[idx[i]] = src[i] and flags[idx[i]] = 1 for i < *m_dev (grid sized for m_max)
@@ -254,9 +258,16 @@ cudaError_t launch_compose_idx(const uint32_t *outer, const uint32_t *inner, uin
 // stable compaction: keep[i] = (vals[i] >= theta) (or flags[i] != 0 if vals == NULL)
 // block_scratch holds compact_scratch_words(m) words: one partial sum per block of
 // COMPACT_ITEMS_PER_BLOCK items plus a slack of 32
+// A count a kernel also writes, with the error word, into pinned host memory (the device
+// address of two mapped host words): the host reads both after a stream synchronisation
+// without a copy of its own.
+struct Publish {
+    uint32_t *host = nullptr;
+    const uint32_t *err = nullptr;
+};
 cudaError_t launch_compact(const uint32_t *vals, const uint8_t *flags, uint32_t theta, uint32_t m,
                            uint32_t *idx_out, uint32_t *count_out, uint32_t *block_scratch,
-                           cudaStream_t st);
+                           cudaStream_t st, Publish pub = {});
 constexpr uint32_t COMPACT_ITEMS_PER_BLOCK = 1024;
 constexpr size_t compact_scratch_words_for(uint64_t m) {
     return (size_t)((m + COMPACT_ITEMS_PER_BLOCK - 1) / COMPACT_ITEMS_PER_BLOCK) + 32;
@@ -276,7 +287,8 @@ cudaError_t launch_level2(const uint32_t *ftypes, uint32_t f, uint32_t n_ivl, bo
 cudaError_t launch_join_count(const fem_episode *F, uint32_t f, uint32_t N, bool repeats,
                               uint32_t *cnt, int sm_count, cudaStream_t st);
 cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t m, uint32_t *out,
-                                  uint32_t *total, uint32_t *scratch, cudaStream_t st);
+                                  uint32_t *total, uint32_t *scratch, cudaStream_t st,
+                                  Publish pub = {});
 cudaError_t launch_join_emit(const fem_episode *F, uint32_t f, uint32_t N, bool repeats,
                              const uint32_t *off, fem_episode *out, int sm_count, cudaStream_t st);
 cudaError_t launch_repeat_flags(const fem_episode *c, const uint32_t *gather, uint32_t m, bool invert,

@@ -337,6 +337,18 @@ cudaError_t launch_len_flags(const fem_episode *c, const uint32_t *gather, uint3
 // ------------------------------------------------------------------ stable compaction
 size_t compact_scratch_words(uint32_t m) { return compact_scratch_words_for(m); }
 
+// (one thread) the count and the error word into the mapped host words, if any
+__device__ __forceinline__ void publish(const Publish &pub, uint32_t count) {
+    if (!pub.host) return;
+    pub.host[0] = count;
+    pub.host[1] = *reinterpret_cast<const volatile uint32_t *>(pub.err);
+}
+
+__global__ void k_set_count(uint32_t *count, Publish pub) {
+    *count = 0;
+    publish(pub, 0);
+}
+
 __global__ void __launch_bounds__(CT) k_keep_count(const uint32_t *vals, const uint8_t *flags,
                                                     uint32_t theta, uint32_t m,
                                                     uint32_t *blocksum) {
@@ -351,7 +363,8 @@ __global__ void __launch_bounds__(CT) k_keep_count(const uint32_t *vals, const u
 }
 
 // In-place exclusive scan of a[0..nb) by one block of 1024 threads; *total = sum.
-__global__ void __launch_bounds__(1024) k_scan_small(uint32_t *a, uint32_t nb, uint32_t *total) {
+__global__ void __launch_bounds__(1024) k_scan_small(uint32_t *a, uint32_t nb, uint32_t *total,
+                                                     Publish pub) {
     __shared__ uint32_t carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
@@ -366,6 +379,7 @@ __global__ void __launch_bounds__(1024) k_scan_small(uint32_t *a, uint32_t nb, u
         __syncthreads();
     }
     if (threadIdx.x == 0 && total) *total = carry;
+    if (threadIdx.x == 0) publish(pub, carry);
 }
 
 __global__ void __launch_bounds__(CT) k_keep_scatter(const uint32_t *vals, const uint8_t *flags,
@@ -394,7 +408,7 @@ static_assert(SI == 16, "k_compact_small takes half a keep-bit word per thread")
 
 __global__ void __launch_bounds__(ST) k_compact_small(const uint32_t *vals, const uint8_t *flags,
                                                       uint32_t theta, uint32_t m, uint32_t *idx,
-                                                      uint32_t *count) {
+                                                      uint32_t *count, Publish pub) {
     // keep bits, one word per 32 items, from coalesced reads (item r * ST + thread)
     __shared__ uint32_t keep_bits[ST * SI / 32];
     const uint32_t lane = threadIdx.x & 31u;
@@ -415,11 +429,15 @@ __global__ void __launch_bounds__(ST) k_compact_small(const uint32_t *vals, cons
         bits &= bits - 1;
         idx[pos++] = base + k;
     }
-    if (threadIdx.x == 0) *count = tot;
+    if (threadIdx.x == 0) {
+        *count = tot;
+        publish(pub, tot);
+    }
 }
 
 __global__ void __launch_bounds__(ST) k_scan_one_block(const uint32_t *in, uint32_t m,
-                                                       uint32_t *out, uint32_t *total) {
+                                                       uint32_t *out, uint32_t *total,
+                                                       Publish pub) {
     const uint32_t base = threadIdx.x * SI;
     uint32_t v[SI], c = 0;
 #pragma unroll
@@ -435,21 +453,27 @@ __global__ void __launch_bounds__(ST) k_scan_one_block(const uint32_t *in, uint3
         pos += v[k];
     }
     if (threadIdx.x == 0 && total) *total = tot;
+    if (threadIdx.x == 0) publish(pub, tot);
 }
 
 cudaError_t launch_compact(const uint32_t *vals, const uint8_t *flags, uint32_t theta, uint32_t m,
                            uint32_t *idx_out, uint32_t *count_out, uint32_t *scratch,
-                           cudaStream_t st) {
-    if (m == 0) return cudaMemsetAsync(count_out, 0, sizeof(uint32_t), st);
+                           cudaStream_t st, Publish pub) {
+    if (m == 0) {
+        if (!pub.host) return cudaMemsetAsync(count_out, 0, sizeof(uint32_t), st);
+        k_set_count<<<1, 1, 0, st>>>(count_out, pub);
+        note_launch();
+        return cudaGetLastError();
+    }
     if (m <= ST * SI) {
-        k_compact_small<<<1, ST, 0, st>>>(vals, flags, theta, m, idx_out, count_out);
+        k_compact_small<<<1, ST, 0, st>>>(vals, flags, theta, m, idx_out, count_out, pub);
         note_launch();
         return cudaGetLastError();
     }
     const uint32_t nb = (m + CB - 1) / CB;
     k_keep_count<<<nb, CT, 0, st>>>(vals, flags, theta, m, scratch);
     note_launch();
-    k_scan_small<<<1, 1024, 0, st>>>(scratch, nb, count_out);
+    k_scan_small<<<1, 1024, 0, st>>>(scratch, nb, count_out, pub);
     note_launch();
     k_keep_scatter<<<nb, CT, 0, st>>>(vals, flags, theta, m, scratch, idx_out);
     note_launch();
@@ -487,17 +511,22 @@ __global__ void __launch_bounds__(CT) k_scan_apply(const uint32_t *in, uint32_t 
 }
 
 cudaError_t launch_exclusive_scan(const uint32_t *in, uint32_t m, uint32_t *out, uint32_t *total,
-                                  uint32_t *scratch, cudaStream_t st) {
-    if (m == 0) return cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
+                                  uint32_t *scratch, cudaStream_t st, Publish pub) {
+    if (m == 0) {
+        if (!pub.host) return cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
+        k_set_count<<<1, 1, 0, st>>>(total, pub);
+        note_launch();
+        return cudaGetLastError();
+    }
     if (m <= ST * SI) {
-        k_scan_one_block<<<1, ST, 0, st>>>(in, m, out, total);
+        k_scan_one_block<<<1, ST, 0, st>>>(in, m, out, total, pub);
         note_launch();
         return cudaGetLastError();
     }
     const uint32_t nb = (m + CB - 1) / CB;
     k_sum_blocks<<<nb, CT, 0, st>>>(in, m, scratch);
     note_launch();
-    k_scan_small<<<1, 1024, 0, st>>>(scratch, nb, total);
+    k_scan_small<<<1, 1024, 0, st>>>(scratch, nb, total, pub);
     note_launch();
     k_scan_apply<<<nb, CT, 0, st>>>(in, m, scratch, out);
     note_launch();

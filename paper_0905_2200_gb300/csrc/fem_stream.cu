@@ -159,4 +159,55 @@ cudaError_t launch_hist_add(const uint8_t *ty, uint64_t n, uint32_t K, int sign,
     return cudaGetLastError();
 }
 
+// Capacity table: cap[a * nh + j] = the most type-a events inside one closed window of
+// length h[j].  A fullest window can start at one of its events, so one thread per
+// (chunk, type) takes the events of its group in turn and, for each width, walks a
+// second pointer forward through the type's groups of this and the following chunks
+// while the times stay within h of the current event (two pointers: the forward one
+// never moves back within the thread's group); the per-thread maxima meet by atomicMax.
+__global__ void __launch_bounds__(256) k_capacity(const uint2 *__restrict__ bev,
+                                                  const uint16_t *__restrict__ boff, uint32_t offs,
+                                                  uint32_t n_chunks, uint32_t K,
+                                                  const uint32_t *__restrict__ h, uint32_t nh,
+                                                  uint32_t *__restrict__ cap) {
+    const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (uint64_t)n_chunks * K) return;
+    const uint32_t c = (uint32_t)(gid / K), a = (uint32_t)(gid % K);
+    const uint32_t g0 = boff[(uint64_t)c * offs + a], g1 = boff[(uint64_t)c * offs + a + 1];
+    if (g0 == g1) return;
+    const uint2 *ev = bev + (uint64_t)c * CHUNK;
+    for (uint32_t j = 0; j < nh; ++j) {
+        const uint64_t w = h[j];
+        // forward pointer: chunk fc, index fk in that chunk's type-a group [fk, f1)
+        uint32_t fc = c, fk = g0, f1 = g1;
+        uint32_t ahead = 0, best = 0;  // events in [current, forward pointer)
+        for (uint32_t k = g0; k < g1; ++k) {
+            const uint64_t lim = (uint64_t)ev[k].x + w;
+            for (;;) {
+                while (fk == f1 && fc + 1 < n_chunks) {  // next chunk's group of type a
+                    ++fc;
+                    fk = boff[(uint64_t)fc * offs + a];
+                    f1 = boff[(uint64_t)fc * offs + a + 1];
+                }
+                if (fk == f1 || bev[(uint64_t)fc * CHUNK + fk].x > lim) break;
+                ++fk;
+                ++ahead;
+            }
+            best = max(best, ahead);
+            --ahead;  // the current event leaves the window's start
+        }
+        atomicMax(&cap[a * nh + j], best);
+    }
+}
+
+cudaError_t launch_capacity(const StreamDev &s, const uint32_t *h, uint32_t nh, uint32_t *cap,
+                            cudaStream_t st) {
+    const uint64_t threads = (uint64_t)s.n_chunks * s.K;
+    if (threads == 0 || nh == 0) return cudaSuccess;
+    k_capacity<<<(uint32_t)((threads + 255) / 256), 256, 0, st>>>(s.bev, s.boff, s.offs,
+                                                                   s.n_chunks, s.K, h, nh, cap);
+    note_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace fem

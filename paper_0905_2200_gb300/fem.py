@@ -71,7 +71,7 @@ class fem_server_config(ctypes.Structure):
 REQ_ONESHOT, REQ_STANDING = 0, 1
 
 EXPORTS = ["fem_create", "fem_destroy", "fem_mem_usage", "fem_append_stream", "fem_set_config", "fem_load_stream", "fem_free_stream",
-           "fem_type_counts", "fem_count_candidates", "fem_count_two_pass",
+           "fem_type_counts", "fem_capacity_table", "fem_count_candidates", "fem_count_two_pass",
            "fem_mine_levelwise", "fem_result_level", "fem_result_max_level", "fem_result_free",
            "fem_last_mine_stats", "fem_strerror", "fem_kernel_launches", "fem_select_noalloc",
            "fem_batch_create", "fem_batch_run", "fem_batch_destroy",
@@ -104,6 +104,7 @@ def load(path: str | None = None):
         "fem_load_stream": (I, [vp, vp, vp, u64, u32, I, vp, ctypes.POINTER(i32)]),
         "fem_free_stream": (I, [vp, i32]),
         "fem_type_counts": (I, [vp, i32, vp]),
+        "fem_capacity_table": (I, [vp, i32, vp, u32, vp]),
         "fem_count_candidates": (I, [vp, i32, vp, u32, I, ctypes.POINTER(fem_interval), u32, I,
                                      vp, I, vp]),
         "fem_count_two_pass": (I, [vp, i32, vp, u32, I, ctypes.POINTER(fem_interval), u32, u32,
@@ -333,6 +334,16 @@ def fem_type_counts(ctx, sid, n_types) -> np.ndarray:
     out = np.zeros(n_types, np.uint32)
     _check(load().fem_type_counts(ctx, int(sid), out.ctypes.data_as(ctypes.c_void_p)),
            "fem_type_counts")
+    return out
+
+
+def fem_capacity_table(ctx, sid, widths_us, n_types) -> np.ndarray:
+    """uint32[n_types, len(widths_us)]: the most events of each type in one closed window
+    of each width."""
+    w = np.ascontiguousarray(widths_us, dtype=np.uint32).reshape(-1)
+    out = np.zeros((n_types, len(w)), np.uint32)
+    _check(load().fem_capacity_table(ctx, int(sid), w.ctypes.data_as(ctypes.c_void_p), len(w),
+                                     out.ctypes.data_as(ctypes.c_void_p)), "fem_capacity_table")
     return out
 
 
