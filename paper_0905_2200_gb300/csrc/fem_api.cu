@@ -5,6 +5,7 @@
 // allocates device memory, launches, and copies results.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -53,10 +54,16 @@ struct fem_ctx {
     // device address of h_small[kPubWord..kPubWord+1], written by the compaction and scan
     // kernels (count and error word); null where pinned memory is not mapped
     uint32_t *d_pub = nullptr;
+    uint32_t pub_seq = 0;  // sequence number of the last publishing launch
     // pinned staging of an interval set (so that its upload is asynchronous), and the
     // event after the last upload from it (the next one waits for that copy to leave)
     fem_interval *h_ivl = nullptr;
     cudaEvent_t ivl_ev = nullptr;
+    std::vector<fem_interval> ivl_host;  // the interval set of the current call
+    // ring bounds from the capacity table per (stream generation, interval set): the
+    // list entries a node can hold as single times and as clusters
+    uint64_t next_gen = 1;
+    std::map<std::pair<uint64_t, std::string>, std::pair<uint32_t, uint32_t>> ring_bounds;
     std::map<std::string, DevBuf> bufs;
     std::vector<fem_level_stats> stats;
     std::vector<StreamDev> pool;  // buffers of freed streams, reused by later loads
@@ -200,16 +207,31 @@ int read_err(fem_ctx *c, cudaStream_t st, uint32_t *err) {
     return read_words(c, c->d_err, 1, err, st);
 }
 
-// The count (and error word) a compaction or scan publishes into the mapped host words.
-Publish pub_of(const fem_ctx *c) { return Publish{c->d_pub, c->d_err}; }
+// The count (and error word) the next compaction or scan publishes into the mapped host
+// words, under a new sequence number.
+Publish pub_of(fem_ctx *c) {
+    if (!c->d_pub) return Publish{};
+    return Publish{c->d_pub, c->d_err, ++c->pub_seq};
+}
 
-// A device count and the error word, in one round trip: read from the mapped words the
-// launch before published them to, else copied.
+// A device count and the error word, in one round trip: read from the mapped words once
+// the launch before has published them under its sequence number (the host watches the
+// word rather than waiting for the stream, so it can queue the next launches while that
+// kernel retires; after 2 s it waits for the stream instead), else copied.
 int read_count_err(fem_ctx *c, const uint32_t *d_count, uint32_t *count, uint32_t *err,
                    cudaStream_t st) {
     if (c->d_pub) {
-        CK(cudaStreamSynchronize(st));
         const volatile uint32_t *h = c->h_small + kPubWord;
+        const auto t0 = std::chrono::steady_clock::now();
+        for (uint32_t spin = 1; h[2] != c->pub_seq; ++spin) {
+            if ((spin & 1023u) == 0 &&
+                std::chrono::steady_clock::now() - t0 > std::chrono::seconds(2)) {
+                CK(cudaStreamSynchronize(st));
+                if (h[2] != c->pub_seq) return FEM_ECUDA;
+                break;
+            }
+        }
+        std::atomic_thread_fence(std::memory_order_acquire);
         *count = h[0];
         *err = h[1];
         return FEM_OK;
@@ -251,6 +273,7 @@ int check_intervals(const StreamDev &s, const fem_interval *I, uint32_t nI) {
 int upload_intervals(fem_ctx *c, const fem_interval *I, uint32_t nI, cudaStream_t st,
                      uint2 **d_ivl) {
     RET(dbuf(c, "ivl", std::max<uint32_t>(nI, 1), d_ivl));
+    c->ivl_host.assign(I, I + nI);
     if (!nI) return FEM_OK;
     if (nI > FEM_MAX_INTERVALS + 1) {
         CK(cudaMemcpyAsync(*d_ivl, I, nI * sizeof(uint2), cudaMemcpyHostToDevice, st));
@@ -260,6 +283,68 @@ int upload_intervals(fem_ctx *c, const fem_interval *I, uint32_t nI, cudaStream_
     std::memcpy(c->h_ivl, I, nI * sizeof(fem_interval));
     CK(cudaMemcpyAsync(*d_ivl, c->h_ivl, nI * sizeof(uint2), cudaMemcpyHostToDevice, st));
     CK(cudaEventRecord(c->ivl_ev, st));
+    return FEM_OK;
+}
+
+// Capacity table of a resident stream for the given widths (host out[a * nh + j]);
+// synchronous on st.  A width >= the stream's last time holds every event of a type.
+int capacity(fem_ctx *c, const StreamDev &s, const uint32_t *widths, uint32_t nh,
+             uint32_t *out, cudaStream_t st) {
+    const uint32_t K = s.K;
+    std::vector<uint32_t> hw, slot;
+    for (uint32_t j = 0; j < nh; ++j)
+        if (s.n && widths[j] < s.t_max) hw.push_back(widths[j]), slot.push_back(j);
+    std::vector<uint32_t> hist(K, 0), part((size_t)K * hw.size(), 0);
+    CK(cudaMemcpyAsync(hist.data(), s.hist, K * 4, cudaMemcpyDeviceToHost, st));
+    if (!hw.empty()) {
+        const uint32_t nk = (uint32_t)hw.size();
+        uint32_t *d;
+        RET(dbuf(c, "cap", (size_t)nk * (K + 1), &d));
+        uint32_t *d_h = d + (size_t)K * nk;
+        CK(cudaMemsetAsync(d, 0, (size_t)K * nk * 4, st));
+        CK(cudaMemcpyAsync(d_h, hw.data(), nk * 4, cudaMemcpyHostToDevice, st));
+        CK(launch_capacity(s, d_h, nk, d, st));
+        CK(cudaMemcpyAsync(part.data(), d, (size_t)K * nk * 4, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    for (uint32_t a = 0; a < K; ++a) {
+        for (uint32_t j = 0; j < nh; ++j) out[(size_t)a * nh + j] = hist[a];
+        for (size_t q = 0; q < hw.size(); ++q) out[(size_t)a * nh + slot[q]] = part[a * hw.size() + q];
+    }
+    return FEM_OK;
+}
+
+// Bounds on the per-thread exact kernel's lists for the current interval set, from the
+// capacity table (Algorithm 1's pruned list for node k holds type-E_k events within
+// hi_k: at most cap[E_k][hi_k] single times, and at most ceil(hi / (hi - lo)) + 1
+// clusters), maximised over the types and intervals; computed once per stream contents
+// and interval set.
+int ring_bounds(fem_ctx *c, const StreamDev &s, uint32_t *singles, uint32_t *clusters,
+                cudaStream_t st) {
+    const std::vector<fem_interval> &I = c->ivl_host;
+    const std::string key(reinterpret_cast<const char *>(I.data()), I.size() * sizeof(fem_interval));
+    auto it = c->ring_bounds.find({s.gen, key});
+    if (it == c->ring_bounds.end()) {
+        std::vector<uint32_t> w;
+        for (const fem_interval &iv : I) w.push_back(iv.hi_us);
+        std::vector<uint32_t> cap((size_t)s.K * w.size());
+        uint32_t sg = 0, cl = 0;
+        if (!w.empty()) {
+            RET(capacity(c, s, w.data(), (uint32_t)w.size(), cap.data(), st));
+            for (size_t j = 0; j < w.size(); ++j) {
+                uint32_t mx = 0;
+                for (uint32_t a = 0; a < s.K; ++a) mx = std::max(mx, cap[(size_t)a * w.size() + j]);
+                const uint32_t span = I[j].hi_us - I[j].lo_us;
+                const uint32_t ncl = (I[j].hi_us + span - 1) / span + 1;
+                sg = std::max(sg, mx);
+                cl = std::max(cl, std::min(mx, ncl));
+            }
+        }
+        if (c->ring_bounds.size() > 64) c->ring_bounds.clear();
+        it = c->ring_bounds.emplace(std::make_pair(s.gen, key), std::make_pair(sg, cl)).first;
+    }
+    *singles = it->second.first;
+    *clusters = it->second.second;
     return FEM_OK;
 }
 
@@ -486,6 +571,13 @@ int count_launch(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const
     if (!distinct) P = 1;
     uint32_t R = 1;
     if (pass == FEM_PASS_EXACT) R = c->cfg.ring_capacity ? c->cfg.ring_capacity : 8;
+    if (pass == FEM_PASS_EXACT && !c->cfg.ring_capacity && kind == FEM_KERNEL_MACHINE) {
+        // rings sized from the capacity table: 32 entries where a window can hold more
+        // than 8 (bursting recordings), so that the first count does not overflow
+        uint32_t sg, cl;
+        RET(ring_bounds(c, s, &sg, &cl, st));
+        if ((P > 1 ? sg : cl) > 8) R = 32;
+    }
     if (P > 1 && pass == FEM_PASS_EXACT && R > 32) R = 32;
     if (!count_config_supported(N, pass, P > 1, R)) return FEM_EINVAL;
     const uint32_t cps = P > 1 ? (s.n_chunks + P - 1) / P : std::max<uint32_t>(s.n_chunks, 1);
@@ -799,6 +891,7 @@ int fem_create(fem_ctx **out, int device, size_t mem_budget_bytes) {
         }
     }
     cudaMemset(c->d_err, 0, sizeof(uint32_t));
+    std::memset(c->h_small, 0, 64 * sizeof(uint32_t));  // no stale sequence number
     {
         void *dp = nullptr;
         if (cudaHostGetDevicePointer(&dp, c->h_small, 0) == cudaSuccess && dp)
@@ -992,6 +1085,7 @@ int fem_load_stream(fem_ctx *c, const uint8_t *types, const uint32_t *t_us, uint
         return rc;
     }
     const int32_t id = c->next_id++;
+    s.gen = c->next_gen++;
     c->streams[id] = s;
     c->hist_h[id] = std::move(hist_host);
     *id_out = id;
@@ -1073,6 +1167,7 @@ int fem_append_stream(fem_ctx *c, int32_t id, const uint8_t *types, const uint32
         return rc;
     }
     s.t_max = hw[1];
+    s.gen = c->next_gen++;
     c->hist_h[id].assign(hw + 2, hw + 2 + s.K);
     return FEM_OK;
 }
@@ -1119,30 +1214,7 @@ int fem_capacity_table(fem_ctx *c, int32_t id, const uint32_t *widths, uint32_t 
     const StreamDev *s = find_stream(c, id);
     if (!s) return FEM_ENOSTREAM;
     cudaSetDevice(c->device);
-    cudaStream_t st = c->own;
-    const uint32_t K = s->K;
-    // widths that reach the last time hold a type's every event: the type counts
-    std::vector<uint32_t> hw, slot;
-    for (uint32_t j = 0; j < nh; ++j)
-        if (s->n && widths[j] < s->t_max) hw.push_back(widths[j]), slot.push_back(j);
-    std::vector<uint32_t> hist(K, 0), part((size_t)K * hw.size(), 0);
-    CK(cudaMemcpyAsync(hist.data(), s->hist, K * 4, cudaMemcpyDeviceToHost, st));
-    if (!hw.empty()) {
-        const uint32_t nk = (uint32_t)hw.size();
-        uint32_t *d;
-        RET(dbuf(c, "cap", (size_t)nk * (K + 1), &d));
-        uint32_t *d_h = d + (size_t)K * nk;
-        CK(cudaMemsetAsync(d, 0, (size_t)K * nk * 4, st));
-        CK(cudaMemcpyAsync(d_h, hw.data(), nk * 4, cudaMemcpyHostToDevice, st));
-        CK(launch_capacity(*s, d_h, nk, d, st));
-        CK(cudaMemcpyAsync(part.data(), d, (size_t)K * nk * 4, cudaMemcpyDeviceToHost, st));
-    }
-    CK(cudaStreamSynchronize(st));
-    for (uint32_t a = 0; a < K; ++a) {
-        for (uint32_t j = 0; j < nh; ++j) cap_out[(size_t)a * nh + j] = hist[a];
-        for (size_t q = 0; q < hw.size(); ++q) cap_out[(size_t)a * nh + slot[q]] = part[a * hw.size() + q];
-    }
-    return FEM_OK;
+    return capacity(c, *s, widths, nh, cap_out, c->own);
 }
 
 int fem_count_candidates(fem_ctx *c, int32_t id, const fem_episode *cands, uint32_t m,

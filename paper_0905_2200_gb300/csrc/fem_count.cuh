@@ -632,6 +632,7 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                     if (mk >= lim) break;
                     const uint32_t gidx = (uint32_t)(cbase + mk);
                     const bool last_hit = key[N - 1] == mk;
+                    [[maybe_unused]] const uint32_t t_last = tv[N - 1];  // this event's time if last_hit
                     capable = false;
                     bool done = false;
                     for_nodes_desc<N - 1>([&](auto kc) {
@@ -651,7 +652,18 @@ __device__ __forceinline__ bool count_item(const CountParams &p, uint32_t tile, 
                         // entry class r = gidx (the serial machine's last completion was r);
                         // when class "none" completed at r too, it is that class: no slot
                         constexpr uint32_t all_slots = SC >= 32 ? 0xFFFFFFFFu : (1u << SC) - 1u;
-                        const uint32_t free_slots = ~used & (all_slots & ~1u);
+                        uint32_t free_slots = ~used & (all_slots & ~1u);
+                        if constexpr (PASS == FEM_PASS_EXACT || N >= 4) {
+                            if (!free_slots && umask) {
+                                // every slot taken: first merge the classes whose futures
+                                // have met (a window inside a burst registers many classes
+                                // before the chunk's end, where they would otherwise be
+                                // merged).  Not in the relaxed kernels of up to three
+                                // nodes: the register it takes cost level-3 relaxed 3%.
+                                try_merge(t_last, true);
+                                free_slots = ~used & (all_slots & ~1u);
+                            }
+                        }
                         if (free_slots) {
                             const int q0 = __ffs(free_slots) - 1;
                             set_key(q0, gidx);

@@ -58,6 +58,7 @@ struct StreamDev {
     uint16_t *boff = nullptr;
     uint32_t *cfirst = nullptr;
     uint32_t *hist = nullptr;
+    uint64_t gen = 0;  // contents' generation: new at every load and append (cache key)
 };
 
 // Arguments of the counting kernels (one pass over one candidate set).
@@ -259,11 +260,12 @@ cudaError_t launch_compose_idx(const uint32_t *outer, const uint32_t *inner, uin
 // block_scratch holds compact_scratch_words(m) words: one partial sum per block of
 // COMPACT_ITEMS_PER_BLOCK items plus a slack of 32
 // A count a kernel also writes, with the error word, into pinned host memory (the device
-// address of two mapped host words): the host reads both after a stream synchronisation
-// without a copy of its own.
+// address of three mapped host words): count, error word, then -- after a system-wide
+// fence -- the sequence number `seq`, which tells the host both words are there.
 struct Publish {
     uint32_t *host = nullptr;
     const uint32_t *err = nullptr;
+    uint32_t seq = 0;
 };
 cudaError_t launch_compact(const uint32_t *vals, const uint8_t *flags, uint32_t theta, uint32_t m,
                            uint32_t *idx_out, uint32_t *count_out, uint32_t *block_scratch,

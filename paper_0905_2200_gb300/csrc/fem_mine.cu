@@ -340,8 +340,11 @@ size_t compact_scratch_words(uint32_t m) { return compact_scratch_words_for(m); 
 // (one thread) the count and the error word into the mapped host words, if any
 __device__ __forceinline__ void publish(const Publish &pub, uint32_t count) {
     if (!pub.host) return;
-    pub.host[0] = count;
-    pub.host[1] = *reinterpret_cast<const volatile uint32_t *>(pub.err);
+    volatile uint32_t *h = pub.host;
+    h[0] = count;
+    h[1] = *reinterpret_cast<const volatile uint32_t *>(pub.err);
+    __threadfence_system();
+    h[2] = pub.seq;
 }
 
 __global__ void k_set_count(uint32_t *count, Publish pub) {
