@@ -55,15 +55,15 @@ struct fem_ctx {
     // kernels (count and error word); null where pinned memory is not mapped
     uint32_t *d_pub = nullptr;
     uint32_t pub_seq = 0;  // sequence number of the last publishing launch
+    // mapped pinned words a load's read-back is published to ([0] error word, [1] last
+    // time, [2..258) type counts, [kLoadSeq] sequence number) and their device address
+    uint32_t *h_load = nullptr, *d_load = nullptr;
     // pinned staging of an interval set (so that its upload is asynchronous), and the
     // event after the last upload from it (the next one waits for that copy to leave)
     fem_interval *h_ivl = nullptr;
     cudaEvent_t ivl_ev = nullptr;
     std::vector<fem_interval> ivl_host;  // the interval set of the current call
-    // ring bounds from the capacity table per (stream generation, interval set): the
-    // list entries a node can hold as single times and as clusters
-    uint64_t next_gen = 1;
-    std::map<std::pair<uint64_t, std::string>, std::pair<uint32_t, uint32_t>> ring_bounds;
+    uint64_t next_gen = 1;  // stream contents' generations
     std::map<std::string, DevBuf> bufs;
     std::vector<fem_level_stats> stats;
     std::vector<StreamDev> pool;  // buffers of freed streams, reused by later loads
@@ -75,7 +75,10 @@ struct fem_ctx {
         size_t cap = 0;
     };
     PinBuf pin[FEM_MAX_LEN + 1];
-    cudaEvent_t kev[3] = {nullptr, nullptr, nullptr};  // around the counting kernel and stitch
+    // around the counting kernel and stitch, two sets used in turn, so that a pass's
+    // times can be read after the next pass has been queued
+    cudaEvent_t kev[2][3] = {};
+    int kev_flip = 0;
     // measured mapping choice: launch shape per (N, pass, distinct, log2 m,
     // log2 chunks, K) class
     struct Shape {
@@ -115,8 +118,9 @@ void report_cuda(cudaError_t e, int line) {
 
 // d_small word assignment
 enum { W_COUNT0 = 0, W_COUNT1 = 1, W_COUNT2 = 2, W_INFO = 8 /* 3 words */ };
-// first of the two pinned host words the kernels publish counts to
+// first of the three pinned host words the kernels publish counts to
 constexpr uint32_t kPubWord = 48;
+constexpr uint32_t kLoadSeq = 2 + 256;  // the load read-back's sequence word
 
 size_t stream_bytes(const StreamDev &s) {
     if (!s.t) return 0;
@@ -214,24 +218,29 @@ Publish pub_of(fem_ctx *c) {
     return Publish{c->d_pub, c->d_err, ++c->pub_seq};
 }
 
+// Wait until the mapped word `w` holds `seq` (written by a kernel on st after what it
+// publishes): the host watches the word rather than waiting for the stream, so it can
+// queue the next launches while that kernel retires; after 2 s it waits for the stream.
+int wait_seq(const volatile uint32_t *w, uint32_t seq, cudaStream_t st) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (uint32_t spin = 1; *w != seq; ++spin) {
+        if ((spin & 1023u) == 0 && std::chrono::steady_clock::now() - t0 > std::chrono::seconds(2)) {
+            CK(cudaStreamSynchronize(st));
+            if (*w != seq) return FEM_ECUDA;
+            break;
+        }
+    }
+    std::atomic_thread_fence(std::memory_order_acquire);
+    return FEM_OK;
+}
+
 // A device count and the error word, in one round trip: read from the mapped words once
-// the launch before has published them under its sequence number (the host watches the
-// word rather than waiting for the stream, so it can queue the next launches while that
-// kernel retires; after 2 s it waits for the stream instead), else copied.
+// the launch before has published them under its sequence number, else copied.
 int read_count_err(fem_ctx *c, const uint32_t *d_count, uint32_t *count, uint32_t *err,
                    cudaStream_t st) {
     if (c->d_pub) {
         const volatile uint32_t *h = c->h_small + kPubWord;
-        const auto t0 = std::chrono::steady_clock::now();
-        for (uint32_t spin = 1; h[2] != c->pub_seq; ++spin) {
-            if ((spin & 1023u) == 0 &&
-                std::chrono::steady_clock::now() - t0 > std::chrono::seconds(2)) {
-                CK(cudaStreamSynchronize(st));
-                if (h[2] != c->pub_seq) return FEM_ECUDA;
-                break;
-            }
-        }
-        std::atomic_thread_fence(std::memory_order_acquire);
+        RET(wait_seq(h + 2, c->pub_seq, st));
         *count = h[0];
         *err = h[1];
         return FEM_OK;
@@ -288,63 +297,85 @@ int upload_intervals(fem_ctx *c, const fem_interval *I, uint32_t nI, cudaStream_
 
 // Capacity table of a resident stream for the given widths (host out[a * nh + j]);
 // synchronous on st.  A width >= the stream's last time holds every event of a type.
+// With dense_out (uint32[K * nh]): also the events of each type whose window of each width
+// holds more than `over` events of the type.
 int capacity(fem_ctx *c, const StreamDev &s, const uint32_t *widths, uint32_t nh,
-             uint32_t *out, cudaStream_t st) {
+             uint32_t *out, cudaStream_t st, uint32_t over = 0, uint32_t *dense_out = nullptr) {
     const uint32_t K = s.K;
     std::vector<uint32_t> hw, slot;
     for (uint32_t j = 0; j < nh; ++j)
         if (s.n && widths[j] < s.t_max) hw.push_back(widths[j]), slot.push_back(j);
-    std::vector<uint32_t> hist(K, 0), part((size_t)K * hw.size(), 0);
+    std::vector<uint32_t> hist(K, 0), part((size_t)K * hw.size(), 0), dpart(part.size(), 0);
     CK(cudaMemcpyAsync(hist.data(), s.hist, K * 4, cudaMemcpyDeviceToHost, st));
     if (!hw.empty()) {
         const uint32_t nk = (uint32_t)hw.size();
         uint32_t *d;
-        RET(dbuf(c, "cap", (size_t)nk * (K + 1), &d));
-        uint32_t *d_h = d + (size_t)K * nk;
-        CK(cudaMemsetAsync(d, 0, (size_t)K * nk * 4, st));
+        RET(dbuf(c, "cap", (size_t)nk * (2 * K + 1), &d));
+        uint32_t *d_dense = d + (size_t)K * nk, *d_h = d + (size_t)2 * K * nk;
+        CK(cudaMemsetAsync(d, 0, (size_t)2 * K * nk * 4, st));
         CK(cudaMemcpyAsync(d_h, hw.data(), nk * 4, cudaMemcpyHostToDevice, st));
-        CK(launch_capacity(s, d_h, nk, d, st));
+        CK(launch_capacity(s, d_h, nk, d, st, over, dense_out ? d_dense : nullptr));
         CK(cudaMemcpyAsync(part.data(), d, (size_t)K * nk * 4, cudaMemcpyDeviceToHost, st));
+        if (dense_out)
+            CK(cudaMemcpyAsync(dpart.data(), d_dense, (size_t)K * nk * 4, cudaMemcpyDeviceToHost, st));
     }
     CK(cudaStreamSynchronize(st));
     for (uint32_t a = 0; a < K; ++a) {
-        for (uint32_t j = 0; j < nh; ++j) out[(size_t)a * nh + j] = hist[a];
-        for (size_t q = 0; q < hw.size(); ++q) out[(size_t)a * nh + slot[q]] = part[a * hw.size() + q];
+        for (uint32_t j = 0; j < nh; ++j) {
+            out[(size_t)a * nh + j] = hist[a];
+            if (dense_out) dense_out[(size_t)a * nh + j] = hist[a] > over ? hist[a] : 0u;
+        }
+        for (size_t q = 0; q < hw.size(); ++q) {
+            out[(size_t)a * nh + slot[q]] = part[a * hw.size() + q];
+            if (dense_out) dense_out[(size_t)a * nh + slot[q]] = dpart[a * hw.size() + q];
+        }
     }
     return FEM_OK;
 }
 
-// Bounds on the per-thread exact kernel's lists for the current interval set, from the
-// capacity table (Algorithm 1's pruned list for node k holds type-E_k events within
-// hi_k: at most cap[E_k][hi_k] single times, and at most ceil(hi / (hi - lo)) + 1
-// clusters), maximised over the types and intervals; computed once per stream contents
-// and interval set.
-int ring_bounds(fem_ctx *c, const StreamDev &s, uint32_t *singles, uint32_t *clusters,
+// Whether the per-thread exact kernel's lists should get rings of 32 entries instead of 8
+// for the current interval set, from the capacity table: Algorithm 1's pruned list for
+// node k holds type-E_k events within hi_k, as single times at most cap[E_k][hi_k] of
+// them, as clusters at most ceil(hi / (hi - lo)) + 1.  Larger rings cost occupancy, so
+// they are taken only where lists outgrow 8 often: more than one event in a thousand
+// starts a window of length hi holding more than 8 events of its type (a bursting
+// recording: 7% at 20 ms; an hour of 50 Hz Poisson trains: 0.001%, where the few
+// episodes that overflow are recounted).  Kept with the stream for its contents and the
+// last interval set.
+constexpr uint32_t kRingSmall = 8, kRingLarge = 32;
+int ring_choice(fem_ctx *c, const StreamDev &s, bool *large_singles, bool *large_clusters,
                 cudaStream_t st) {
     const std::vector<fem_interval> &I = c->ivl_host;
     const std::string key(reinterpret_cast<const char *>(I.data()), I.size() * sizeof(fem_interval));
-    auto it = c->ring_bounds.find({s.gen, key});
-    if (it == c->ring_bounds.end()) {
+    if (s.ring_gen != s.gen || s.ring_ivl != key) {
         std::vector<uint32_t> w;
         for (const fem_interval &iv : I) w.push_back(iv.hi_us);
-        std::vector<uint32_t> cap((size_t)s.K * w.size());
-        uint32_t sg = 0, cl = 0;
-        if (!w.empty()) {
-            RET(capacity(c, s, w.data(), (uint32_t)w.size(), cap.data(), st));
+        std::vector<uint32_t> cap((size_t)s.K * w.size()), dense(cap.size());
+        bool sg = false, cl = false;
+        if (!w.empty() && s.n) {
+            RET(capacity(c, s, w.data(), (uint32_t)w.size(), cap.data(), st, kRingSmall,
+                         dense.data()));
             for (size_t j = 0; j < w.size(); ++j) {
                 uint32_t mx = 0;
-                for (uint32_t a = 0; a < s.K; ++a) mx = std::max(mx, cap[(size_t)a * w.size() + j]);
+                uint64_t nd = 0;
+                for (uint32_t a = 0; a < s.K; ++a) {
+                    mx = std::max(mx, cap[(size_t)a * w.size() + j]);
+                    nd += dense[(size_t)a * w.size() + j];
+                }
+                const bool often = nd * 1000 > s.n;
                 const uint32_t span = I[j].hi_us - I[j].lo_us;
                 const uint32_t ncl = (I[j].hi_us + span - 1) / span + 1;
-                sg = std::max(sg, mx);
-                cl = std::max(cl, std::min(mx, ncl));
+                sg = sg || (often && mx > kRingSmall);
+                cl = cl || (often && std::min(mx, ncl) > kRingSmall);
             }
         }
-        if (c->ring_bounds.size() > 64) c->ring_bounds.clear();
-        it = c->ring_bounds.emplace(std::make_pair(s.gen, key), std::make_pair(sg, cl)).first;
+        s.ring_gen = s.gen;
+        s.ring_ivl = key;
+        s.ring_singles = sg;
+        s.ring_clusters = cl;
     }
-    *singles = it->second.first;
-    *clusters = it->second.second;
+    *large_singles = s.ring_singles;
+    *large_clusters = s.ring_clusters;
     return FEM_OK;
 }
 
@@ -519,6 +550,7 @@ struct PassLaunch {
     int N = 0, pass = 0;
     bool distinct = true, chain = false;
     uint32_t R = 1;
+    int evset = 0;  // the kernel event set recorded around it
 };
 
 // Launch one counting pass over m candidates (all of length N) -> out[0..m)
@@ -572,11 +604,11 @@ int count_launch(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const
     uint32_t R = 1;
     if (pass == FEM_PASS_EXACT) R = c->cfg.ring_capacity ? c->cfg.ring_capacity : 8;
     if (pass == FEM_PASS_EXACT && !c->cfg.ring_capacity && kind == FEM_KERNEL_MACHINE) {
-        // rings sized from the capacity table: 32 entries where a window can hold more
-        // than 8 (bursting recordings), so that the first count does not overflow
-        uint32_t sg, cl;
-        RET(ring_bounds(c, s, &sg, &cl, st));
-        if ((P > 1 ? sg : cl) > 8) R = 32;
+        // rings sized from the capacity table where lists outgrow the small rings often
+        // (bursting recordings), so that the first count does not overflow
+        bool sg, cl;
+        RET(ring_choice(c, s, &sg, &cl, st));
+        if (P > 1 ? sg : cl) R = kRingLarge;
     }
     if (P > 1 && pass == FEM_PASS_EXACT && R > 32) R = 32;
     if (!count_config_supported(N, pass, P > 1, R)) return FEM_EINVAL;
@@ -587,7 +619,10 @@ int count_launch(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const
     if (P > 1) {
         RET(dbuf(c, "tables", (size_t)P * m * S_MAX, &p.tables));
     }
-    CK(cudaEventRecord(c->kev[0], st));
+    const int es = c->kev_flip ^= 1;
+    pl->evset = es;
+    cudaEvent_t *kev = c->kev[es];
+    CK(cudaEventRecord(kev[0], st));
     pl->chain = kind == FEM_KERNEL_CHAIN;
     if (kind == FEM_KERNEL_CHAIN) {
         uint32_t T = c->cfg.threads_per_block ? c->cfg.threads_per_block : (T_t ? T_t : chain_threads(m));
@@ -601,9 +636,9 @@ int count_launch(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const
             T = auto_threads(N, pass, P > 1, R, s.offs, m);
         CK(launch_count(N, pass, P > 1, R, T, p, st));
     }
-    CK(cudaEventRecord(c->kev[1], st));
+    CK(cudaEventRecord(kev[1], st));
     if (P > 1) CK(launch_stitch(p.tables, m, P, out, redo, c->d_err, st));
-    CK(cudaEventRecord(c->kev[2], st));
+    CK(cudaEventRecord(kev[2], st));
     pl->p = p;
     pl->R = R;
     return FEM_OK;
@@ -615,8 +650,8 @@ void pass_info(fem_ctx *c, const PassLaunch &pl, PassInfo *info) {
     info->kernel = pl.p.m ? (pl.chain ? FEM_KERNEL_CHAIN : FEM_KERNEL_MACHINE) : 0u;
     info->ms_kernel = info->ms_stitch = 0;
     if (!pl.p.m) return;
-    cudaEventElapsedTime(&info->ms_kernel, c->kev[0], c->kev[1]);
-    cudaEventElapsedTime(&info->ms_stitch, c->kev[1], c->kev[2]);
+    cudaEventElapsedTime(&info->ms_kernel, c->kev[pl.evset][0], c->kev[pl.evset][1]);
+    cudaEventElapsedTime(&info->ms_stitch, c->kev[pl.evset][1], c->kev[pl.evset][2]);
 }
 
 // Complete a launched pass given the error word read after it: report hard errors,
@@ -637,9 +672,9 @@ int count_finish(fem_ctx *c, const StreamDev &s, const PassLaunch &pl, uint32_t 
     uint32_t *ridx, *rg, *rout, *scratch;
     RET(dbuf(c, "redo_idx", m, &ridx));
     RET(dbuf(c, "redo_scratch", compact_scratch_words(m), &scratch));
-    CK(launch_compact(nullptr, redo, 0, m, ridx, c->d_small + W_COUNT2, scratch, st));
-    uint32_t r;
-    RET(read_words(c, c->d_small + W_COUNT2, 1, &r, st));
+    CK(launch_compact(nullptr, redo, 0, m, ridx, c->d_small + W_COUNT2, scratch, st, pub_of(c)));
+    uint32_t r, er;
+    RET(read_count_err(c, c->d_small + W_COUNT2, &r, &er, st));
     if (std::getenv("FEM_DEBUG"))
         std::fprintf(stderr, "fem: pass %d N=%d m=%u P=%u R=%u: %u episodes recounted (err %#x)\n",
                      pass, N, m, P, R, r, e);
@@ -656,14 +691,20 @@ int count_finish(fem_ctx *c, const StreamDev &s, const PassLaunch &pl, uint32_t 
         bool mc;
         uint32_t R;
         bool same_segments;
+        uint32_t cls;  // entry-class slots of the segmented tables
     };
     std::vector<Try> tries;
-    // (a latest-chain launch that only ran out of entry-class slots goes straight to the
-    // one-chunk segments with four times the slots: its few episodes finish sooner there)
-    if (pl.chain && (e & ~ERR_CLASS & ERR_CAP)) tries.push_back({P > 1, 8u, true});
-    tries.push_back({true, 32u, false});
-    tries.push_back({false, 32u, false});
-    tries.push_back({false, 128u, false});
+    if (pl.chain) {
+        // a latest-chain launch that only ran out of its entry-class slots: the per-thread
+        // kernel has twice the slots and merges classes before refusing one; one chunk per
+        // segment, so that the few episodes spread over the GPU.  Other guards: the
+        // per-thread kernel with the pass's own segments.
+        if (e & ~ERR_CLASS & ERR_CAP) tries.push_back({P > 1, 8u, true, S_MAX});
+        else tries.push_back({true, 8u, false, S_MAX});
+    }
+    tries.push_back({true, 32u, false, S_RECOUNT});  // four times the slots, larger rings
+    tries.push_back({false, 32u, false, S_MAX});
+    tries.push_back({false, 128u, false, S_MAX});
     for (const Try &tr : tries) {
         if (tr.mc && !distinct) continue;
         CK(cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), st));
@@ -674,9 +715,7 @@ int count_finish(fem_ctx *c, const StreamDev &s, const PassLaunch &pl, uint32_t 
         RET(dbuf(c, "redo2", r, &q.redo));
         CK(cudaMemsetAsync(q.redo, 0, r, st));
         const uint32_t Rq = pass == FEM_PASS_EXACT ? tr.R : 1;
-        // the segmented recount has four times the entry-class slots (episodes come
-        // here when a window held more classes than a table could)
-        const uint32_t cls = tr.mc && s.n_chunks > 1 && !tr.same_segments ? S_RECOUNT : S_MAX;
+        const uint32_t cls = tr.mc && s.n_chunks > 1 ? tr.cls : S_MAX;
         if (tr.same_segments) {
             if (q.P > 1) RET(dbuf(c, "redo_tables", (size_t)q.P * r * cls, &q.tables));
         } else if (tr.mc && s.n_chunks > 1) {
@@ -874,14 +913,23 @@ int fem_create(fem_ctx **out, int device, size_t mem_budget_bytes) {
         cudaMalloc(&c->d_err, sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc(&c->d_small, 64 * sizeof(uint32_t)) != cudaSuccess ||
         cudaMallocHost(&c->h_small, 64 * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost(&c->h_load, (kLoadSeq + 1) * sizeof(uint32_t)) != cudaSuccess ||
         cudaMallocHost(&c->h_ivl, (FEM_MAX_INTERVALS + 1) * sizeof(fem_interval)) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ivl_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreate(&c->kev[0]) != cudaSuccess || cudaEventCreate(&c->kev[1]) != cudaSuccess ||
-        cudaEventCreate(&c->kev[2]) != cudaSuccess || cudaEventCreate(&c->tev[0]) != cudaSuccess ||
+        cudaEventCreate(&c->tev[0]) != cudaSuccess ||
         cudaEventCreate(&c->tev[1]) != cudaSuccess) {
         cudaGetLastError();
         fem_destroy(c);
         return FEM_ECUDA;
+    }
+    for (auto &set : c->kev) {
+        for (auto &e : set) {
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                fem_destroy(c);
+                return FEM_ECUDA;
+            }
+        }
     }
     for (auto &e : c->ev) {
         if (cudaEventCreate(&e) != cudaSuccess) {
@@ -892,10 +940,14 @@ int fem_create(fem_ctx **out, int device, size_t mem_budget_bytes) {
     }
     cudaMemset(c->d_err, 0, sizeof(uint32_t));
     std::memset(c->h_small, 0, 64 * sizeof(uint32_t));  // no stale sequence number
+    std::memset(c->h_load, 0, (kLoadSeq + 1) * sizeof(uint32_t));
     {
-        void *dp = nullptr;
-        if (cudaHostGetDevicePointer(&dp, c->h_small, 0) == cudaSuccess && dp)
+        void *dp = nullptr, *dl = nullptr;
+        if (cudaHostGetDevicePointer(&dp, c->h_small, 0) == cudaSuccess && dp &&
+            cudaHostGetDevicePointer(&dl, c->h_load, 0) == cudaSuccess && dl) {
             c->d_pub = static_cast<uint32_t *>(dp) + kPubWord;
+            c->d_load = static_cast<uint32_t *>(dl);
+        }
         cudaGetLastError();
     }
     *out = c;
@@ -911,12 +963,14 @@ int fem_destroy(fem_ctx *c) {
     if (c->d_err) cudaFree(c->d_err);
     if (c->d_small) cudaFree(c->d_small);
     if (c->h_small) cudaFreeHost(c->h_small);
+    if (c->h_load) cudaFreeHost(c->h_load);
     if (c->h_ivl) cudaFreeHost(c->h_ivl);
     if (c->ivl_ev) cudaEventDestroy(c->ivl_ev);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
-    for (auto &e : c->kev)
-        if (e) cudaEventDestroy(e);
+    for (auto &set : c->kev)
+        for (auto &e : set)
+            if (e) cudaEventDestroy(e);
     for (auto &e : c->tev)
         if (e) cudaEventDestroy(e);
     for (StreamDev &s : c->pool) free_stream_buffers(s);
@@ -1061,7 +1115,23 @@ int fem_load_stream(fem_ctx *c, const uint8_t *types, const uint32_t *t_us, uint
                 break;
             }
         }
-        // error word, last time and type histogram in one round trip
+        // error word, last time and type histogram in one round trip: published by a
+        // kernel into mapped words, else copied
+        if (c->d_load) {
+            const uint32_t seq = ++c->pub_seq;
+            if (launch_publish_load(c->d_err, n ? s.t + (n - 1) : nullptr, s.hist, n_types,
+                                    c->d_load, kLoadSeq, seq, st) != cudaSuccess) {
+                rc = FEM_ECUDA;
+                break;
+            }
+            if ((rc = wait_seq(c->h_load + kLoadSeq, seq, st)) != FEM_OK) break;
+            const volatile uint32_t *hv = c->h_load;
+            if ((rc = err_status(hv[0])) != FEM_OK) break;
+            if (n) s.t_max = hv[1];
+            hist_host.assign(n_types, 0);
+            for (uint32_t a = 0; a < n_types; ++a) hist_host[a] = hv[2 + a];
+            break;
+        }
         void *hp;
         if ((rc = pinbuf(c, 0, (2 + 256) * sizeof(uint32_t), st, &hp)) != FEM_OK) break;
         uint32_t *hw = static_cast<uint32_t *>(hp);
@@ -1555,19 +1625,10 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
         cudaEventRecord(c->ev[4], st);
         uint32_t ms;
         RETF(compact_and_read(rel, m, idx_s, W_COUNT0, scratch, plr, &ms, c->ev[5]));
-        // work statistics, queued after the wait: the device would otherwise sit idle
-        // while the host prepares the next launch
-        CKF(launch_touched(cands, nullptr, m, s.hist, touched + 2 * N, st));
-        PassInfo pi;
-        pass_info(c, plr, &pi);
-        cudaEventElapsedTime(&ls.ms_generate, c->ev[0], c->ev[1]);
-        cudaEventElapsedTime(&ls.ms_relaxed, c->ev[2], c->ev[3]);
-        ls.segments = pi.segments;
-        ls.kernel_relaxed = pi.kernel;
-        ls.ms_relaxed_kernel = pi.ms_kernel;
-        ls.ms_relaxed_stitch = pi.ms_stitch;
         ls.survivors = ms;
-        // second pass (Algorithm 1) on the survivors, then keep exact >= theta
+        // second pass (Algorithm 1) on the survivors, then keep exact >= theta; the
+        // relaxed pass's times are read and its statistics queued after this launch, so
+        // that the device does not wait for the host's bookkeeping
         RETF(dbuf(c, "ex", ms, &ex));
         RETF(dbuf(c, "idx_f", ms, &idx_f));
         PassLaunch plx;
@@ -1578,9 +1639,23 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
             RETF(count_launch(c, s, cands, idx_s, ms, (int)N, d_ivl, nI, FEM_PASS_EXACT, ex, true,
                               st, &plx));
         cudaEventRecord(c->ev[7], st);
+        PassInfo pi;
+        pass_info(c, plr, &pi);
+        cudaEventElapsedTime(&ls.ms_generate, c->ev[0], c->ev[1]);
+        cudaEventElapsedTime(&ls.ms_relaxed, c->ev[2], c->ev[3]);
+        ls.segments = pi.segments;
+        ls.kernel_relaxed = pi.kernel;
+        ls.ms_relaxed_kernel = pi.ms_kernel;
+        ls.ms_relaxed_stitch = pi.ms_stitch;
         uint32_t f = 0;
         if (ms) RETF(compact_and_read(ex, ms, idx_f, W_COUNT1, scratch, plx, &f, nullptr));
-        CKF(launch_touched(cands, idx_s, ms, s.hist, touched + 2 * N + 1, st));
+        // work statistics of both passes (idx_s and the candidates stay until the next
+        // level): queued behind the next wait's publishing launch where there is one
+        auto queue_touched = [&]() -> int {
+            CK(launch_touched(cands, nullptr, m, s.hist, touched + 2 * N, st));
+            CK(launch_touched(cands, idx_s, ms, s.hist, touched + 2 * N + 1, st));
+            return FEM_OK;
+        };
         PassInfo pe;
         pass_info(c, plx, &pe);
         cudaEventElapsedTime(&ls.ms_compact, c->ev[4], c->ev[5]);
@@ -1590,7 +1665,10 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
         ls.kernel_exact = ms ? pe.kernel : 0;
         ls.frequent = f;
         c->stats.push_back(ls);
-        if (f == 0) break;
+        if (f == 0) {
+            RETF(queue_touched());
+            break;
+        }
         RETF(dbuf(c, "fcnt", f, &fcnt));
         RETF(dbuf(c, "F", f, &F));
         CKF(launch_gather_frequent(cands, idx_s, idx_f, f, ex, F, fcnt, st));
@@ -1600,7 +1678,10 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
         CKF(cudaMemcpyAsync(static_cast<uint8_t *>(h) + (size_t)f * sizeof(fem_episode), fcnt,
                             (size_t)f * 4, cudaMemcpyDeviceToHost, st));
         staged_f[N] = f;
-        if (N == max_len) break;
+        if (N == max_len) {
+            RETF(queue_touched());
+            break;
+        }
         // join level N -> N + 1
         uint32_t *jc, *joff;
         RETF(dbuf(c, "jc", f, &jc));
@@ -1608,6 +1689,7 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
         cudaEventRecord(c->ev[0], st);
         CKF(launch_join_count(F, f, N, repeats, jc, c->sm_count, st));
         CKF(launch_exclusive_scan(jc, f, joff, c->d_small + W_COUNT2, scratch, st, pub_of(c)));
+        RETF(queue_touched());
         uint32_t mn, ej;
         RETF(read_count_err(c, c->d_small + W_COUNT2, &mn, &ej, st));
         RETF(err_status(ej));

@@ -13,6 +13,8 @@
 // (TMA) copy; each thread then walks only the groups of its episode's types.
 #pragma once
 
+#include <string>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -59,6 +61,10 @@ struct StreamDev {
     uint32_t *cfirst = nullptr;
     uint32_t *hist = nullptr;
     uint64_t gen = 0;  // contents' generation: new at every load and append (cache key)
+    // the ring choice for the last interval set counted over these contents (host side)
+    mutable uint64_t ring_gen = 0;
+    mutable std::string ring_ivl;
+    mutable bool ring_singles = false, ring_clusters = false;
 };
 
 // Arguments of the counting kernels (one pass over one candidate set).
@@ -186,10 +192,16 @@ cudaError_t launch_load_stream(StreamDev &s, cudaStream_t st, uint32_t *d_err,
 cudaError_t launch_bucket_chunks(StreamDev &s, uint32_t c0, uint32_t c1, cudaStream_t st,
                                  uint32_t *d_err = nullptr);
 // hist[ty[i]] += sign (+1 or -1) for i < n
+// host[0] = *err, host[1] = *t_last (0 if null), host[2 .. 2 + K) = hist, then
+// host[seq_word] = seq (host: the device address of mapped pinned words)
+cudaError_t launch_publish_load(const uint32_t *err, const uint32_t *t_last, const uint32_t *hist,
+                                uint32_t K, uint32_t *host, uint32_t seq_word, uint32_t seq,
+                                cudaStream_t st);
 // cap[a * nh + j] (zeroed by the caller): the most type-a events in a closed window of
-// length h[j] (device array)
+// length h[j] (device array); with dense (zeroed), also the number of type-a events whose
+// window of length h[j] holds more than `over` events
 cudaError_t launch_capacity(const StreamDev &s, const uint32_t *h, uint32_t nh, uint32_t *cap,
-                            cudaStream_t st);
+                            cudaStream_t st, uint32_t over = 0, uint32_t *dense = nullptr);
 cudaError_t launch_hist_add(const uint8_t *ty, uint64_t n, uint32_t K, int sign, uint32_t *hist,
                             cudaStream_t st);
 // dst[idx[i]] = src[i] and flags[idx[i]] = 1 for i < *m_dev (grid sized for m_max)

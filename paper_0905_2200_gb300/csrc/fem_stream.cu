@@ -159,17 +159,46 @@ cudaError_t launch_hist_add(const uint8_t *ty, uint64_t n, uint32_t K, int sign,
     return cudaGetLastError();
 }
 
+// What a load reads back, into mapped pinned host words: the error word, the last time
+// and the K type counts, then (after each thread's system-wide fence and a barrier) the
+// sequence number the host watches for.
+__global__ void __launch_bounds__(256) k_publish_load(const uint32_t *err, const uint32_t *t_last,
+                                                      const uint32_t *hist, uint32_t K,
+                                                      uint32_t *host, uint32_t seq_word,
+                                                      uint32_t seq) {
+    volatile uint32_t *h = host;
+    for (uint32_t a = threadIdx.x; a < K; a += blockDim.x) h[2 + a] = hist[a];
+    if (threadIdx.x == 0) {
+        h[0] = *reinterpret_cast<const volatile uint32_t *>(err);
+        h[1] = t_last ? *t_last : 0u;
+    }
+    __threadfence_system();
+    __syncthreads();
+    if (threadIdx.x == 0) h[seq_word] = seq;
+}
+
+cudaError_t launch_publish_load(const uint32_t *err, const uint32_t *t_last, const uint32_t *hist,
+                                uint32_t K, uint32_t *host, uint32_t seq_word, uint32_t seq,
+                                cudaStream_t st) {
+    k_publish_load<<<1, 256, 0, st>>>(err, t_last, hist, K, host, seq_word, seq);
+    note_launch();
+    return cudaGetLastError();
+}
+
 // Capacity table: cap[a * nh + j] = the most type-a events inside one closed window of
 // length h[j].  A fullest window can start at one of its events, so one thread per
 // (chunk, type) takes the events of its group in turn and, for each width, walks a
 // second pointer forward through the type's groups of this and the following chunks
 // while the times stay within h of the current event (two pointers: the forward one
 // never moves back within the thread's group); the per-thread maxima meet by atomicMax.
+// With `dense`, dense[a * nh + j] also counts the type-a events whose window of length
+// h[j] holds more than `over` events (how often a bound is approached, not only whether).
 __global__ void __launch_bounds__(256) k_capacity(const uint2 *__restrict__ bev,
                                                   const uint16_t *__restrict__ boff, uint32_t offs,
                                                   uint32_t n_chunks, uint32_t K,
                                                   const uint32_t *__restrict__ h, uint32_t nh,
-                                                  uint32_t *__restrict__ cap) {
+                                                  uint32_t *__restrict__ cap, uint32_t over,
+                                                  uint32_t *__restrict__ dense) {
     const uint64_t gid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (uint64_t)n_chunks * K) return;
     const uint32_t c = (uint32_t)(gid / K), a = (uint32_t)(gid % K);
@@ -180,7 +209,7 @@ __global__ void __launch_bounds__(256) k_capacity(const uint2 *__restrict__ bev,
         const uint64_t w = h[j];
         // forward pointer: chunk fc, index fk in that chunk's type-a group [fk, f1)
         uint32_t fc = c, fk = g0, f1 = g1;
-        uint32_t ahead = 0, best = 0;  // events in [current, forward pointer)
+        uint32_t ahead = 0, best = 0, n_over = 0;  // events in [current, forward pointer)
         for (uint32_t k = g0; k < g1; ++k) {
             const uint64_t lim = (uint64_t)ev[k].x + w;
             for (;;) {
@@ -194,18 +223,21 @@ __global__ void __launch_bounds__(256) k_capacity(const uint2 *__restrict__ bev,
                 ++ahead;
             }
             best = max(best, ahead);
+            n_over += ahead > over;
             --ahead;  // the current event leaves the window's start
         }
         atomicMax(&cap[a * nh + j], best);
+        if (dense && n_over) atomicAdd(&dense[a * nh + j], n_over);
     }
 }
 
 cudaError_t launch_capacity(const StreamDev &s, const uint32_t *h, uint32_t nh, uint32_t *cap,
-                            cudaStream_t st) {
+                            cudaStream_t st, uint32_t over, uint32_t *dense) {
     const uint64_t threads = (uint64_t)s.n_chunks * s.K;
     if (threads == 0 || nh == 0) return cudaSuccess;
     k_capacity<<<(uint32_t)((threads + 255) / 256), 256, 0, st>>>(s.bev, s.boff, s.offs,
-                                                                   s.n_chunks, s.K, h, nh, cap);
+                                                                   s.n_chunks, s.K, h, nh, cap,
+                                                                   over, dense);
     note_launch();
     return cudaGetLastError();
 }
