@@ -72,8 +72,10 @@ def kernel_source_hash() -> str:
 
 
 def dom_kernel(level: int, ps: str, kind: int = 1) -> str:
-    """Name of the library's counting kernel for a (length, pass) launch; kind 2 is the
-    latest-chain kernel, 1 the per-thread machine."""
+    """Name of the library's counting kernel for a (length, pass) launch; kind 3 is the
+    level-2 pair kernel, 2 the latest-chain kernel, 1 the per-thread machine."""
+    if kind == 3:
+        return "k_pairs_relaxed"
     if kind == 2:
         return f"k_chain<{level}, {ps}>"
     if ps == "exact":

@@ -551,6 +551,7 @@ struct PassLaunch {
     bool distinct = true, chain = false;
     uint32_t R = 1;
     int evset = 0;  // the kernel event set recorded around it
+    bool pairs = false;  // the level-2 pair kernel
 };
 
 // Launch one counting pass over m candidates (all of length N) -> out[0..m)
@@ -644,10 +645,70 @@ int count_launch(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const
     return FEM_OK;
 }
 
+// The relaxed pass of fem_mine_levelwise's level 2 (f frequent types x nI <= 4 intervals,
+// m = f (f - 1) nI candidates in canonical order) with every interval variant of an
+// ordered type pair in one thread (fem_pairs.cu); segments for about three 256-thread
+// blocks per SM (or the configured count), tables, stitch and completion as in
+// count_launch.
+int count_launch_pairs(fem_ctx *c, const StreamDev &s, const fem_episode *cands, uint32_t m,
+                       uint32_t f, const uint2 *d_ivl, uint32_t nI, uint32_t *out, cudaStream_t st,
+                       PassLaunch *pl) {
+    pl->p = CountParams{};
+    pl->N = 2, pl->pass = FEM_PASS_RELAXED, pl->distinct = true, pl->chain = false;
+    pl->pairs = true;
+    if (m == 0) return FEM_OK;
+    CountParams p{};
+    p.bev = s.bev;
+    p.boff = s.boff;
+    p.cfirst = s.cfirst;
+    p.t = s.t;
+    p.offs = s.offs;
+    p.n_chunks = s.n_chunks;
+    p.n = s.n;
+    p.K = s.K;
+    p.cands = cands;
+    p.m = m;
+    p.ivl = d_ivl;
+    p.n_ivl = nI;
+    p.out = out;
+    p.err = c->d_err;
+    p.pair_types = f;
+    uint8_t *redo;
+    RET(dbuf(c, "redo", m, &redo));
+    CK(cudaMemsetAsync(redo, 0, m, st));
+    p.redo = redo;
+    const uint64_t pairs = (uint64_t)f * (f - 1);
+    uint32_t P;
+    if (c->cfg.segments) {
+        P = std::min<uint32_t>(c->cfg.segments, std::max<uint32_t>(s.n_chunks, 1));
+    } else {
+        const uint64_t target = (uint64_t)c->sm_count * 3 * 256;
+        P = (uint32_t)std::min<uint64_t>((target + pairs - 1) / pairs, std::max<uint32_t>(s.n_chunks, 1));
+    }
+    const uint32_t cps = P > 1 ? (s.n_chunks + P - 1) / P : std::max<uint32_t>(s.n_chunks, 1);
+    if (P > 1) P = (s.n_chunks + cps - 1) / cps;
+    p.cps = cps;
+    p.P = P;
+    if (P > 1) RET(dbuf(c, "tables", (size_t)P * m * S_MAX, &p.tables));
+    const int es = c->kev_flip ^= 1;
+    pl->evset = es;
+    cudaEvent_t *kev = c->kev[es];
+    CK(cudaEventRecord(kev[0], st));
+    CK(launch_pairs_relaxed(p, 256, st));
+    CK(cudaEventRecord(kev[1], st));
+    if (P > 1) CK(launch_stitch(p.tables, m, P, out, redo, c->d_err, st));
+    CK(cudaEventRecord(kev[2], st));
+    pl->p = p;
+    pl->R = 1;
+    return FEM_OK;
+}
+
 // Kernel and stitch times of the last launched pass (its events have completed).
 void pass_info(fem_ctx *c, const PassLaunch &pl, PassInfo *info) {
     info->segments = pl.p.m ? pl.p.P : 0;
-    info->kernel = pl.p.m ? (pl.chain ? FEM_KERNEL_CHAIN : FEM_KERNEL_MACHINE) : 0u;
+    info->kernel = pl.p.m ? (pl.pairs ? FEM_KERNEL_PAIRS
+                                      : pl.chain ? FEM_KERNEL_CHAIN : FEM_KERNEL_MACHINE)
+                          : 0u;
     info->ms_kernel = info->ms_stitch = 0;
     if (!pl.p.m) return;
     cudaEventElapsedTime(&info->ms_kernel, c->kev[pl.evset][0], c->kev[pl.evset][1]);
@@ -694,6 +755,7 @@ int count_finish(fem_ctx *c, const StreamDev &s, const PassLaunch &pl, uint32_t 
         uint32_t cls;  // entry-class slots of the segmented tables
     };
     std::vector<Try> tries;
+    if (pl.pairs) tries.push_back({true, 8u, false, S_MAX});  // one chunk per segment
     if (pl.chain) {
         // a latest-chain launch that only ran out of its entry-class slots: the per-thread
         // kernel has twice the slots and merges classes before refusing one; one chunk per
@@ -1285,6 +1347,41 @@ int fem_capacity_table(fem_ctx *c, int32_t id, const uint32_t *widths, uint32_t 
     if (!s) return FEM_ENOSTREAM;
     cudaSetDevice(c->device);
     return capacity(c, *s, widths, nh, cap_out, c->own);
+}
+
+int fem_count_pairs_relaxed(fem_ctx *c, int32_t id, const uint8_t *types, uint32_t f,
+                            const fem_interval *I, uint32_t nI, uint32_t *counts_out) {
+    if (!c || !types || !counts_out || f < 2 || f > 256 || nI == 0 || nI > 4) return FEM_EINVAL;
+    const StreamDev *s = find_stream(c, id);
+    if (!s) return FEM_ENOSTREAM;
+    RET(check_intervals(*s, I, nI));
+    bool seen[256] = {};
+    for (uint32_t i = 0; i < f; ++i) {
+        if (types[i] >= s->K || seen[types[i]]) return FEM_EINVAL;
+        seen[types[i]] = true;
+    }
+    cudaSetDevice(c->device);
+    cudaStream_t st = c->own;
+    CK(cudaMemsetAsync(c->d_err, 0, 4, st));
+    uint2 *d_ivl;
+    RET(upload_intervals(c, I, nI, st, &d_ivl));
+    const uint32_t m = f * (f - 1) * nI;
+    uint32_t *ft, *out;
+    fem_episode *cands;
+    RET(dbuf(c, "pair_types", f, &ft));
+    RET(dbuf(c, "pair_cands", m, &cands));
+    RET(dbuf(c, "pair_out", m, &out));
+    std::vector<uint32_t> ftv(types, types + f);
+    CK(cudaMemcpyAsync(ft, ftv.data(), f * 4, cudaMemcpyHostToDevice, st));
+    CK(launch_level2(ft, f, nI, false, cands, st));
+    PassLaunch pl;
+    RET(count_launch_pairs(c, *s, cands, m, f, d_ivl, nI, out, st, &pl));
+    uint32_t e;
+    RET(read_err(c, st, &e));
+    RET(count_finish(c, *s, pl, e, st));
+    CK(cudaMemcpyAsync(counts_out, out, (size_t)m * 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return FEM_OK;
 }
 
 int fem_count_candidates(fem_ctx *c, int32_t id, const fem_episode *cands, uint32_t m,

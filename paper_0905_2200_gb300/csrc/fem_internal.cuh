@@ -94,6 +94,8 @@ struct CountParams {
     // (single segment only)
     uint32_t *state;            // per-candidate carried state (count, machine), in and out
     uint32_t state_stride;      // words per candidate: 1 + (N-1) relaxed, 1 + (N-1)(1 + 2R) exact
+    // (level-2 pair kernel) frequent types f of a level-2 set of f (f - 1) n_ivl candidates
+    uint32_t pair_types;
 };
 
 // MapConcatenate as printed (fem_literal.cu): time segments (tau[p], tau[p+1]]
@@ -197,6 +199,10 @@ cudaError_t launch_bucket_chunks(StreamDev &s, uint32_t c0, uint32_t c1, cudaStr
 cudaError_t launch_publish_load(const uint32_t *err, const uint32_t *t_last, const uint32_t *hist,
                                 uint32_t K, uint32_t *host, uint32_t seq_word, uint32_t seq,
                                 cudaStream_t st);
+// fem_pairs.cu: the relaxed pass of a level-2 set, all interval variants of an ordered
+// type pair in one thread (p.pair_types = f, p.n_ivl <= 4; P > 1: MapConcatenate tables)
+cudaError_t launch_pairs_relaxed(const CountParams &p, uint32_t threads, cudaStream_t st);
+size_t pairs_smem_bytes(bool mc, uint32_t threads, uint32_t offs);
 // cap[a * nh + j] (zeroed by the caller): the most type-a events in a closed window of
 // length h[j] (device array); with dense (zeroed), also the number of type-a events whose
 // window of length h[j] holds more than `over` events

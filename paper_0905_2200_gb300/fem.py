@@ -42,7 +42,7 @@ class fem_config(ctypes.Structure):
                 ("ring_capacity", ctypes.c_uint32), ("kernel", ctypes.c_uint32)]
 
 
-KERNEL_AUTO, KERNEL_MACHINE, KERNEL_CHAIN = 0, 1, 2
+KERNEL_AUTO, KERNEL_MACHINE, KERNEL_CHAIN, KERNEL_PAIRS = 0, 1, 2, 3
 
 
 class fem_level_stats(ctypes.Structure):
@@ -72,6 +72,7 @@ REQ_ONESHOT, REQ_STANDING = 0, 1
 
 EXPORTS = ["fem_create", "fem_destroy", "fem_mem_usage", "fem_append_stream", "fem_set_config", "fem_load_stream", "fem_free_stream",
            "fem_type_counts", "fem_capacity_table", "fem_count_candidates", "fem_count_two_pass",
+           "fem_count_pairs_relaxed",
            "fem_mine_levelwise", "fem_result_level", "fem_result_max_level", "fem_result_free",
            "fem_last_mine_stats", "fem_strerror", "fem_kernel_launches", "fem_select_noalloc",
            "fem_batch_create", "fem_batch_run", "fem_batch_destroy",
@@ -105,6 +106,7 @@ def load(path: str | None = None):
         "fem_free_stream": (I, [vp, i32]),
         "fem_type_counts": (I, [vp, i32, vp]),
         "fem_capacity_table": (I, [vp, i32, vp, u32, vp]),
+        "fem_count_pairs_relaxed": (I, [vp, i32, vp, u32, ctypes.POINTER(fem_interval), u32, vp]),
         "fem_count_candidates": (I, [vp, i32, vp, u32, I, ctypes.POINTER(fem_interval), u32, I,
                                      vp, I, vp]),
         "fem_count_two_pass": (I, [vp, i32, vp, u32, I, ctypes.POINTER(fem_interval), u32, u32,
@@ -344,6 +346,18 @@ def fem_capacity_table(ctx, sid, widths_us, n_types) -> np.ndarray:
     out = np.zeros((n_types, len(w)), np.uint32)
     _check(load().fem_capacity_table(ctx, int(sid), w.ctypes.data_as(ctypes.c_void_p), len(w),
                                      out.ctypes.data_as(ctypes.c_void_p)), "fem_capacity_table")
+    return out
+
+
+def fem_count_pairs_relaxed(ctx, sid, types, intervals) -> np.ndarray:
+    """Relaxed counts of every ordered pair of distinct `types` with every interval, in
+    level 2's canonical order (uint32[f (f - 1) len(intervals)])."""
+    ty = np.ascontiguousarray(types, dtype=np.uint8).reshape(-1)
+    iv, nI = _intervals(intervals)
+    out = np.zeros(len(ty) * (len(ty) - 1) * nI, np.uint32)
+    _check(load().fem_count_pairs_relaxed(ctx, int(sid), ty.ctypes.data_as(ctypes.c_void_p),
+                                          len(ty), iv, nI, out.ctypes.data_as(ctypes.c_void_p)),
+           "fem_count_pairs_relaxed")
     return out
 
 
