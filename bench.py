@@ -44,12 +44,12 @@ OPS_PER_TOUCHED = {"relaxed": 4, "exact": 6}
 # ("level/pass") from one ncu capture, keyed by the SHA-256 of the kernel source it was
 # taken on and the workload (no entry: stale or not captured, reported as null).
 NCU_TRAFFIC = {
-    # ncu --set full of the first mining step with the rule's kernels and shapes (--no-tune;
-    # the tuned step runs the same kernels): dram__bytes_read.sum + dram__bytes_write.sum
-    # per launch (level 3 exact was not among the four captured launches)
-    "7805d7504c0a5dfa": {
-        "single_recording_64types_300s": {"2/relaxed": 13667072, "2/exact": 8665344,
-                                          "3/relaxed": 12862976},
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:"k_count|k_chain"
+    # -c 5 over the first mining step with the rule's kernels and shapes (--no-tune; the
+    # tuned step runs the same kernels), per launch
+    "9a5c87245245fce0": {
+        "single_recording_64types_300s": {"2/relaxed": 13232384, "2/exact": 8706816,
+                                          "3/relaxed": 12876544, "3/exact": 3915520},
     },
 }
 
