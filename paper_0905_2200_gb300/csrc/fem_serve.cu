@@ -522,7 +522,8 @@ int fem_server_submit(fem_server *v, int32_t sid, const fem_episode *cands, uint
     StreamDev &s = ss.s;
     for (uint32_t i = 0; i < nI; ++i)
         if (I[i].lo_us >= I[i].hi_us || I[i].hi_us > kServeMaxHi) return FEM_EINVAL;
-    std::vector<uint32_t> order(m);
+    // candidates grouped by length, stable (a counting sort over the eight lengths)
+    uint32_t by_len[FEM_MAX_LEN + 2] = {};
     for (uint32_t c = 0; c < m; ++c) {
         const fem_episode &e = cands[c];
         if (e.len < 1 || e.len > FEM_MAX_LEN) return FEM_EINVAL;
@@ -530,11 +531,12 @@ int fem_server_submit(fem_server *v, int32_t sid, const fem_episode *cands, uint
             if (e.types[k] >= s.K) return FEM_EINVAL;
         for (uint32_t k = 0; k + 1 < e.len; ++k)
             if (e.ivl[k] >= nI) return FEM_EINVAL;
-        order[c] = c;
+        ++by_len[e.len + 1];
     }
     if (v->active >= v->cfg.max_active) return FEM_EADMIT;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](uint32_t a, uint32_t b) { return cands[a].len < cands[b].len; });
+    for (uint32_t N = 1; N <= FEM_MAX_LEN + 1; ++N) by_len[N] += by_len[N - 1];
+    std::vector<uint32_t> order(m);
+    for (uint32_t c = 0; c < m; ++c) order[by_len[cands[c].len]++] = c;
     Request r;
     r.id = v->next_req;
     r.sid = sid;
