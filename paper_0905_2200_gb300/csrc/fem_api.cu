@@ -435,19 +435,23 @@ bool chain_eligible(const fem_ctx *c, int N, bool distinct, uint32_t m) {
            (c->clustered || (N >= 3 && m <= kChainSmallSet));
 }
 
-// The rule's kernel where no measurement says otherwise: the latest-chain kernels for the
-// exact pass, whose per-thread machine (sliding-window lists) costs the most per event,
-// over at least a block of candidates, or over a small set (there a block's eight warps
-// build the prefix lists together where the per-thread machine leaves a single warp per
-// block: level-3 exact of 32 survivors 0.097 -> 0.063 ms); the per-thread machine for the
-// relaxed pass, whose single slot per node makes it cheap (the two measured within a few
-// percent of each other on the 64-type recording, and the chain form pays for class and
-// list overflows).
+// The rule's kernel where no measurement says otherwise.  The latest-chain kernels for
+// the exact pass, whose per-thread machine (sliding-window lists) costs the most per
+// event, over at least a block of candidates, or over a small set (there a block's eight
+// warps build the prefix lists together where the per-thread machine leaves a single
+// warp per block: level-3 exact of 32 survivors 0.097 -> 0.063 ms).  For the relaxed pass,
+// whose single slot per node makes the per-thread machine cheap, the latest-chain kernels
+// only for longer episodes in large sets, where many candidates share each prefix list
+// (the deep variant of the 64-type recording: level 3, 2.4M candidates, 55.5 -> 32.0 ms;
+// level 4, 73k, 3.65 -> 1.60 ms), or in small sets; at the bench step's 13,657 level-3
+// candidates, many of them in short prefix runs, the two measured level.
+constexpr uint32_t kChainLargeSet = 32768;
 uint32_t rule_kernel(const fem_ctx *c, int N, int pass, bool distinct, uint32_t m) {
-    return chain_eligible(c, N, distinct, m) && pass == FEM_PASS_EXACT &&
-                   (m >= 256 || m <= kChainSmallSet)
-               ? FEM_KERNEL_CHAIN
-               : FEM_KERNEL_MACHINE;
+    if (!chain_eligible(c, N, distinct, m)) return FEM_KERNEL_MACHINE;
+    if (pass == FEM_PASS_EXACT)
+        return m >= 256 || m <= kChainSmallSet ? FEM_KERNEL_CHAIN : FEM_KERNEL_MACHINE;
+    return N >= 3 && (m >= kChainLargeSet || m <= kChainSmallSet) ? FEM_KERNEL_CHAIN
+                                                                   : FEM_KERNEL_MACHINE;
 }
 
 // Block size of the latest-chain kernels: 256 threads, also for a few episodes (the
