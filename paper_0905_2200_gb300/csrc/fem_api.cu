@@ -427,12 +427,12 @@ uint32_t ceil_log2(uint64_t v) {
 }
 
 // The latest-chain kernels count distinct-type episodes of 2..8 nodes in sets that come
-// in runs of shared prefixes, and small sets of longer episodes however scattered (the
-// kernel splits a tile's prefixes into parts: at most three for 64 candidates).
+// in runs of shared prefixes (level-wise mining's candidates; fem_count_candidates
+// measures the runs).  (Scattered candidates would be counted in parts, one per run of
+// the node tables' capacity: slower than the per-thread machine.)
 constexpr uint32_t kChainSmallSet = 64;
 bool chain_eligible(const fem_ctx *c, int N, bool distinct, uint32_t m) {
-    return distinct && N >= 2 && N <= FEM_MAX_LEN && m > 0 &&
-           (c->clustered || (N >= 3 && m <= kChainSmallSet));
+    return distinct && N >= 2 && N <= FEM_MAX_LEN && m > 0 && c->clustered;
 }
 
 // The rule's kernel where no measurement says otherwise.  The latest-chain kernels for
