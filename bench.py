@@ -44,12 +44,12 @@ OPS_PER_TOUCHED = {"relaxed": 4, "exact": 6}
 # ("level/pass") from one ncu capture, keyed by the SHA-256 of the kernel source it was
 # taken on and the workload (no entry: stale or not captured, reported as null).
 NCU_TRAFFIC = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:"k_count|k_chain"
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:"k_count|k_chain|k_pairs"
     # -c 5 over the first mining step with the rule's kernels and shapes (--no-tune; the
     # tuned step runs the same kernels), per launch
-    "9a5c87245245fce0": {
-        "single_recording_64types_300s": {"2/relaxed": 13232384, "2/exact": 8706816,
-                                          "3/relaxed": 12876544, "3/exact": 3915520},
+    "1a4385e1d5f33ac7": {
+        "single_recording_64types_300s": {"2/relaxed": 22745600, "2/exact": 8728320,
+                                          "3/relaxed": 12866048},
     },
 }
 
@@ -63,7 +63,8 @@ def kernel_source_hash() -> str:
     for f in ("fem_count.cuh", "fem_count_launch.cuh", "fem_count.cu", "fem_count_relaxed.cu",
               "fem_count_exact.cu", "fem_count_exact_n12.cu", "fem_count_exact_n34.cu",
               "fem_count_exact_n56.cu", "fem_count_exact_n78.cu", "fem_chain.cuh",
-              "fem_chain_launch.cuh", "fem_chain_relaxed.cu", "fem_chain_exact.cu"):
+              "fem_chain_launch.cuh", "fem_chain_relaxed.cu", "fem_chain_exact.cu",
+              "fem_pairs.cu"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     with open(os.path.join(csrc, "fem_internal.cuh"), "rb") as fh:

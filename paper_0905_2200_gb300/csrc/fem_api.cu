@@ -1673,10 +1673,17 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
         *out = res;
         return FEM_OK;
     }
-    // level 2: ordered pairs of distinct frequent types x intervals
     uint64_t m64 = (uint64_t)f1 * nI * (repeats ? f1 : f1 - 1);
     if (m64 > 0xFFFFFFF0ull) return fail(FEM_ENOMEM);
     uint32_t m = (uint32_t)m64;
+    // level 2: ordered pairs of distinct frequent types x intervals.  Its relaxed pass
+    // runs on the pair kernel (fem_pairs.cu) unless a kernel is configured or a shape
+    // was measured or loaded for the pass's class: with two or more intervals a thread
+    // shares one merge of a pair's events among its variants (on the 64-type
+    // recording 0.26 ms against 0.29 for one thread per candidate)
+    const bool pairs_level2 =
+        !repeats && !c->cfg.kernel && nI >= 2 && nI <= 4 &&
+        c->tune.find(tune_key(2, FEM_PASS_RELAXED, true, m, s.n_chunks, s.K)) == c->tune.end();
     const char *cname[2] = {"candsA", "candsB"};
     int cur = 0;
     fem_episode *cands;
@@ -1717,11 +1724,21 @@ int fem_mine_levelwise_ex(fem_ctx *c, int32_t id, const fem_interval *I, uint32_
         // first pass (Algorithm 3) on every candidate, then eliminate relaxed < theta
         PassLaunch plr;
         cudaEventRecord(c->ev[2], st);
-        if (repeats)  // repeated types among the candidates: split and count (count_any)
+        if (repeats) {  // repeated types among the candidates: split and count (count_any)
             RETF(count_any(c, s, cands, nullptr, m, d_ivl, nI, FEM_PASS_RELAXED, rel, st));
-        else
+        } else if (N == 2 && pairs_level2) {
+            // every interval variant of an ordered type pair from one merge; the
+            // candidates it gives up on go to the exact pass unfiltered when they are
+            // at most 1/64 of the level, else to the recount
+            uint32_t *work;
+            RETF(dbuf(c, "pairs_work", 2, &work));
+            CKF(cudaMemsetAsync(work, 0, 2 * sizeof(uint32_t), st));
+            RETF(count_launch_pairs(c, s, cands, m, f1, d_ivl, nI, rel, st, &plr));
+            CKF(launch_pairs_pass_flagged(rel, plr.p.redo, m, m / 64, work, c->d_err, st));
+        } else {
             RETF(count_launch(c, s, cands, nullptr, m, (int)N, d_ivl, nI, FEM_PASS_RELAXED, rel,
                               true, st, &plr));
+        }
         cudaEventRecord(c->ev[3], st);
         cudaEventRecord(c->ev[4], st);
         uint32_t ms;

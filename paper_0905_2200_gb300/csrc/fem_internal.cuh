@@ -203,6 +203,12 @@ cudaError_t launch_publish_load(const uint32_t *err, const uint32_t *t_last, con
 // type pair in one thread (p.pair_types = f, p.n_ivl <= 4; P > 1: MapConcatenate tables)
 cudaError_t launch_pairs_relaxed(const CountParams &p, uint32_t threads, cudaStream_t st);
 size_t pairs_smem_bytes(bool mc, uint32_t threads, uint32_t offs);
+// after that pass in level-wise mining: the flagged candidates' counts set to pass any
+// threshold; their capacity bits cleared when at most `limit` are flagged (work: two
+// words, zero before the first launch, left zero)
+cudaError_t launch_pairs_pass_flagged(uint32_t *out, const uint8_t *redo, uint32_t m,
+                                      uint32_t limit, uint32_t *work, uint32_t *err,
+                                      cudaStream_t st);
 // cap[a * nh + j] (zeroed by the caller): the most type-a events in a closed window of
 // length h[j] (device array); with dense (zeroed), also the number of type-a events whose
 // window of length h[j] holds more than `over` events

@@ -324,4 +324,43 @@ cudaError_t launch_pairs_relaxed(const CountParams &p, uint32_t threads, cudaStr
     return cudaGetLastError();
 }
 
+// Level-wise mining's use of the pass (Algorithm 4).  A candidate whose relaxed count the
+// pair kernel did not finish (flagged: more entry classes than its slots, or a table the
+// stitch could not compose) gets the largest count.  When such candidates are few (at
+// most `limit`), that is all: they pass the elimination and the exact pass decides them
+// -- the relaxed count bounds the exact one from above, so the frequent set is the same
+// -- and the flags' error bits are cleared.  When they are many (bursts), the bits stay
+// and the host recounts them (overwriting the largest counts) before the elimination.
+// work[0..1]: zero before the launch (flag total, blocks done); the last block resets them.
+__global__ void k_pairs_pass_flagged(uint32_t *__restrict__ out, const uint8_t *__restrict__ redo,
+                                     uint32_t m, uint32_t limit, uint32_t *work, uint32_t *err) {
+    __shared__ bool last;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool f = i < m && redo[i] != 0;
+    if (f) out[i] = 0xFFFFFFFFu;
+    const uint32_t nf = (uint32_t)__syncthreads_count(f);
+    if (threadIdx.x == 0) {
+        if (nf) atomicAdd(&work[0], nf);
+        __threadfence();
+        last = atomicAdd(&work[1], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t total = atomicAdd(&work[0], 0u);
+        if (total <= limit) atomicAnd(err, ~(ERR_CLASS | ERR_TABLE));
+        work[0] = 0;
+        work[1] = 0;
+    }
+}
+
+cudaError_t launch_pairs_pass_flagged(uint32_t *out, const uint8_t *redo, uint32_t m,
+                                      uint32_t limit, uint32_t *work, uint32_t *err,
+                                      cudaStream_t st) {
+    if (m == 0) return cudaSuccess;
+    k_pairs_pass_flagged<<<(m + 255) / 256, 256, 0, st>>>(out, redo, m, limit, work, err);
+    note_launch();
+    return cudaGetLastError();
+}
+
 }  // namespace fem

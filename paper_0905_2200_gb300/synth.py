@@ -173,6 +173,26 @@ def bursty_recording(seed=0xFE06, n_types=64, duration_s=300.0, base_hz=5.0,
                 candidates=cands, bursts=(b0, blen))
 
 
+def sparse_bursts(seed=3, n_types=16, base_hz=5.0, duration_s=300.0, n_bursts=6,
+                  burst_ms=100.0, burst_rate_hz=200.0):
+    """A quiet Poisson stream (every type at `base_hz`) with `n_bursts` bursts of
+    `burst_ms` each, at uniform times, in which every type fires at `burst_rate_hz`.
+    Returns (types uint8[n], t uint32[n]), sorted by time (ties by type)."""
+    t, ty = poisson_stream(seed, n_types, base_hz, duration_s)
+    rng = np.random.default_rng(seed)
+    T_us = int(round(duration_s * 1e6))
+    ln = int(round(burst_ms * 1000))
+    bt, bty = [t.astype(np.int64)], [ty.astype(np.int64)]
+    for _ in range(n_bursts):
+        start = int(rng.integers(T_us // 300, T_us - T_us // 300))
+        k = rng.poisson(burst_rate_hz * burst_ms * 1e-3, size=n_types)
+        bt.append(start + np.floor(rng.random(int(k.sum())) * ln).astype(np.int64))
+        bty.append(np.repeat(np.arange(n_types), k))
+    t2, ty2 = np.concatenate(bt), np.concatenate(bty)
+    order = np.lexsort((ty2, t2))
+    return ty2[order].astype(np.uint8), t2[order].astype(np.uint32)
+
+
 def large_stream(seed=0xFE04, n_candidates=100_000, duration_s=3600.0):
     """64 types at 50 Hz for 1 h plus 8 chains; 100k random candidates of lengths 3-5
     with distinct types and random intervals from I_MS4; threshold 5x the chance

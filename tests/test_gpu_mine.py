@@ -82,6 +82,53 @@ def test_mine_repeated_types_equals_oracle(ctx, segments):
     fem.fem_free_stream(ctx, sid)
 
 
+@pytest.mark.parametrize("theta", [1300, 4000])
+@pytest.mark.parametrize("segments", [0, 40])
+def test_mine_bursts_level2_pairs_equals_oracle(ctx, segments, theta):
+    """Level 2's relaxed pass runs on the pair kernel (every interval variant of an
+    ordered type pair in one thread).  In bursts hundreds of candidates need more entry
+    classes than its four slots -- more than 1/64 of the level -- so they are recounted
+    before the elimination: the mined sets and the level-2 survivors equal the oracle's
+    (at theta 4000, above every relaxed count, there are none).  Stream: the bursting
+    recording's types 0, 4, ..., 60 (96k events)."""
+    cfg = synth.bursty_recording()
+    s, I = cfg["stream"], cfg["intervals"]
+    keep = (s.types % 4) == 0
+    ty, t = (s.types[keep] // 4).astype(np.uint8), s.t[keep]
+    sid = fem.fem_load_stream(ctx, ty, t, 16)
+    fem.fem_set_config(ctx, segments=segments)
+    got = fem.fem_mine_levelwise(ctx, sid, I, theta, 3)
+    stats = fem.fem_last_mine_stats(ctx)
+    fem.fem_free_stream(ctx, sid)
+    want = oracle.mine(ty, t, 16, I, theta, 3)
+    assert got == want
+    L, E, iv = synth.level2_candidates(range(16), len(I))
+    rel = oracle.count_batch(ty, t, L, E, iv, I, oracle.RELAXED)
+    assert stats[0]["level"] == 2 and stats[0]["kernel_relaxed"] == fem.KERNEL_PAIRS
+    assert stats[0]["survivors"] == int((rel >= theta).sum())
+
+
+def test_mine_few_flagged_pass_to_exact(ctx):
+    """A quiet 16-type stream with six 100 ms bursts, four segments: 15 level-2
+    candidates (960 / 64) need more entry classes than the pair kernel's slots.  So few
+    go to the exact pass unfiltered -- their relaxed counts are below theta, so the
+    oracle eliminates them -- and the exact pass drops them again: the mined sets equal
+    the oracle's and the level-2 survivors are the oracle's plus those 15."""
+    ty, t = synth.sparse_bursts()
+    I, theta = synth.I_BURST.copy(), 400
+    sid = fem.fem_load_stream(ctx, ty, t, 16)
+    fem.fem_set_config(ctx, segments=4)
+    got = fem.fem_mine_levelwise(ctx, sid, I, theta, 3)
+    stats = fem.fem_last_mine_stats(ctx)
+    fem.fem_free_stream(ctx, sid)
+    assert got == oracle.mine(ty, t, 16, I, theta, 3)
+    L, E, iv = synth.level2_candidates(range(16), len(I))
+    rel = oracle.count_batch(ty, t, L, E, iv, I, oracle.RELAXED)
+    want = int((rel >= theta).sum())
+    assert stats[0]["kernel_relaxed"] == fem.KERNEL_PAIRS and stats[0]["segments"] == 4
+    assert want < stats[0]["survivors"] <= want + len(L) // 64
+
+
 @pytest.fixture(scope="module")
 def single_recording(ctx):
     cfg = synth.single_recording()
