@@ -160,26 +160,30 @@ cudaError_t launch_hist_add(const uint8_t *ty, uint64_t n, uint32_t K, int sign,
 }
 
 // What a load reads back, into mapped pinned host words: the error word, the last time
-// and the K type counts, then (after each thread's system-wide fence and a barrier) the
-// sequence number the host watches for.
+// and the K type counts, then (after one system-wide fence) the sequence number the host
+// watches for.  The block stages the counts in shared memory and one thread writes
+// them all: the writes to host memory are posted, and a single fence is cheaper than one
+// per thread (a fence waits for every earlier write of its thread to reach the host).
 __global__ void __launch_bounds__(256) k_publish_load(const uint32_t *err, const uint32_t *t_last,
                                                       const uint32_t *hist, uint32_t K,
                                                       uint32_t *host, uint32_t seq_word,
                                                       uint32_t seq) {
-    volatile uint32_t *h = host;
-    for (uint32_t a = threadIdx.x; a < K; a += blockDim.x) h[2 + a] = hist[a];
-    if (threadIdx.x == 0) {
-        h[0] = *reinterpret_cast<const volatile uint32_t *>(err);
-        h[1] = t_last ? *t_last : 0u;
-    }
-    __threadfence_system();
+    __shared__ uint32_t hs[256];  // K <= 256
+    for (uint32_t a = threadIdx.x; a < K; a += blockDim.x) hs[a] = hist[a];
     __syncthreads();
-    if (threadIdx.x == 0) h[seq_word] = seq;
+    if (threadIdx.x != 0) return;
+    volatile uint32_t *h = host;
+    for (uint32_t a = 0; a < K; ++a) h[2 + a] = hs[a];
+    h[0] = *reinterpret_cast<const volatile uint32_t *>(err);
+    h[1] = t_last ? *t_last : 0u;
+    __threadfence_system();
+    h[seq_word] = seq;
 }
 
 cudaError_t launch_publish_load(const uint32_t *err, const uint32_t *t_last, const uint32_t *hist,
                                 uint32_t K, uint32_t *host, uint32_t seq_word, uint32_t seq,
                                 cudaStream_t st) {
+    if (K > 256) return cudaErrorInvalidValue;
     k_publish_load<<<1, 256, 0, st>>>(err, t_last, hist, K, host, seq_word, seq);
     note_launch();
     return cudaGetLastError();
