@@ -382,7 +382,7 @@ def run_ours(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded Poisson spike trains with embedded cascades)",
         "config": dict(step_config(cfg, args),
-                       mapping=("rule (segments for ~2048 threads per SM)" if args.no_tune else
+                       mapping=("rule (segments for ~2048 threads per SM, ~1024 for two-node latest-chain counts)" if args.no_tune else
                                 "measured: launch shapes tuned during the warm-up steps, "
                                 f"{tuned} classes cached")),
         "levels": per_level,

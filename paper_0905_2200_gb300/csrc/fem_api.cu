@@ -379,15 +379,20 @@ int ring_choice(fem_ctx *c, const StreamDev &s, bool *large_singles, bool *large
     return FEM_OK;
 }
 
-// Segments per episode for one pass.  One thread per (episode, segment); the
-// aim is about 2048 threads per SM (segments are whole chunks, so at most one
-// segment per chunk).
-uint32_t choose_segments(fem_ctx *c, const StreamDev &s, uint32_t m, bool distinct) {
+// Segments per episode for one pass.  One thread per (episode, segment); the aim is
+// about 2048 threads per SM, and about 1024 for the two-node latest-chain kernel (one
+// resident wave of its four 256-thread blocks per SM): the shapes the tuner keeps on
+// the 64-type recording -- level-2 exact 29 segments (0.169 ms where 50 took 0.201),
+// 13 on the deep variant -- while its longer episodes keep the larger aim (level-4
+// exact of the deep variant: 6 segments 1.65 ms, 3 took 2.07).  Segments are whole
+// chunks, so at most one per chunk.
+uint32_t choose_segments(fem_ctx *c, const StreamDev &s, uint32_t m, bool distinct,
+                         bool one_wave = false) {
     if (s.n_chunks == 0) return 1;
     const uint32_t maxP = std::min<uint32_t>(s.n_chunks, 65535);
     if (c->cfg.segments) return std::min<uint32_t>(c->cfg.segments, s.n_chunks);
     if (!distinct) return 1;
-    const uint64_t target = (uint64_t)c->sm_count * 2048;
+    const uint64_t target = (uint64_t)c->sm_count * (one_wave ? 1024 : 2048);
     uint64_t P = (target + m - 1) / m;
     if (P < 2) return 1;
     return (uint32_t)std::min<uint64_t>(P, maxP);
@@ -479,12 +484,16 @@ int count_pass(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const u
 int tune_pass(fem_ctx *c, const std::string &key, const StreamDev &s, const fem_episode *cands,
               const uint32_t *gather, uint32_t m, int N, const uint2 *d_ivl, uint32_t nI,
               int pass, uint32_t *out, bool distinct, cudaStream_t st) {
-    const uint32_t P0 = choose_segments(c, s, m, distinct);
-    std::vector<uint32_t> Ps{P0};
-    if (distinct) {
-        if (P0 > 1) Ps.push_back(std::max<uint32_t>(1, P0 / 2));
-        if (P0 * 2 <= s.n_chunks) Ps.push_back(P0 * 2);
-    }
+    // per kernel: its rule's segments, half and twice as many
+    auto segment_choices = [&](bool chain_kind) {
+        const uint32_t P0 = choose_segments(c, s, m, distinct, chain_kind && N == 2);
+        std::vector<uint32_t> Ps{P0};
+        if (distinct) {
+            if (P0 > 1) Ps.push_back(std::max<uint32_t>(1, P0 / 2));
+            if (P0 * 2 <= s.n_chunks) Ps.push_back(P0 * 2);
+        }
+        return Ps;
+    };
     const uint32_t R0 = pass == FEM_PASS_EXACT ? (c->cfg.ring_capacity ? c->cfg.ring_capacity : 8) : 1;
     // the shapes to time: per segment count and kernel the rule's block size and its
     // neighbours; the rule's own shape first
@@ -494,7 +503,7 @@ int tune_pass(fem_ctx *c, const std::string &key, const StreamDev &s, const fem_
     for (uint32_t kind : {k0, k0 == FEM_KERNEL_CHAIN ? (uint32_t)FEM_KERNEL_MACHINE : (uint32_t)FEM_KERNEL_CHAIN}) {
         if (kind == FEM_KERNEL_CHAIN && !chain) continue;
         if (c->cfg.kernel && kind != c->cfg.kernel) continue;
-        for (uint32_t P : Ps) {
+        for (uint32_t P : segment_choices(kind == FEM_KERNEL_CHAIN)) {
             if (kind == FEM_KERNEL_CHAIN) {
                 const uint32_t T0 = chain_threads(m);
                 shapes.push_back(fem_ctx::Shape{P, T0, -1.f, kind});
@@ -604,7 +613,7 @@ int count_launch(fem_ctx *c, const StreamDev &s, const fem_episode *cands, const
     p.redo = redo;
 
     uint32_t P = P_t ? std::min<uint32_t>(P_t, std::max<uint32_t>(s.n_chunks, 1))
-                     : choose_segments(c, s, m, distinct);
+                     : choose_segments(c, s, m, distinct, kind == FEM_KERNEL_CHAIN && N == 2);
     if (!distinct) P = 1;
     uint32_t R = 1;
     if (pass == FEM_PASS_EXACT) R = c->cfg.ring_capacity ? c->cfg.ring_capacity : 8;
